@@ -1,0 +1,378 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 NEDNER-NUFFT: one step = one forward
+reconstruction and one adjoint (f = A g, then A^T f) of the 128x128 sensor
+workload (16384 non-equispaced sensors, 512 samples, 128x128x256 voxels).
+
+Prints ONE JSON line (rank 0).  Multi-GPU (torchrun): each rank runs its own
+replica of the workload ("replicas only": a single reconstruction does not
+shard without a collective), timing is the max over ranks and `value` counts
+the voxels of all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the NUFFT algorithm in numpy) on
+the host cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "voxels/s (NEDNER-NUFFT fwd+adjoint, FP32, ≤1e-4 rel L2 vs FP64) and HBM roofline %"
+UNIT = "voxels/s"
+WORKLOAD = ("128x128 non-equispaced sensors over 12.8 mm (8192 jittered lattice + 8192 centre-dense), "
+            "512 samples at 20 ns, 20 balls + 1% noise, output 128x128x256 at 100 um, sigma 2, width 8")
+STAGES = ["ned_spread_rowfft", "ned_colfft", "ner_fused", "image_x", "image_y_c2r", "image_y_adj",
+          "image_x_adj", "ner_adj", "ned_colfft_adj", "ned_rowifft_interp"]
+
+
+def stage_bytes(M, Nt, Nx, Ny, Nz, sigma=2):
+    """Algorithmic bytes per launch of each kernel: its input read once and
+    its output written once (complex64 = 8 B, float32 = 4 B)."""
+    Mx = sigma * Nx
+    nX1, nY1 = 2 * (Nx // 2) + 1, Ny // 2 + 1
+    g = 4 * M * Nt
+    T = 8 * Mx * nY1 * Nt
+    G1 = 8 * nX1 * nY1 * Nt
+    F = 8 * Nx * nY1 * Nz
+    f = 4 * Nx * Ny * Nz
+    return {"ned_spread_rowfft": g + T, "ned_colfft": T + G1, "ner_fused": G1 + F, "image_x": 2 * F,
+            "image_y_c2r": F + f, "image_y_adj": f + F, "image_x_adj": 2 * F, "ner_adj": F + G1,
+            "ned_colfft_adj": G1 + T, "ned_rowifft_interp": T + g}
+
+
+def pipeline_min_bytes(M, Nt, Nx, Ny, Nz):
+    """Minimum HBM bytes of one forward (and, mirrored, one adjoint): read g,
+    write f, round-trip the spatial spectrum and the image spectrum once."""
+    nY1 = Ny // 2 + 1
+    return 4 * M * Nt + 4 * Nx * Ny * Nz + 2 * 8 * Nx * nY1 * Nt + 2 * 8 * Nx * nY1 * Nz
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1501_02946_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as fh:
+                h.update(fn.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(stage):
+    """DRAM bytes per launch of `stage` from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    v = d.get("bytes_per_launch", {}).get(stage)
+    return None if v is None else float(v)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_step(P, fb_seed=0):
+    """One forward + adjoint of the FP64 NUFFT oracle (as it stands)."""
+    import numpy as np
+    from oracle import nufft
+    t0 = time.perf_counter()
+    f = nufft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid)
+    nufft.reconstruct_adjoint(P.xy, P.h, f, P.dt, P.c, P.grid, P.n_t)
+    return time.perf_counter() - t0
+
+
+def cropped(P, s):
+    """Sub-aperture sample of a workload: the sensors within the central
+    (X/s) x (Y/s) square and the matching (nx/s) x (ny/s) x nz output grid."""
+    import numpy as np
+    import synth
+    if s == 1:
+        return P
+    gr = P.grid
+    hx, hy = gr.nx * gr.dx / (2 * s), gr.ny * gr.dy / (2 * s)
+    keep = (P.xy[:, 0] >= -hx) & (P.xy[:, 0] < hx) & (P.xy[:, 1] >= -hy) & (P.xy[:, 1] < hy)
+    grid = synth.Grid(gr.nx // s, gr.ny // s, gr.nz, gr.dx, gr.dy, gr.dz)
+    M = int(keep.sum())
+    h = np.full(M, (2 * hx) * (2 * hy) / M)
+    return synth.Problem(P.name + f"_crop{s}", P.xy[keep], h, P.g[keep], P.dt, P.c, grid)
+
+
+def cpu_baseline_subprocess(s=1):
+    """Time the oracle single-threaded in a fresh interpreter (BLAS/FFT threads
+    pinned to 1 so `cores` is exact)."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench, synth; "
+            "P = bench.cropped(synth.c2(), %d); t = bench.cpu_oracle_step(P); "
+            "print(json.dumps({'t': t, 'voxels': P.grid.nx * P.grid.ny * P.grid.nz, 'M': P.n_sensors}))"
+            % (ROOT, s))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("cpu baseline failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import synth
+    # sample per step: a central sub-aperture crop sized so that the whole
+    # (steps + warmup) run stays within about three minutes
+    t_full_est = 25.0
+    n = args.steps + args.warmup
+    s = 1
+    while s < 8 and n * t_full_est / (s * s) > 180.0:
+        s *= 2
+    P = cropped(synth.c2(), s)
+    times = []
+    for i in range(n):
+        t = cpu_oracle_step(P)
+        if i >= args.warmup:
+            times.append(t)
+    voxels = P.grid.nx * P.grid.ny * P.grid.nz
+    ms = 1e3 * sum(times) / len(times)
+    value = voxels / (ms / 1e3)
+    sample = (f"central {P.grid.nx}x{P.grid.ny} of 128x128 sub-aperture ({P.n_sensors} sensors), "
+              f"512 samples, depth 256; one FP64 forward+adjoint per step")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample": sample, "oracle": "FP64 NUFFT (numpy), width 16"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1501_02946_gb300 as pa
+    import synth
+
+    P = synth.c2()
+    Nx, Ny, Nz = P.grid.shape
+    voxels = Nx * Ny * Nz
+    plan = pa.Plan(P.xy, P.n_t, P.dt, P.c, P.grid.as_tuple(), weights=P.h)
+    g = torch.tensor(P.g, dtype=torch.float32, device=dev)
+    f = torch.empty(P.grid.shape, dtype=torch.float32, device=dev)
+    g2 = torch.empty_like(g)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.reconstruct(g, out=f)
+        plan.adjoint(f, out=g2)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    plan.profile(True)
+    plan.profile_read()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(dev.index if world == 1 else int(os.environ.get("LOCAL_RANK", "0")))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (256 MiB written), outside the events
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    gpu_ms = sum(a.elapsed_time(b) for a, b in ev)
+    prof = plan.profile_read()
+    plan.profile(False)
+    if world > 1:
+        t = torch.tensor([gpu_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        gpu_ms = float(t.item())
+    ms_per_step = gpu_ms / args.steps
+    value = world * voxels / (ms_per_step / 1e3)
+
+    # roofline of the dominant kernel (largest device time in the timed region)
+    peaks, peak_kind = measured_peaks()
+    sb = stage_bytes(P.n_sensors, P.n_t, Nx, Ny, Nz)
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / prof[dom][1]
+    achieved = sb[dom] / (dom_ms / 1e3) / 1e9
+    hbm = float(peaks["hbm_gbs"])
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": ncu_traffic(dom), "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": sb[dom], "launch_ms": dom_ms}
+    stages = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
+                  "gbs": sb[k] / (v[0] / v[1] / 1e3) / 1e9 if k in sb else None,
+                  "share": v[0] / sum(x[0] for x in prof.values())} for k, v in prof.items()}
+    pipe = 2 * pipeline_min_bytes(P.n_sensors, P.n_t, Nx, Ny, Nz)
+    pipeline = {"min_bytes_per_step": pipe, "achieved_gbs": pipe / (ms_per_step / 1e3) / 1e9,
+                "frac": pipe / (ms_per_step / 1e3) / 1e9 / hbm}
+
+    # end to end through the public API with host buffers
+    g_h = torch.tensor(P.g, dtype=torch.float32).pin_memory()
+    f_h = torch.empty(P.grid.shape, dtype=torch.float32).pin_memory()
+    g2_h = torch.empty(g_h.shape, dtype=torch.float32).pin_memory()
+    n_e2e = min(args.steps, 10)
+    for _ in range(2):
+        g.copy_(g_h, non_blocking=True)
+        step()
+        f_h.copy_(f, non_blocking=True)
+        g2_h.copy_(g2, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n_e2e):
+        g.copy_(g_h, non_blocking=True)
+        step()
+        f_h.copy_(f, non_blocking=True)
+        g2_h.copy_(g2, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / n_e2e
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * voxels / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": g_h.numel() * 4,
+           "d2h_bytes_per_step": (f_h.numel() + g2_h.numel()) * 4, "ms_per_step": e2e_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = cpu_baseline_subprocess(1)
+        cpu = {"value": r["voxels"] / r["t"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one FP64 forward+adjoint of the full workload (NUFFT oracle, width 16), "
+                         "single thread", "seconds": r["t"]}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "step": "forward + adjoint (A g, then A^T of the result)",
+                      "l2": "flushed between timed steps (256 MiB write outside the timed events)",
+                      "parallelism": f"replicas x{world}", "wall_s": t_wall},
+           "roofline": roofline, "pipeline_roofline": pipeline, "stages": stages, "cpu_baseline": cpu,
+           "e2e": e2e, "gpu_launches": 10 * args.steps, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(out))
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

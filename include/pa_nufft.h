@@ -1,0 +1,198 @@
+/*
+ * pa_nufft.h -- C ABI of the GB300 NEDNER-NUFFT library for planar-sensor
+ * photoacoustic reconstruction (Schmid, Glatz, Zabihian, Liu, Drexler,
+ * Scherzer, "Computational Realization of a Non-Equidistant Grid Sampling in
+ * Photoacoustics with a Non-Uniform FFT").
+ *
+ * What the library computes (Sec. 2, eq:exact discretised as eq:disc_rec,
+ * evaluated by the three NUFFT steps of Sec. 3), in physical units with sound
+ * speed c.  Sensors m = 0..M-1 sit at (x_m, y_m) on the plane z = 0 with
+ * detector areas h_m; data g[m][n] is sampled at t_n = n*dt, n = 0..n_t-1.
+ * For the output grid nx x ny x nz with spacings dx, dy, dz
+ * (X = nx dx, Y = ny dy, Z = nz dz), frequency indices j in
+ * {-floor(N/2) .. ceil(N/2)-1} per axis and k = 2 pi j / X:
+ *
+ *   G1(j,n)  = sum_m (h_m/(dx dy)) g[m][n] exp(-i (kx x_m + ky y_m))   eq:NUDFT2
+ *   w(j,l)   = c sign(l) sqrt(kx^2 + ky^2 + kz^2)     (sign(0) = +1)
+ *   F(j,l)   = (dt/dz) W(j,l) sum_n G1(j,n) exp(-i w(j,l) t_n)         eq:NUDFT1
+ *   W(j,l)   = 2 c |kz| / |K|,  W(0,0) = 2c            (factor 2 K_y / kappa, eq:exact)
+ *   f[p][q][k] = Re( 1/(nx ny nz) sum_{j,l} F(j,l) exp(i(kx x_p + ky y_q + kz z_k)) )
+ *
+ * with voxel centres x_p = (p - floor(nx/2)) dx, y_q = (q - floor(ny/2)) dy,
+ * z_k = k dz.  The sums over m and over n are evaluated approximately by the
+ * NED-NUFFT (eq:NED_NUFFT) and the NER-NUFFT (eq:NER_NUFFT) with a
+ * Kaiser-Bessel window of `width` taps on a grid oversampled by `sigma`; the
+ * rest is exact.  All device arithmetic is FP32 (frequency arguments formed
+ * in double-float precision).
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: PA_OK (0) or one of the PA_ERR_* codes below; on error
+ *    pa_last_error() returns a message (thread-local, valid until the next
+ *    call from the same thread).
+ *  - Device buffers ("*_dev") are owned by the caller, live on the device the
+ *    plan was created on, are not aliased with each other, and are dense
+ *    C-order FP32 arrays.  Calls are asynchronous and ordered on `stream`
+ *    (a cudaStream_t; NULL means the legacy default stream).
+ *  - A plan owns its device workspace and tables; it is not safe to run one
+ *    plan on two streams at the same time.
+ */
+#ifndef PA_NUFFT_H
+#define PA_NUFFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PA_OK 0
+#define PA_ERR_INVALID_ARG 1      /* NULL pointer, non-finite or out-of-range value */
+#define PA_ERR_UNSUPPORTED_SIZE 2 /* a transform length is not 2^a 3^b 5^c 7^d or too large */
+#define PA_ERR_CUDA 3             /* a CUDA runtime call failed (message has the CUDA error) */
+#define PA_ERR_OOM 4              /* device allocation failed */
+#define PA_ERR_TIMEOUT 5          /* a bounded device wait gave up (batched persistent path) */
+#define PA_ERR_DEVICE 6           /* a kernel recorded an error in the plan's status word */
+
+#define PA_FLAG_DEFAULT 0
+
+typedef struct pa_plan pa_plan;
+typedef struct pa_batch pa_batch;
+
+/* Output grid: nx x ny x nz voxels with spacings dx, dy, dz in metres. */
+typedef struct {
+  int32_t nx, ny, nz;
+  double dx, dy, dz;
+} pa_grid;
+
+/*
+ * Create a reconstruction plan (Sec. 3: the set-up of both NUFFTs).
+ *   out        receives the plan (set to NULL on failure).
+ *   n_sensors  M >= 1.
+ *   sensor_xy  host, [M][2] doubles (x_m, y_m) in metres; copied.  Any finite
+ *              value is accepted: positions are reduced modulo X and Y, which
+ *              is exact because the sums are X- and Y-periodic.
+ *   weights    host, [M] detector areas h_m in m^2 (> 0), copied; NULL means
+ *              h_m = X*Y/M (Sec. 2 requires sum h_m = X^(d-1)).
+ *   n_t        number of time samples (>= 2); dt > 0 sampling step in s;
+ *   c          sound speed in m/s (> 0).
+ *   grid       output grid (sizes >= 2, spacings > 0).
+ *   sigma      oversampling factor c of Sec. 3, integer in [2, 4].
+ *   width      window taps 2K of Sec. 3, even, in {6, 8, 12, 16}.
+ *   flags      PA_FLAG_DEFAULT.
+ *   stream     stream used for the initial uploads (a cudaStream_t or NULL).
+ * Supported sizes: nx, ny, nz, n_t and sigma*nx, sigma*ny, sigma*n_t must be
+ * products of 2, 3, 5, 7, with sigma*nx, sigma*ny, nz, nx, ny <= 4096,
+ * sigma*n_t <= 4096 and sigma*nx, sigma*ny >= 2*width; else
+ * PA_ERR_UNSUPPORTED_SIZE.  The plan is created on the current CUDA device.
+ */
+int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy,
+                   const double *weights, int64_t n_t, double dt, double c,
+                   const pa_grid *grid, int sigma, int width, int flags,
+                   void *stream);
+
+/*
+ * Forward reconstruction f = A g (eq:disc_rec via NEDNER-NUFFT, Sec. 3).
+ *   g_dev  device [M][n_t] float, sensor order as given to pa_plan_create.
+ *   f_dev  device [nx][ny][nz] float (written entirely).
+ */
+int pa_reconstruct(pa_plan *plan, const float *g_dev, float *f_dev, void *stream);
+
+/*
+ * Adjoint g = A^T f: the exact transpose (real inner products) of the
+ * approximate forward operator of this plan -- same windows, grids and
+ * tables -- so that <A g, f> = <g, A^T f> up to FP32 rounding.
+ *   f_dev  device [nx][ny][nz] float;  g_dev device [M][n_t] float (written).
+ */
+int pa_reconstruct_adjoint(pa_plan *plan, const float *f_dev, float *g_dev, void *stream);
+
+/*
+ * Sensor-position gradient of L = <grad_f, A(x) g> for fixed h_m, through the
+ * window derivative of eq:NED_NUFFT:
+ *   dL/dx_m = (h_m/(dx dy)) sum_n g[m][n] sum_{p,q} (sigma nx / X) phi'(Ux_m - p)
+ *             phi(Uy_m - q) R[p][q][n],  likewise for y,
+ * where R is the oversampled-grid cotangent of the transposed chain.
+ *   g_dev        device [M][n_t] data the forward was applied to.
+ *   grad_f_dev   device [nx][ny][nz] cotangent of the image.
+ *   grad_g_dev   device [M][n_t] or NULL: also receives A^T grad_f.
+ *   grad_xy_dev  device [M][2] float, receives (dL/dx_m, dL/dy_m).
+ */
+int pa_position_grad(pa_plan *plan, const float *g_dev, const float *grad_f_dev,
+                     float *grad_g_dev, float *grad_xy_dev, void *stream);
+
+/*
+ * Replace the sensor positions (host [M][2] doubles, metres) of an existing
+ * plan; the binning and window taps are rebuilt and uploaded on `stream`.
+ * Weights stay as they were.
+ */
+int pa_plan_update_positions(pa_plan *plan, const double *sensor_xy, void *stream);
+
+/*
+ * Same-GPU baseline of Sec. 2's polynomial interpolation: identical NED and
+ * inverse FFT, but the time transform is a plain n_t-point FFT per column
+ * followed by 4-tap cubic Lagrange interpolation at the non-integer
+ * frequencies instead of the NER-NUFFT.  Benchmark comparison only.
+ */
+int pa_reconstruct_cubic(pa_plan *plan, const float *g_dev, float *f_dev, void *stream);
+
+/* Destroy a plan and free its device memory (NULL-safe; synchronises the device). */
+int pa_plan_destroy(pa_plan *plan);
+
+/*
+ * Batched reconstruction of many independent plans of uneven sizes: every
+ * stage runs as one launch over all instances, and the launch sequence is
+ * captured once in a CUDA graph and replayed.
+ *   pa_batch_create: plans[n] (not owned; must outlive the batch; same sigma
+ *                    and width), n >= 1.
+ *   pa_batch_run:    g_dev[i] / f_dev[i] host arrays of n device pointers.
+ */
+int pa_batch_create(pa_batch **out, int n, pa_plan *const *plans, void *stream);
+int pa_batch_run(pa_batch *batch, const float *const *g_dev, float *const *f_dev, void *stream);
+int pa_batch_destroy(pa_batch *batch);
+
+/*
+ * Read and clear the plan's device status word (synchronises `stream`):
+ * *device_status = 0 when no kernel recorded an error.
+ */
+int pa_status(pa_plan *plan, int *device_status, void *stream);
+
+/* Plan properties: sizes of the workspace in bytes and of the problem. */
+int pa_plan_info(const pa_plan *plan, int64_t *n_sensors, int64_t *n_t,
+                 int64_t *workspace_bytes);
+
+/*
+ * Copy one of the plan's intermediate buffers, as left by the last call, into
+ * a caller buffer (tests and diagnostics).
+ * which: 0 = G1, the spatial spectrum after the NED step (Sec. 3 step 1),
+ *            complex64 [2*floor(nx/2)+1][floor(ny/2)+1][n_t] holding
+ *            jx = -floor(nx/2)..floor(nx/2) and jy = 0..floor(ny/2);
+ *        1 = the image spectrum after the NER step and the inverse DFT over
+ *            depth, complex64 [nx][floor(ny/2)+1][nz] (jx = ix - floor(nx/2)).
+ * dst_dev: device buffer of capacity_bytes; *bytes receives the size.  With
+ * dst_dev NULL only *bytes is set.  Asynchronous on `stream`.
+ */
+int pa_plan_buffer(const pa_plan *plan, int which, void *dst_dev, int64_t capacity_bytes,
+                   int64_t *bytes, void *stream);
+
+/*
+ * Per-stage timing with CUDA events recorded on the call's stream around
+ * every kernel launch (diagnostics, off by default).  pa_profile_read waits
+ * for the recorded events, returns per stage the summed device time in ms
+ * and the number of launches since the last read, and clears them.
+ * Stages: see pa_profile_stage_name (0 .. PA_PROFILE_STAGES-1).
+ */
+#define PA_PROFILE_STAGES 12
+int pa_profile_enable(pa_plan *plan, int enable);
+int pa_profile_read(pa_plan *plan, double *ms_total, int64_t *launches);
+const char *pa_profile_stage_name(int stage);
+
+/* Message of the last error on this thread ("" if none). */
+const char *pa_last_error(void);
+
+/* Library version string. */
+const char *pa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PA_NUFFT_H */

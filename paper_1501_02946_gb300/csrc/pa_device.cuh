@@ -1,0 +1,314 @@
+// pa_device.cuh -- device helpers of the NEDNER-NUFFT kernels: complex
+// arithmetic, double-float arithmetic for the time-frequency arguments, and a
+// batched mixed-radix Stockham FFT that runs in shared memory.
+#pragma once
+
+#include "pa_internal.h"
+
+namespace pa {
+
+// ---------------------------------------------------------------- complex
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by DIR * i (DIR = -1: by -i, DIR = +1: by +i)
+template <int DIR>
+__device__ __forceinline__ float2 mul_i(float2 a) {
+  return DIR > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// ---------------------------------------------------------- double-float
+// Error-free transformations (Knuth two-sum, FMA two-product) and the
+// resulting ~48-bit arithmetic on (hi, lo) pairs of floats.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff quick_two_sum(float a, float b) {
+  float s = a + b;
+  float e = b - (s - a);
+  return {s, e};
+}
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+__device__ __forceinline__ ff two_prod(float a, float b) {
+  float p = a * b;
+  float e = fmaf(a, b, -p);
+  return {p, e};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = two_sum(a.hi, b.hi);
+  s.lo += a.lo + b.lo;
+  return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  ff p = two_prod(a.hi, b);
+  p.lo = fmaf(a.lo, b, p.lo);
+  return quick_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  ff p = two_prod(a.hi, b.hi);
+  p.lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
+  return quick_two_sum(p.hi, p.lo);
+}
+// square root with one Newton correction: s + (a - s^2) / (2 s)
+__device__ __forceinline__ ff ff_sqrt(ff a) {
+  if (!(a.hi > 0.f)) return {0.f, 0.f};
+  float s = sqrtf(a.hi);
+  ff s2 = two_prod(s, s);
+  float r = ((a.hi - s2.hi) - s2.lo + a.lo) / (2.f * s);
+  return quick_two_sum(s, r);
+}
+
+// -------------------------------------------------------------- FFT
+// Exact values of cos(2 pi m / R) and sin(2 pi m / R) for R = 16, 3, 5, 7
+// (indices are compile-time constants after unrolling, so these fold).
+struct Tw16 {
+  __device__ __forceinline__ static constexpr float c(int m) {
+    return m == 0 ? 1.0f : m == 1 ? 0.92387953251128674f : m == 2 ? 0.70710678118654752f
+         : m == 3 ? 0.38268343236508977f : m == 4 ? 0.0f : m == 5 ? -0.38268343236508977f
+         : m == 6 ? -0.70710678118654752f : m == 7 ? -0.92387953251128674f : m == 8 ? -1.0f
+         : m == 9 ? -0.92387953251128674f : m == 10 ? -0.70710678118654752f
+         : m == 11 ? -0.38268343236508977f : m == 12 ? 0.0f : m == 13 ? 0.38268343236508977f
+         : m == 14 ? 0.70710678118654752f : 0.92387953251128674f;
+  }
+  __device__ __forceinline__ static constexpr float s(int m) { return c((m + 12) & 15); }
+};
+struct Tw3 {
+  __device__ __forceinline__ static constexpr float c(int m) { return m == 0 ? 1.0f : -0.5f; }
+  __device__ __forceinline__ static constexpr float s(int m) {
+    return m == 0 ? 0.0f : m == 1 ? 0.86602540378443865f : -0.86602540378443865f;
+  }
+};
+struct Tw5 {
+  __device__ __forceinline__ static constexpr float c(int m) {
+    return m == 0 ? 1.0f : (m == 1 || m == 4) ? 0.30901699437494742f : -0.80901699437494742f;
+  }
+  __device__ __forceinline__ static constexpr float s(int m) {
+    return m == 0 ? 0.0f : m == 1 ? 0.95105651629515357f : m == 2 ? 0.58778525229247313f
+         : m == 3 ? -0.58778525229247313f : -0.95105651629515357f;
+  }
+};
+struct Tw7 {
+  __device__ __forceinline__ static constexpr float c(int m) {
+    return m == 0 ? 1.0f : (m == 1 || m == 6) ? 0.62348980185873353f
+         : (m == 2 || m == 5) ? -0.22252093395631440f : -0.90096886790241913f;
+  }
+  __device__ __forceinline__ static constexpr float s(int m) {
+    return m == 0 ? 0.0f : m == 1 ? 0.78183148246802981f : m == 2 ? 0.97492791218182361f
+         : m == 3 ? 0.43388373911755812f : m == 4 ? -0.43388373911755812f
+         : m == 5 ? -0.97492791218182361f : -0.78183148246802981f;
+  }
+};
+
+// In-register DFT of size R: v[k] <- sum_n v[n] exp(DIR 2 pi i n k / R).
+template <int R, int DIR>
+struct Dft;
+
+template <int DIR>
+struct Dft<2, DIR> {
+  __device__ __forceinline__ static void run(float2 *v) {
+    float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <int DIR>
+struct Dft<4, DIR> {
+  __device__ __forceinline__ static void run(float2 *v) {
+    float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    float2 s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
+    float2 t = mul_i<DIR>(d13);
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    v[1] = cadd(d02, t);
+    v[3] = csub(d02, t);
+  }
+};
+
+template <typename TW, int R, int DIR>
+struct DftNaive {
+  __device__ __forceinline__ static void run(float2 *v) {
+    float2 out[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      float2 acc = v[0];
+#pragma unroll
+      for (int n = 1; n < R; ++n) {
+        const int e = (n * k) % R;
+        if (e == 0) {
+          acc = cadd(acc, v[n]);
+        } else {
+          const float c = TW::c(e), s = DIR * TW::s(e);
+          acc.x += v[n].x * c - v[n].y * s;
+          acc.y += v[n].x * s + v[n].y * c;
+        }
+      }
+      out[k] = acc;
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = out[k];
+  }
+};
+template <int DIR>
+struct Dft<3, DIR> : DftNaive<Tw3, 3, DIR> {};
+template <int DIR>
+struct Dft<5, DIR> : DftNaive<Tw5, 5, DIR> {};
+template <int DIR>
+struct Dft<7, DIR> : DftNaive<Tw7, 7, DIR> {};
+
+// Cooley-Tukey composition N = N1 N2 (N divides 16): n = N2 n1 + n2,
+// k = k1 + N1 k2, inner twiddle exp(DIR 2 pi i n2 k1 / N).
+template <int N1, int N2, int DIR>
+struct DftComp {
+  __device__ __forceinline__ static void run(float2 *v) {
+    constexpr int N = N1 * N2;
+    float2 y[N2][N1];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) {
+      float2 t[N1];
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) t[n1] = v[N2 * n1 + n2];
+      Dft<N1, DIR>::run(t);
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        const int e = ((n2 * k1) * (16 / N)) % 16;
+        if (e == 0) {
+          y[n2][k1] = t[k1];
+        } else {
+          const float c = Tw16::c(e), s = DIR * Tw16::s(e);
+          y[n2][k1] = make_float2(t[k1].x * c - t[k1].y * s, t[k1].x * s + t[k1].y * c);
+        }
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      float2 t[N2];
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) t[n2] = y[n2][k1];
+      Dft<N2, DIR>::run(t);
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) v[k1 + N1 * k2] = t[k2];
+    }
+  }
+};
+template <int DIR>
+struct Dft<8, DIR> : DftComp<2, 4, DIR> {};
+template <int DIR>
+struct Dft<16, DIR> : DftComp<4, 4, DIR> {};
+
+// Items (butterflies) a thread holds per round, by radix.
+template <int R>
+struct Ipt {
+  static constexpr int v = R >= 16 ? 1 : (R >= 5 ? 2 : 4);
+};
+
+// One Stockham stage (Govindaraju et al., "High performance discrete Fourier
+// transforms on graphics processors", SC 2008) applied in place: every item
+// j < L/R reads x[j + t L/R] (t < R), multiplies by exp(DIR 2 pi i t k / (Ns R))
+// with k = j mod Ns, takes an R-point DFT and writes position
+// (j / Ns) Ns R + k + t Ns.  Sequences b < nb are interleaved with stride 1
+// (element i of sequence b at buf[i * estride + b]).  Reads of a round finish
+// (barrier) before its writes; rounds cover whole sequences.
+template <int R, int DIR>
+__device__ __forceinline__ void fft_stage(float2 *buf, int estride, int nb, int L, int Ns,
+                                          const float2 *__restrict__ tw, int tid, int nthr) {
+  constexpr int IPT = Ipt<R>::v;
+  const int nj = L / R;
+  const int twstep = L / (Ns * R);
+  int spr = (nthr * IPT) / nj;
+  if (spr < 1) spr = 1;
+  for (int b0 = 0; b0 < nb; b0 += spr) {
+    const int nbr = min(spr, nb - b0);
+    const int items = nj * nbr;
+    float2 v[IPT][R];
+#pragma unroll
+    for (int it = 0; it < IPT; ++it) {
+      const int item = tid + it * nthr;
+      if (item < items) {
+        const int b = b0 + item % nbr;
+        const int j = item / nbr;
+        const int k = j % Ns;
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+          float2 x = buf[(j + t * nj) * estride + b];
+          if (t > 0 && k > 0) {
+            float2 w = __ldg(tw + t * k * twstep);
+            if (DIR > 0) w.y = -w.y;
+            x = cmul(x, w);
+          }
+          v[it][t] = x;
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < IPT; ++it) {
+      const int item = tid + it * nthr;
+      if (item < items) {
+        const int b = b0 + item % nbr;
+        const int j = item / nbr;
+        const int k = j % Ns;
+        Dft<R, DIR>::run(v[it]);
+        const int o = (j / Ns) * Ns * R + k;
+#pragma unroll
+        for (int t = 0; t < R; ++t) buf[(o + t * Ns) * estride + b] = v[it][t];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Whole transform y[k] = sum_i x[i] exp(DIR 2 pi i i k / L), unnormalised,
+// in place in shared memory.  All threads of the block must call it.
+template <int DIR>
+__device__ void fft_smem(float2 *buf, int estride, int nb, const FftPlan &fp, const float2 *__restrict__ twbase,
+                         int tid, int nthr) {
+  const float2 *tw = twbase + fp.tw;
+  const int L = fp.L;
+  const int nst = fp.nst;
+  int Ns = 1, s = 0;
+  // The schedule lists radices in the order 16, 8, 4, 2, 3, 5, 7; one loop per
+  // radix keeps the register allocation of each radix separate.
+#define PA_FFT_RUN(R)                                                   \
+  while (s < nst && fp.radix[s] == R) {                                 \
+    fft_stage<R, DIR>(buf, estride, nb, L, Ns, tw, tid, nthr);          \
+    Ns *= R;                                                            \
+    ++s;                                                                \
+  }
+  PA_FFT_RUN(16)
+  PA_FFT_RUN(8)
+  PA_FFT_RUN(4)
+  PA_FFT_RUN(2)
+  PA_FFT_RUN(3)
+  PA_FFT_RUN(5)
+  PA_FFT_RUN(7)
+#undef PA_FFT_RUN
+}
+
+// Instance and tile of this block.
+__device__ __forceinline__ void block_work(const int2 *__restrict__ work, int &inst, int &tile) {
+  if (work) {
+    int2 w = work[blockIdx.x];
+    inst = w.x;
+    tile = w.y;
+  } else {
+    inst = 0;
+    tile = blockIdx.x;
+  }
+}
+
+__device__ __forceinline__ int wrap(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+}  // namespace pa

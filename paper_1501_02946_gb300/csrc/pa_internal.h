@@ -1,0 +1,136 @@
+// pa_internal.h -- data structures shared by the host plan code and the
+// sm_103a kernels of the NEDNER-NUFFT library.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pa {
+
+constexpr int kMaxStages = 12;
+constexpr int kMaxFft = 4096;
+constexpr int kMaxWidth = 16;
+constexpr int kMaxDeg = 15;
+
+// Mixed-radix Stockham schedule for one transform length L: the radices in
+// the order they are applied and the offset of the length-L twiddle table
+// exp(-2 pi i m / L), m = 0..L-1, inside the plan's twiddle array.
+struct FftPlan {
+  int L;
+  int nst;
+  int radix[kMaxStages];
+  int tw;
+};
+
+// Horner coefficients of the window taps used by the NER interpolation:
+// tap t (0..w-1) at fraction fr in [0,1) of the oversampled time-frequency
+// grid is phi(fr + w/2 - 1 - t) = sum_d c[t][d] s^d with s = 2 fr - 1, where
+// phi is the Kaiser-Bessel window normalised to phi(0) = 1.
+struct HornerTable {
+  float c[kMaxWidth][kMaxDeg + 1];
+};
+
+// One reconstruction instance as the kernels see it.  Every kernel reads
+// only this struct (plus its own tile index), so a batch is an array of them.
+struct InstDesc {
+  // problem sizes
+  int M, Nt, Nx, Ny, Nz;
+  int Mx, My, Mt;       // oversampled lengths sigma*Nx, sigma*Ny, sigma*Nt
+  int w;                // window taps
+  int hx, hy, hz, nc;   // floor(N/2) of x, y, z, t
+  int nX1, nY1;         // rows of the spatial spectrum: 2*hx+1 (jx) and hy+1 (jy)
+  int nchunk_adj;       // n-chunks of the adjoint NED kernel (gradient partials)
+
+  FftPlan fMy, fMx, fMt, fNz, fNx, fNy, fNt;
+  const float2 *tw;
+
+  // sensors sorted by (bx, by); taps t = 0..w-1 cover cells base - w/2 + 1 + t
+  const int *perm;      // sorted -> caller's sensor index
+  const int *sbx, *sby; // base cells, wrapped into [0, Mx) and [0, My)
+  const float *wx, *wy; // [M][w]; wy carries a_m = h_m/(dx dy)
+  const float *dwx, *dwy;  // [M][w] derivative taps d/dx_m and d/dy_m
+  const int *cell_start;   // [Mx*My + 1] CSR offsets of the sorted sensors per cell
+  // deconvolution factors 1/phihat (window normalised to phi(0) = 1)
+  const float *invphx;  // [nX1], jx = ix - hx, at jx / Mx
+  const float *invphy;  // [nY1], jy, at jy / My
+  const float *invpht;  // [Nt], at (n - nc) / Mt
+
+  // time-frequency constants, each as a double-float pair (hi, lo):
+  // tau(j,l)^2 = ax jx^2 + ay jy^2 + az l^2, tau = omega Nt dt / (2 pi),
+  // phase turns of the centring exp(-2 pi i tau nc / Nt) = tau * ph.
+  float ax_hi, ax_lo, ay_hi, ay_lo, az_hi, az_lo;
+  float ph_hi, ph_lo;
+  float sqrt_az;        // c Nt dt / Z, for W(j,l) = 2c sqrt_az |l| / |tau|
+  float two_c;          // 2 c
+  float scale;          // dt / (dz Nx Ny Nz)
+  int sigma;
+
+  // workspace (device)
+  float2 *T;            // [Mx][nY1][Nt]   after the row transform (aliases Fz/U)
+  float2 *G1;           // [nX1][nY1][Nt]  spatial spectrum
+  float2 *Fz;           // [Nx][nY1][Nz]   after NER and the inverse depth DFT
+  float2 *U;            // [Nx][nY1][Nz]   after the inverse x DFT
+  float2 *grad_part;    // [nchunk_adj][M] per-chunk position-gradient partials
+  int *status;
+};
+
+// Caller buffers of one call (device pointers).  Single-plan launches pass
+// them by value; batched launches pass a device table indexed by instance.
+struct IoPtrs {
+  const float *g_in;    // [M][Nt]
+  float *f_out;         // [Nx][Ny][Nz]
+  const float *f_in;    // [Nx][Ny][Nz]
+  float *g_out;         // [M][Nt] or null
+  float *grad_xy;       // [M][2] or null
+};
+
+// Tile shapes (chosen on the host; kernels are templated on them).
+constexpr int kSpreadP = 4;      // oversampled rows per forward NED strip
+constexpr int kSpreadNCP = 8;    // complex pairs of samples per forward strip
+constexpr int kSpreadGPW = 8;    // q-groups per warp
+constexpr int kSpreadSMax = 128; // sensors staged per pass
+constexpr int kColNC = 16;       // samples per column-FFT tile
+constexpr int kAdjPo = 4;        // owned sensor rows per adjoint NED tile
+constexpr int kAdjNCP = 4;       // sample pairs per adjoint NED tile
+constexpr int kImgZC = 16;       // depth samples per inverse-x tile
+constexpr int kImgZP = 16;       // depth pairs per y-C2R tile
+
+// Launch helpers implemented in the .cu files.  `work` lists (instance, tile)
+// pairs for batched launches; null means instance 0 and tile = blockIdx.x.
+struct Launch {
+  const InstDesc *descs;  // device array
+  const int2 *work;       // device array or null
+  IoPtrs io;              // caller buffers (single plan)
+  const IoPtrs *io_table; // device array (batch) or null
+  int nblocks;
+  size_t smem;
+  cudaStream_t stream;
+};
+
+// Block counts and shared-memory sizes per stage for one instance.
+int blocks_spread(const InstDesc &d);
+size_t smem_spread(const InstDesc &d);
+int threads_spread(const InstDesc &d);
+int blocks_colfft(const InstDesc &d);
+size_t smem_colfft(const InstDesc &d);
+int blocks_ner(const InstDesc &d);
+size_t smem_ner(const InstDesc &d);
+int blocks_ner_adj(const InstDesc &d);
+size_t smem_ner_adj(const InstDesc &d);
+int blocks_imgx(const InstDesc &d);
+size_t smem_imgx(const InstDesc &d);
+int blocks_imgy(const InstDesc &d);
+size_t smem_imgy(const InstDesc &d);
+int blocks_interp(const InstDesc &d);
+size_t smem_interp(const InstDesc &d);
+
+cudaError_t launch_spread(const Launch &L, int threads);
+cudaError_t launch_colfft(const Launch &L, bool adjoint);
+cudaError_t launch_ner(const Launch &L, int width, const HornerTable &ht, bool adjoint);
+cudaError_t launch_cubic(const Launch &L);
+cudaError_t launch_imgx(const Launch &L, bool adjoint);
+cudaError_t launch_imgy(const Launch &L, bool adjoint);
+cudaError_t launch_interp_width(const Launch &L, int width, bool grad);
+cudaError_t launch_grad_reduce(const Launch &L, int M);
+
+}  // namespace pa

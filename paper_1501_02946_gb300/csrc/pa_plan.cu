@@ -1,0 +1,872 @@
+// pa_plan.cu -- host side of the NEDNER-NUFFT library: plan construction
+// (Sec. 3 set-up: grid coordinates of the sensors, their window taps and
+// binning, deconvolution tables, FFT schedules, time-frequency constants),
+// the C ABI of include/pa_nufft.h and the batched CUDA-graph path.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "pa_internal.h"
+#include "pa_nufft.h"
+
+using pa::FftPlan;
+using pa::HornerTable;
+using pa::InstDesc;
+using pa::IoPtrs;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+#define PA_CUDA(expr)                                                                 \
+  do {                                                                                \
+    cudaError_t e_ = (expr);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      if (e_ == cudaErrorMemoryAllocation)                                            \
+        return fail(PA_ERR_OOM, std::string(#expr) + ": " + cudaGetErrorString(e_));  \
+      return fail(PA_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));   \
+    }                                                                                 \
+  } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Modified Bessel functions by their power series (all terms positive).
+double bessel_i0(double z) {
+  const double q = 0.25 * z * z;
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 500; ++k) {
+    term *= q / (double(k) * double(k));
+    sum += term;
+    if (term < 1e-17 * sum) break;
+  }
+  return sum;
+}
+double bessel_i1(double z) {
+  const double q = 0.25 * z * z;
+  double term = 0.5 * z, sum = term;
+  for (int k = 1; k < 500; ++k) {
+    term *= q / (double(k) * double(k + 1));
+    sum += term;
+    if (std::fabs(term) < 1e-17 * std::fabs(sum)) break;
+  }
+  return sum;
+}
+
+// Kaiser-Bessel window of w taps for oversampling sigma, normalised so that
+// phi(0) = 1; phihat is its continuous Fourier transform (same normalisation).
+struct Kb {
+  int w;
+  double beta, phi0;
+  Kb(int w_, int sigma) : w(w_) {
+    const double a = double(w_) / sigma * (sigma - 0.5);
+    beta = kPi * std::sqrt(a * a - 0.8);
+    phi0 = bessel_i0(beta);
+  }
+  double phi(double x) const {
+    const double t = 1.0 - (2.0 * x / w) * (2.0 * x / w);
+    if (t < 0.0) return 0.0;
+    return bessel_i0(beta * std::sqrt(t)) / phi0;
+  }
+  double dphi(double x) const {
+    const double t = 1.0 - (2.0 * x / w) * (2.0 * x / w);
+    if (t <= 0.0) return 0.0;
+    const double s = std::sqrt(t);
+    return bessel_i1(beta * s) * beta * (-4.0 * x / (double(w) * w)) / s / phi0;
+  }
+  double phihat(double xi) const {
+    const double a = kPi * w * xi;
+    const double s = beta * beta - a * a;
+    const double r = std::sqrt(std::fabs(s));
+    double v;
+    if (s > 1e-300)
+      v = w * std::sinh(r) / r;
+    else if (s < -1e-300)
+      v = w * std::sin(r) / r;
+    else
+      v = w;
+    return v / phi0;
+  }
+};
+
+bool smooth7(long n) {
+  if (n < 1) return false;
+  for (int p : {2, 3, 5, 7})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+int ipt_of(int r) { return r >= 16 ? 1 : (r >= 5 ? 2 : 4); }
+
+// Radix schedule of an in-place Stockham FFT; every stage must fit in one
+// round per sequence for `nthr` threads.
+bool make_fft_plan(int L, int nthr, FftPlan &fp) {
+  std::memset(&fp, 0, sizeof(fp));
+  fp.L = L;
+  int rem = L;
+  const int order[] = {16, 8, 4, 2, 3, 5, 7};
+  while (rem > 1) {
+    bool found = false;
+    for (int r : order) {
+      if (rem % r == 0) {
+        if (fp.nst >= pa::kMaxStages) return false;
+        fp.radix[fp.nst++] = r;
+        rem /= r;
+        found = true;
+        break;
+      }
+    }
+    if (!found) return false;
+  }
+  for (int s = 0; s < fp.nst; ++s)
+    if (L / fp.radix[s] > nthr * ipt_of(fp.radix[s])) return false;
+  return true;
+}
+
+void split_ff(double v, float &hi, float &lo) {
+  hi = float(v);
+  lo = float(v - double(hi));
+}
+
+int horner_degree(int w) { return w <= 6 ? 7 : (w <= 8 ? 8 : (w <= 12 ? 10 : 14)); }
+
+// Monomial coefficients in s = 2 fr - 1 of the Chebyshev interpolant of
+// degree D of phi(fr + w/2 - 1 - t), fr in [0, 1].
+void fit_horner(const Kb &kb, int D, HornerTable &ht) {
+  std::memset(&ht, 0, sizeof(ht));
+  const int w = kb.w;
+  std::vector<double> nodes(D + 1), vals(D + 1);
+  for (int t = 0; t < w; ++t) {
+    for (int k = 0; k <= D; ++k) {
+      nodes[k] = std::cos(kPi * (k + 0.5) / (D + 1));
+      const double fr = 0.5 * (nodes[k] + 1.0);
+      vals[k] = kb.phi(fr + 0.5 * w - 1.0 - t);
+    }
+    // Chebyshev coefficients a_j
+    std::vector<double> a(D + 1, 0.0);
+    for (int j = 0; j <= D; ++j) {
+      double s = 0.0;
+      for (int k = 0; k <= D; ++k) s += vals[k] * std::cos(j * kPi * (k + 0.5) / (D + 1));
+      a[j] = 2.0 * s / (D + 1);
+    }
+    a[0] *= 0.5;
+    // sum_j a_j T_j(s) -> monomials, with T_{j+1} = 2 s T_j - T_{j-1}
+    std::vector<double> Tm(D + 1, 0.0), T0(D + 1, 0.0), T1(D + 1, 0.0), out(D + 1, 0.0);
+    T0[0] = 1.0;
+    if (D >= 1) T1[1] = 1.0;
+    for (int k = 0; k <= D; ++k) out[k] += a[0] * T0[k];
+    if (D >= 1)
+      for (int k = 0; k <= D; ++k) out[k] += a[1] * T1[k];
+    for (int j = 2; j <= D; ++j) {
+      std::vector<double> T2(D + 1, 0.0);
+      for (int k = 0; k <= D; ++k) {
+        if (k >= 1) T2[k] += 2.0 * T1[k - 1];
+        T2[k] -= T0[k];
+      }
+      for (int k = 0; k <= D; ++k) out[k] += a[j] * T2[k];
+      T0 = T1;
+      T1 = T2;
+    }
+    for (int k = 0; k <= D; ++k) ht.c[t][k] = float(out[k]);
+  }
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct pa_plan {
+  int device = 0;
+  int64_t M = 0, Nt = 0;
+  double dt = 0, c = 0;
+  pa_grid grid{};
+  int sigma = 2, w = 8;
+  InstDesc h{};
+  InstDesc *d_desc = nullptr;
+  HornerTable ht{};
+  char *d_static = nullptr;
+  char *d_work = nullptr;
+  size_t static_bytes = 0, work_bytes = 0;
+  std::vector<double> weights;  // h_m
+  int spread_threads = 256;
+  size_t smem_limit = 0;
+  // optional per-stage event timing
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+};
+
+struct pa_batch {
+  std::vector<pa_plan *> plans;
+  InstDesc *d_descs = nullptr;
+  IoPtrs *d_io = nullptr;
+  int2 *d_work = nullptr;
+  struct Stage {
+    size_t off = 0;
+    int nblocks = 0;
+    size_t smem = 0;
+  } st_spread, st_col, st_ner, st_imgx, st_imgy;
+  int spread_threads = 256;
+  HornerTable ht{};
+  int width = 8;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+};
+
+namespace {
+
+// Sensor geometry: grid coordinates, window taps, binning; uploads into the
+// plan's static buffers.
+int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
+  const int M = int(P->M), w = P->w;
+  const int Mx = P->h.Mx, My = P->h.My;
+  const double X = P->grid.nx * P->grid.dx, Y = P->grid.ny * P->grid.dy;
+  const Kb kb(w, P->sigma);
+  std::vector<int> bx(M), by(M);
+  std::vector<double> frx(M), fry(M);
+  for (int m = 0; m < M; ++m) {
+    const double x = xy[2 * m], y = xy[2 * m + 1];
+    if (!std::isfinite(x) || !std::isfinite(y)) return fail(PA_ERR_INVALID_ARG, "non-finite sensor position");
+    double ux = x / X, uy = y / Y;
+    ux -= std::floor(ux + 0.5);
+    uy -= std::floor(uy + 0.5);
+    const double Ux = Mx * ux, Uy = My * uy;
+    const double fbx = std::floor(Ux), fby = std::floor(Uy);
+    frx[m] = Ux - fbx;
+    fry[m] = Uy - fby;
+    bx[m] = ((int(fbx) % Mx) + Mx) % Mx;
+    by[m] = ((int(fby) % My) + My) % My;
+  }
+  // counting sort by cell
+  const size_t ncell = size_t(Mx) * My;
+  std::vector<int> cs(ncell + 1, 0), perm(M);
+  for (int m = 0; m < M; ++m) cs[size_t(bx[m]) * My + by[m] + 1]++;
+  for (size_t k = 0; k < ncell; ++k) cs[k + 1] += cs[k];
+  {
+    std::vector<int> fill(cs.begin(), cs.end() - 1);
+    for (int m = 0; m < M; ++m) perm[fill[size_t(bx[m]) * My + by[m]]++] = m;
+  }
+  std::vector<int> sbx(M), sby(M);
+  std::vector<float> wx(size_t(M) * w), wy(size_t(M) * w), dwx(size_t(M) * w), dwy(size_t(M) * w);
+  const double ax = 1.0 / (P->grid.dx * P->grid.dy);
+  for (int i = 0; i < M; ++i) {
+    const int m = perm[i];
+    sbx[i] = bx[m];
+    sby[i] = by[m];
+    const double a = P->weights[m] * ax;
+    for (int t = 0; t < w; ++t) {
+      const double ddx = frx[m] + 0.5 * w - 1.0 - t;
+      const double ddy = fry[m] + 0.5 * w - 1.0 - t;
+      wx[size_t(i) * w + t] = float(kb.phi(ddx));
+      wy[size_t(i) * w + t] = float(a * kb.phi(ddy));
+      dwx[size_t(i) * w + t] = float(kb.dphi(ddx) * Mx / X);
+      dwy[size_t(i) * w + t] = float(a * kb.dphi(ddy) * My / Y);
+    }
+  }
+  PA_CUDA(cudaMemcpyAsync((void *)P->h.perm, perm.data(), sizeof(int) * M, cudaMemcpyHostToDevice, stream));
+  PA_CUDA(cudaMemcpyAsync((void *)P->h.sbx, sbx.data(), sizeof(int) * M, cudaMemcpyHostToDevice, stream));
+  PA_CUDA(cudaMemcpyAsync((void *)P->h.sby, sby.data(), sizeof(int) * M, cudaMemcpyHostToDevice, stream));
+  PA_CUDA(cudaMemcpyAsync((void *)P->h.wx, wx.data(), sizeof(float) * wx.size(), cudaMemcpyHostToDevice, stream));
+  PA_CUDA(cudaMemcpyAsync((void *)P->h.wy, wy.data(), sizeof(float) * wy.size(), cudaMemcpyHostToDevice, stream));
+  PA_CUDA(cudaMemcpyAsync((void *)P->h.dwx, dwx.data(), sizeof(float) * dwx.size(), cudaMemcpyHostToDevice, stream));
+  PA_CUDA(cudaMemcpyAsync((void *)P->h.dwy, dwy.data(), sizeof(float) * dwy.size(), cudaMemcpyHostToDevice, stream));
+  PA_CUDA(cudaMemcpyAsync((void *)P->h.cell_start, cs.data(), sizeof(int) * cs.size(), cudaMemcpyHostToDevice,
+                          stream));
+  // pageable sources: the copies above are complete when they return
+  return PA_OK;
+}
+
+void free_plan(pa_plan *P) {
+  if (!P) return;
+  for (auto &u : P->ev_used) {
+    cudaEventDestroy(u.second.first);
+    cudaEventDestroy(u.second.second);
+  }
+  for (auto e : P->ev_pool) cudaEventDestroy(e);
+  cudaFree(P->d_desc);
+  cudaFree(P->d_static);
+  cudaFree(P->d_work);
+  delete P;
+}
+
+pa::Launch make_launch(const pa_plan *P, cudaStream_t s) {
+  pa::Launch L{};
+  L.descs = P->d_desc;
+  L.work = nullptr;
+  L.io_table = nullptr;
+  L.stream = s;
+  return L;
+}
+
+int check_launch(cudaError_t e, const char *what) {
+  if (e != cudaSuccess) return fail(PA_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return PA_OK;
+}
+
+const char *const kStageNames[PA_PROFILE_STAGES] = {
+    "ned_spread_rowfft", "ned_colfft", "ner_fused", "image_x", "image_y_c2r", "image_y_adj",
+    "image_x_adj", "ner_adj", "ned_colfft_adj", "ned_rowifft_interp", "grad_reduce", "cubic_baseline"};
+
+cudaEvent_t take_event(pa_plan *P) {
+  if (!P->ev_pool.empty()) {
+    cudaEvent_t e = P->ev_pool.back();
+    P->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Launch `fn` on stream s; with profiling on, bracket it with events.
+template <typename Fn>
+int timed(pa_plan *P, int stage, cudaStream_t s, Fn fn, const char *what) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (P->profiling) {
+    e0 = take_event(P);
+    e1 = take_event(P);
+    if (e0) cudaEventRecord(e0, s);
+  }
+  int rc = check_launch(fn(), what);
+  if (P->profiling && e0 && e1) {
+    cudaEventRecord(e1, s);
+    P->ev_used.push_back({stage, {e0, e1}});
+  }
+  return rc;
+}
+
+int run_forward(pa_plan *P, const IoPtrs &io, cudaStream_t s, bool cubic) {
+  pa::Launch L = make_launch(P, s);
+  L.io = io;
+  const InstDesc &h = P->h;
+  int rc;
+  L.nblocks = pa::blocks_spread(h);
+  L.smem = pa::smem_spread(h);
+  if ((rc = timed(P, 0, s, [&] { return pa::launch_spread(L, P->spread_threads); }, "spread")) != PA_OK) return rc;
+  L.nblocks = pa::blocks_colfft(h);
+  L.smem = pa::smem_colfft(h);
+  if ((rc = timed(P, 1, s, [&] { return pa::launch_colfft(L, false); }, "colfft")) != PA_OK) return rc;
+  L.nblocks = pa::blocks_ner(h);
+  L.smem = pa::smem_ner(h);
+  if (cubic) {
+    if ((rc = timed(P, 11, s, [&] { return pa::launch_cubic(L); }, "cubic")) != PA_OK) return rc;
+  } else {
+    if ((rc = timed(P, 2, s, [&] { return pa::launch_ner(L, P->w, P->ht, false); }, "ner")) != PA_OK) return rc;
+  }
+  L.nblocks = pa::blocks_imgx(h);
+  L.smem = pa::smem_imgx(h);
+  if ((rc = timed(P, 3, s, [&] { return pa::launch_imgx(L, false); }, "imgx")) != PA_OK) return rc;
+  L.nblocks = pa::blocks_imgy(h);
+  L.smem = pa::smem_imgy(h);
+  if ((rc = timed(P, 4, s, [&] { return pa::launch_imgy(L, false); }, "imgy")) != PA_OK) return rc;
+  return PA_OK;
+}
+
+int run_adjoint(pa_plan *P, const IoPtrs &io, cudaStream_t s, bool grad) {
+  pa::Launch L = make_launch(P, s);
+  L.io = io;
+  const InstDesc &h = P->h;
+  int rc;
+  L.nblocks = pa::blocks_imgy(h);
+  L.smem = pa::smem_imgy(h);
+  if ((rc = timed(P, 5, s, [&] { return pa::launch_imgy(L, true); }, "imgy_adj")) != PA_OK) return rc;
+  L.nblocks = pa::blocks_imgx(h);
+  L.smem = pa::smem_imgx(h);
+  if ((rc = timed(P, 6, s, [&] { return pa::launch_imgx(L, true); }, "imgx_adj")) != PA_OK) return rc;
+  L.nblocks = pa::blocks_ner_adj(h);
+  L.smem = pa::smem_ner_adj(h);
+  if ((rc = timed(P, 7, s, [&] { return pa::launch_ner(L, P->w, P->ht, true); }, "ner_adj")) != PA_OK) return rc;
+  L.nblocks = pa::blocks_colfft(h);
+  L.smem = pa::smem_colfft(h);
+  if ((rc = timed(P, 8, s, [&] { return pa::launch_colfft(L, true); }, "colfft_adj")) != PA_OK) return rc;
+  L.nblocks = pa::blocks_interp(h);
+  L.smem = pa::smem_interp(h);
+  if ((rc = timed(P, 9, s, [&] { return pa::launch_interp_width(L, P->w, grad); }, "interp")) != PA_OK) return rc;
+  if (grad) {
+    L.nblocks = std::min(1024, int((P->M + 255) / 256));
+    if ((rc = timed(P, 10, s, [&] { return pa::launch_grad_reduce(L, 1); }, "grad_reduce")) != PA_OK) return rc;
+  }
+  return PA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pa_last_error(void) { return g_err.c_str(); }
+
+const char *pa_version(void) { return "pa_nufft 0.1 (sm_103a)"; }
+
+int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, const double *weights, int64_t n_t,
+                   double dt, double c, const pa_grid *grid, int sigma, int width, int flags, void *stream) {
+  g_err.clear();
+  if (!out) return fail(PA_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!sensor_xy || !grid) return fail(PA_ERR_INVALID_ARG, "sensor_xy or grid is NULL");
+  if (n_sensors < 1 || n_sensors > (int64_t(1) << 30)) return fail(PA_ERR_INVALID_ARG, "n_sensors out of range");
+  if (n_t < 2 || n_t > 4096) return fail(PA_ERR_INVALID_ARG, "n_t out of range [2, 4096]");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(PA_ERR_INVALID_ARG, "dt must be finite and > 0");
+  if (!(c > 0) || !std::isfinite(c)) return fail(PA_ERR_INVALID_ARG, "c must be finite and > 0");
+  if (grid->nx < 2 || grid->ny < 2 || grid->nz < 2) return fail(PA_ERR_INVALID_ARG, "grid sizes must be >= 2");
+  if (!(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0) || !std::isfinite(grid->dx) ||
+      !std::isfinite(grid->dy) || !std::isfinite(grid->dz))
+    return fail(PA_ERR_INVALID_ARG, "grid spacings must be finite and > 0");
+  if (sigma < 2 || sigma > 4) return fail(PA_ERR_INVALID_ARG, "sigma must be 2, 3 or 4");
+  if (!(width == 6 || width == 8 || width == 12 || width == 16))
+    return fail(PA_ERR_INVALID_ARG, "width must be 6, 8, 12 or 16");
+  if (flags != PA_FLAG_DEFAULT) return fail(PA_ERR_INVALID_ARG, "unknown flags");
+  for (int64_t m = 0; m < 2 * n_sensors; ++m)
+    if (!std::isfinite(sensor_xy[m])) return fail(PA_ERR_INVALID_ARG, "non-finite sensor position");
+  const double X = grid->nx * grid->dx, Y = grid->ny * grid->dy;
+  if (weights) {
+    for (int64_t m = 0; m < n_sensors; ++m)
+      if (!(weights[m] > 0) || !std::isfinite(weights[m]))
+        return fail(PA_ERR_INVALID_ARG, "weights must be finite and > 0");
+  }
+  const long Nx = grid->nx, Ny = grid->ny, Nz = grid->nz, Nt = n_t;
+  const long Mx = sigma * Nx, My = sigma * Ny, Mt = sigma * Nt;
+  for (long L : {Nx, Ny, Nz, Nt, Mx, My, Mt})
+    if (!smooth7(L)) return fail(PA_ERR_UNSUPPORTED_SIZE, "a transform length is not a product of 2, 3, 5, 7");
+  if (Mx > 4096 || My > 512 || Nz > 4096 || Nx > 4096 || Ny > 4096 || Mt > 4096)
+    return fail(PA_ERR_UNSUPPORTED_SIZE, "a transform length exceeds the supported maximum");
+  if (Mx < 2 * width || My < 2 * width) return fail(PA_ERR_UNSUPPORTED_SIZE, "sigma*nx and sigma*ny must be >= 2*width");
+
+  pa_plan *P = new pa_plan();
+  P->M = n_sensors;
+  P->Nt = n_t;
+  P->dt = dt;
+  P->c = c;
+  P->grid = *grid;
+  P->sigma = sigma;
+  P->w = width;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t ce = cudaGetDevice(&P->device);
+  if (ce != cudaSuccess) {
+    delete P;
+    return fail(PA_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce));
+  }
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+  P->smem_limit = size_t(smem_optin);
+  P->weights.resize(n_sensors);
+  for (int64_t m = 0; m < n_sensors; ++m) P->weights[m] = weights ? weights[m] : X * Y / double(n_sensors);
+
+  InstDesc &h = P->h;
+  std::memset(&h, 0, sizeof(h));
+  h.M = int(n_sensors);
+  h.Nt = int(Nt);
+  h.Nx = int(Nx);
+  h.Ny = int(Ny);
+  h.Nz = int(Nz);
+  h.Mx = int(Mx);
+  h.My = int(My);
+  h.Mt = int(Mt);
+  h.w = width;
+  h.hx = int(Nx / 2);
+  h.hy = int(Ny / 2);
+  h.hz = int(Nz / 2);
+  h.nc = int(Nt / 2);
+  h.nX1 = 2 * h.hx + 1;
+  h.nY1 = h.hy + 1;
+  h.nchunk_adj = int((Nt + 2 * pa::kAdjNCP - 1) / (2 * pa::kAdjNCP));
+  h.sigma = sigma;
+  P->spread_threads = pa::threads_spread(h);
+
+  // FFT schedules and twiddles
+  struct Len {
+    FftPlan *fp;
+    int L;
+    int nthr;
+  } lens[] = {{&h.fMy, int(My), P->spread_threads < 256 ? P->spread_threads : 256},
+              {&h.fMx, int(Mx), 256},
+              {&h.fMt, int(Mt), 256},
+              {&h.fNz, int(Nz), 256},
+              {&h.fNx, int(Nx), 256},
+              {&h.fNy, int(Ny), 256},
+              {&h.fNt, int(Nt), 256}};
+  std::vector<float2> tw;
+  for (auto &ln : lens) {
+    if (!make_fft_plan(ln.L, ln.nthr, *ln.fp)) {
+      delete P;
+      return fail(PA_ERR_UNSUPPORTED_SIZE, "no in-place FFT schedule for length " + std::to_string(ln.L));
+    }
+    ln.fp->tw = int(tw.size());
+    for (int m = 0; m < ln.L; ++m) {
+      const double a = -2.0 * kPi * double(m) / ln.L;
+      tw.push_back(make_float2(float(std::cos(a)), float(std::sin(a))));
+    }
+  }
+  // deconvolution tables and time-frequency constants
+  const Kb kb(width, sigma);
+  std::vector<float> ipx(h.nX1), ipy(h.nY1), ipt(Nt);
+  for (int ix = 0; ix < h.nX1; ++ix) ipx[ix] = float(1.0 / kb.phihat(double(ix - h.hx) / Mx));
+  for (int iy = 0; iy < h.nY1; ++iy) ipy[iy] = float(1.0 / kb.phihat(double(iy) / My));
+  for (long n = 0; n < Nt; ++n) ipt[n] = float(1.0 / kb.phihat(double(n - h.nc) / Mt));
+  const double Z = Nz * grid->dz;
+  const double cT = c * Nt * dt;
+  split_ff((cT / X) * (cT / X), h.ax_hi, h.ax_lo);
+  split_ff((cT / Y) * (cT / Y), h.ay_hi, h.ay_lo);
+  split_ff((cT / Z) * (cT / Z), h.az_hi, h.az_lo);
+  split_ff(double(h.nc) / double(Nt), h.ph_hi, h.ph_lo);
+  h.sqrt_az = float(cT / Z);
+  h.two_c = float(2.0 * c);
+  h.scale = float(dt / (grid->dz * double(Nx) * double(Ny) * double(Nz)));
+  fit_horner(kb, horner_degree(width), P->ht);
+
+  // shared-memory limits
+  const size_t smems[] = {pa::smem_spread(h), pa::smem_colfft(h), pa::smem_ner(h), pa::smem_ner_adj(h),
+                          pa::smem_imgx(h), pa::smem_imgy(h), pa::smem_interp(h)};
+  for (size_t sm : smems)
+    if (sm > P->smem_limit) {
+      delete P;
+      return fail(PA_ERR_UNSUPPORTED_SIZE, "problem needs more shared memory per block than the device has");
+    }
+
+  // static device memory
+  const size_t M = size_t(n_sensors), W = size_t(width);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  const size_t o_perm = take(sizeof(int) * M), o_sbx = take(sizeof(int) * M), o_sby = take(sizeof(int) * M);
+  const size_t o_wx = take(sizeof(float) * M * W), o_wy = take(sizeof(float) * M * W);
+  const size_t o_dwx = take(sizeof(float) * M * W), o_dwy = take(sizeof(float) * M * W);
+  const size_t o_cs = take(sizeof(int) * (size_t(Mx) * My + 1));
+  const size_t o_ipx = take(sizeof(float) * ipx.size()), o_ipy = take(sizeof(float) * ipy.size());
+  const size_t o_ipt = take(sizeof(float) * ipt.size());
+  const size_t o_tw = take(sizeof(float2) * tw.size());
+  const size_t o_status = take(sizeof(int));
+  P->static_bytes = off;
+  // workspace
+  off = 0;
+  const size_t nG1 = size_t(h.nX1) * h.nY1 * Nt;
+  const size_t nT = size_t(Mx) * h.nY1 * Nt;
+  const size_t nF = size_t(Nx) * h.nY1 * Nz;
+  const size_t o_G1 = take(sizeof(float2) * nG1);
+  const size_t o_reg = take(sizeof(float2) * std::max(nT, 2 * nF));
+  const size_t o_gp = take(sizeof(float2) * size_t(h.nchunk_adj) * M);
+  P->work_bytes = off;
+
+  ce = cudaMalloc(&P->d_static, P->static_bytes);
+  if (ce == cudaSuccess) ce = cudaMalloc(&P->d_work, P->work_bytes);
+  if (ce == cudaSuccess) ce = cudaMalloc(&P->d_desc, sizeof(InstDesc));
+  if (ce != cudaSuccess) {
+    free_plan(P);
+    return fail(ce == cudaErrorMemoryAllocation ? PA_ERR_OOM : PA_ERR_CUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(ce));
+  }
+  char *S = P->d_static;
+  char *Wk = P->d_work;
+  h.perm = reinterpret_cast<const int *>(S + o_perm);
+  h.sbx = reinterpret_cast<const int *>(S + o_sbx);
+  h.sby = reinterpret_cast<const int *>(S + o_sby);
+  h.wx = reinterpret_cast<const float *>(S + o_wx);
+  h.wy = reinterpret_cast<const float *>(S + o_wy);
+  h.dwx = reinterpret_cast<const float *>(S + o_dwx);
+  h.dwy = reinterpret_cast<const float *>(S + o_dwy);
+  h.cell_start = reinterpret_cast<const int *>(S + o_cs);
+  h.invphx = reinterpret_cast<const float *>(S + o_ipx);
+  h.invphy = reinterpret_cast<const float *>(S + o_ipy);
+  h.invpht = reinterpret_cast<const float *>(S + o_ipt);
+  h.tw = reinterpret_cast<const float2 *>(S + o_tw);
+  h.status = reinterpret_cast<int *>(S + o_status);
+  h.G1 = reinterpret_cast<float2 *>(Wk + o_G1);
+  h.T = reinterpret_cast<float2 *>(Wk + o_reg);
+  h.Fz = reinterpret_cast<float2 *>(Wk + o_reg);
+  h.U = h.Fz + nF;
+  h.grad_part = reinterpret_cast<float2 *>(Wk + o_gp);
+
+  int rc = upload_sensors(P, sensor_xy, s);
+  if (rc != PA_OK) {
+    free_plan(P);
+    return rc;
+  }
+  auto up = [&](const void *dst, const void *src, size_t bytes) {
+    return cudaMemcpyAsync(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice, s);
+  };
+  ce = up(h.invphx, ipx.data(), sizeof(float) * ipx.size());
+  if (ce == cudaSuccess) ce = up(h.invphy, ipy.data(), sizeof(float) * ipy.size());
+  if (ce == cudaSuccess) ce = up(h.invpht, ipt.data(), sizeof(float) * ipt.size());
+  if (ce == cudaSuccess) ce = up(h.tw, tw.data(), sizeof(float2) * tw.size());
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h.status, 0, sizeof(int), s);
+  if (ce == cudaSuccess) ce = up(P->d_desc, &h, sizeof(InstDesc));
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) {
+    free_plan(P);
+    return fail(PA_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(ce));
+  }
+  *out = P;
+  return PA_OK;
+}
+
+int pa_plan_update_positions(pa_plan *plan, const double *sensor_xy, void *stream) {
+  g_err.clear();
+  if (!plan || !sensor_xy) return fail(PA_ERR_INVALID_ARG, "plan or sensor_xy is NULL");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  return upload_sensors(plan, sensor_xy, s);
+}
+
+int pa_reconstruct(pa_plan *plan, const float *g_dev, float *f_dev, void *stream) {
+  g_err.clear();
+  if (!plan || !g_dev || !f_dev) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  IoPtrs io{};
+  io.g_in = g_dev;
+  io.f_out = f_dev;
+  return run_forward(plan, io, reinterpret_cast<cudaStream_t>(stream), false);
+}
+
+int pa_reconstruct_cubic(pa_plan *plan, const float *g_dev, float *f_dev, void *stream) {
+  g_err.clear();
+  if (!plan || !g_dev || !f_dev) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  IoPtrs io{};
+  io.g_in = g_dev;
+  io.f_out = f_dev;
+  return run_forward(plan, io, reinterpret_cast<cudaStream_t>(stream), true);
+}
+
+int pa_reconstruct_adjoint(pa_plan *plan, const float *f_dev, float *g_dev, void *stream) {
+  g_err.clear();
+  if (!plan || !g_dev || !f_dev) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  IoPtrs io{};
+  io.f_in = f_dev;
+  io.g_out = g_dev;
+  return run_adjoint(plan, io, reinterpret_cast<cudaStream_t>(stream), false);
+}
+
+int pa_position_grad(pa_plan *plan, const float *g_dev, const float *grad_f_dev, float *grad_g_dev,
+                     float *grad_xy_dev, void *stream) {
+  g_err.clear();
+  if (!plan || !g_dev || !grad_f_dev || !grad_xy_dev) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  IoPtrs io{};
+  io.g_in = g_dev;
+  io.f_in = grad_f_dev;
+  io.g_out = grad_g_dev;
+  io.grad_xy = grad_xy_dev;
+  return run_adjoint(plan, io, reinterpret_cast<cudaStream_t>(stream), true);
+}
+
+int pa_profile_enable(pa_plan *plan, int enable) {
+  g_err.clear();
+  if (!plan) return fail(PA_ERR_INVALID_ARG, "plan is NULL");
+  plan->profiling = enable != 0;
+  return PA_OK;
+}
+
+int pa_profile_read(pa_plan *plan, double *ms_total, int64_t *launches) {
+  g_err.clear();
+  if (!plan || !ms_total || !launches) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  for (int k = 0; k < PA_PROFILE_STAGES; ++k) {
+    ms_total[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (auto &u : plan->ev_used) {
+    PA_CUDA(cudaEventSynchronize(u.second.second));
+    float ms = 0.f;
+    PA_CUDA(cudaEventElapsedTime(&ms, u.second.first, u.second.second));
+    ms_total[u.first] += ms;
+    launches[u.first] += 1;
+    plan->ev_pool.push_back(u.second.first);
+    plan->ev_pool.push_back(u.second.second);
+  }
+  plan->ev_used.clear();
+  return PA_OK;
+}
+
+const char *pa_profile_stage_name(int stage) {
+  if (stage < 0 || stage >= PA_PROFILE_STAGES) return "";
+  return kStageNames[stage];
+}
+
+int pa_plan_destroy(pa_plan *plan) {
+  g_err.clear();
+  if (!plan) return PA_OK;
+  cudaDeviceSynchronize();
+  free_plan(plan);
+  return PA_OK;
+}
+
+int pa_status(pa_plan *plan, int *device_status, void *stream) {
+  g_err.clear();
+  if (!plan || !device_status) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int v = 0;
+  PA_CUDA(cudaMemcpyAsync(&v, plan->h.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PA_CUDA(cudaStreamSynchronize(s));
+  PA_CUDA(cudaMemsetAsync(plan->h.status, 0, sizeof(int), s));
+  *device_status = v;
+  return v ? fail(PA_ERR_DEVICE, "a kernel recorded an error") : PA_OK;
+}
+
+int pa_plan_info(const pa_plan *plan, int64_t *n_sensors, int64_t *n_t, int64_t *workspace_bytes) {
+  g_err.clear();
+  if (!plan) return fail(PA_ERR_INVALID_ARG, "plan is NULL");
+  if (n_sensors) *n_sensors = plan->M;
+  if (n_t) *n_t = plan->Nt;
+  if (workspace_bytes) *workspace_bytes = int64_t(plan->work_bytes + plan->static_bytes);
+  return PA_OK;
+}
+
+int pa_plan_buffer(const pa_plan *plan, int which, void *dst_dev, int64_t capacity_bytes, int64_t *bytes,
+                   void *stream) {
+  g_err.clear();
+  if (!plan || !bytes) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  const InstDesc &h = plan->h;
+  const void *src;
+  int64_t n;
+  if (which == 0) {
+    src = h.G1;
+    n = int64_t(sizeof(float2)) * h.nX1 * h.nY1 * h.Nt;
+  } else if (which == 1) {
+    src = h.Fz;
+    n = int64_t(sizeof(float2)) * h.Nx * h.nY1 * h.Nz;
+  } else {
+    return fail(PA_ERR_INVALID_ARG, "unknown buffer");
+  }
+  *bytes = n;
+  if (!dst_dev) return PA_OK;
+  if (capacity_bytes < n) return fail(PA_ERR_INVALID_ARG, "destination buffer too small");
+  PA_CUDA(cudaMemcpyAsync(dst_dev, src, size_t(n), cudaMemcpyDeviceToDevice, reinterpret_cast<cudaStream_t>(stream)));
+  return PA_OK;
+}
+
+// ------------------------------------------------------------------ batch
+int pa_batch_create(pa_batch **out, int n, pa_plan *const *plans, void *stream) {
+  g_err.clear();
+  if (!out || !plans || n < 1) return fail(PA_ERR_INVALID_ARG, "bad batch arguments");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i]) return fail(PA_ERR_INVALID_ARG, "NULL plan in batch");
+    if (plans[i]->w != plans[0]->w || plans[i]->sigma != plans[0]->sigma)
+      return fail(PA_ERR_INVALID_ARG, "all plans of a batch need the same sigma and width");
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  pa_batch *B = new pa_batch();
+  B->plans.assign(plans, plans + n);
+  B->width = plans[0]->w;
+  B->ht = plans[0]->ht;
+  std::vector<InstDesc> descs(n);
+  for (int i = 0; i < n; ++i) descs[i] = plans[i]->h;
+  std::vector<int2> work;
+  auto add_stage = [&](pa_batch::Stage &st, int (*nb)(const InstDesc &), size_t (*sm)(const InstDesc &)) {
+    st.off = work.size();
+    st.smem = 0;
+    for (int i = 0; i < n; ++i) {
+      const int cnt = nb(descs[i]);
+      for (int t = 0; t < cnt; ++t) work.push_back(make_int2(i, t));
+      st.smem = std::max(st.smem, sm(descs[i]));
+    }
+    st.nblocks = int(work.size() - st.off);
+  };
+  add_stage(B->st_spread, pa::blocks_spread, pa::smem_spread);
+  add_stage(B->st_col, pa::blocks_colfft, pa::smem_colfft);
+  add_stage(B->st_ner, pa::blocks_ner, pa::smem_ner);
+  add_stage(B->st_imgx, pa::blocks_imgx, pa::smem_imgx);
+  add_stage(B->st_imgy, pa::blocks_imgy, pa::smem_imgy);
+  for (int i = 0; i < n; ++i) B->spread_threads = std::max(B->spread_threads, plans[i]->spread_threads);
+  cudaError_t ce = cudaMalloc(&B->d_descs, sizeof(InstDesc) * n);
+  if (ce == cudaSuccess) ce = cudaMalloc(&B->d_io, sizeof(IoPtrs) * n);
+  if (ce == cudaSuccess) ce = cudaMalloc(&B->d_work, sizeof(int2) * work.size());
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(B->d_descs, descs.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(B->d_work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) {
+    cudaFree(B->d_descs);
+    cudaFree(B->d_io);
+    cudaFree(B->d_work);
+    delete B;
+    return fail(ce == cudaErrorMemoryAllocation ? PA_ERR_OOM : PA_ERR_CUDA,
+                std::string("batch setup: ") + cudaGetErrorString(ce));
+  }
+  *out = B;
+  return PA_OK;
+}
+
+static int batch_launches(pa_batch *B, cudaStream_t s) {
+  pa::Launch L{};
+  L.descs = B->d_descs;
+  L.io_table = B->d_io;
+  L.stream = s;
+  int rc;
+  L.work = B->d_work + B->st_spread.off;
+  L.nblocks = B->st_spread.nblocks;
+  L.smem = B->st_spread.smem;
+  if ((rc = check_launch(pa::launch_spread(L, B->spread_threads), "batch spread")) != PA_OK) return rc;
+  L.work = B->d_work + B->st_col.off;
+  L.nblocks = B->st_col.nblocks;
+  L.smem = B->st_col.smem;
+  if ((rc = check_launch(pa::launch_colfft(L, false), "batch colfft")) != PA_OK) return rc;
+  L.work = B->d_work + B->st_ner.off;
+  L.nblocks = B->st_ner.nblocks;
+  L.smem = B->st_ner.smem;
+  if ((rc = check_launch(pa::launch_ner(L, B->width, B->ht, false), "batch ner")) != PA_OK) return rc;
+  L.work = B->d_work + B->st_imgx.off;
+  L.nblocks = B->st_imgx.nblocks;
+  L.smem = B->st_imgx.smem;
+  if ((rc = check_launch(pa::launch_imgx(L, false), "batch imgx")) != PA_OK) return rc;
+  L.work = B->d_work + B->st_imgy.off;
+  L.nblocks = B->st_imgy.nblocks;
+  L.smem = B->st_imgy.smem;
+  if ((rc = check_launch(pa::launch_imgy(L, false), "batch imgy")) != PA_OK) return rc;
+  return PA_OK;
+}
+
+int pa_batch_run(pa_batch *B, const float *const *g_dev, float *const *f_dev, void *stream) {
+  g_err.clear();
+  if (!B || !g_dev || !f_dev) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int n = int(B->plans.size());
+  std::vector<IoPtrs> io(n);
+  for (int i = 0; i < n; ++i) {
+    if (!g_dev[i] || !f_dev[i]) return fail(PA_ERR_INVALID_ARG, "NULL buffer in batch");
+    io[i] = IoPtrs{};
+    io[i].g_in = g_dev[i];
+    io[i].f_out = f_dev[i];
+  }
+  // pageable source: the copy has consumed `io` when the call returns
+  PA_CUDA(cudaMemcpyAsync(B->d_io, io.data(), sizeof(IoPtrs) * n, cudaMemcpyHostToDevice, s));
+  if (!B->exec) {
+    // kernel attributes are set outside the capture by a first direct run
+    int rc = batch_launches(B, s);
+    if (rc != PA_OK) return rc;
+    cudaStream_t cap;
+    PA_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+      rc = batch_launches(B, cap);
+      ce = cudaStreamEndCapture(cap, &B->graph);
+    }
+    cudaStreamDestroy(cap);
+    if (ce != cudaSuccess || rc != PA_OK)
+      return rc != PA_OK ? rc : fail(PA_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    PA_CUDA(cudaGraphInstantiate(&B->exec, B->graph, 0));
+    return PA_OK;
+  }
+  PA_CUDA(cudaGraphLaunch(B->exec, s));
+  return PA_OK;
+}
+
+int pa_batch_destroy(pa_batch *B) {
+  g_err.clear();
+  if (!B) return PA_OK;
+  cudaDeviceSynchronize();
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  cudaFree(B->d_descs);
+  cudaFree(B->d_io);
+  cudaFree(B->d_work);
+  delete B;
+  return PA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,313 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerance: relative L2 error <= 1e-4 against the FP64 oracle for every
+reconstruction, adjoint and position gradient; the FP32 NUFFT with a width-8
+Kaiser-Bessel window is expected near 1e-6.  Dot-product tests of the GPU
+operator and its adjoint: <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import ndft, nufft
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1501_02946_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def pa():
+    import paper_1501_02946_gb300 as m
+    return m
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def plan_of(P, width=8, sigma=2):
+    return pa().Plan(P.xy, P.n_t, P.dt, P.c, P.grid.as_tuple(), weights=P.h, sigma=sigma, width=width)
+
+
+def custom_problem(nsx, nsy, grid, n_t, dt=20e-9, seed=0, jitter=0.4):
+    rng = np.random.default_rng(seed)
+    xy = synth.jittered_lattice(rng, nsx, nsy, grid.dx, grid.dy, jitter)
+    g = rng.normal(size=(xy.shape[0], n_t))
+    X, Y = grid.nx * grid.dx, grid.ny * grid.dy
+    return synth.Problem("custom", xy, np.full(xy.shape[0], X * Y / xy.shape[0]), g, dt, 1500.0, grid)
+
+
+# ----------------------------------------------------------------- forward
+@pytest.mark.parametrize("name", ["tiny", "c1"])
+def test_forward_matches_direct_sum(name):
+    P = getattr(synth, name)()
+    ref = ndft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid)
+    plan = plan_of(P)
+    f = host(plan.reconstruct(dev(P.g)))
+    err = rel(f, ref)
+    print(f"{name}: rel L2 vs O1 = {err:.3e}")
+    assert err <= TOL
+    assert plan.status() == 0
+
+
+@pytest.mark.parametrize("grid,n_t,ns", [
+    (synth.Grid(15, 21, 25, 1e-4, 1e-4, 1e-4), 45, (15, 21)),
+    (synth.Grid(12, 9, 10, 1e-4, 1.5e-4, 1e-4), 36, (12, 9)),
+    (synth.Grid(10, 14, 27, 1.2e-4, 1e-4, 0.8e-4), 50, (9, 13)),
+    (synth.Grid(16, 8, 12, 1e-4, 1e-4, 1e-4), 35, (20, 11)),
+])
+def test_forward_odd_and_ragged_sizes(grid, n_t, ns):
+    P = custom_problem(ns[0], ns[1], grid, n_t)
+    ref = ndft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid)
+    f = host(plan_of(P).reconstruct(dev(P.g)))
+    err = rel(f, ref)
+    print(f"{grid.shape} nt={n_t}: rel L2 = {err:.3e}")
+    assert err <= TOL
+
+
+@pytest.mark.parametrize("width", [6, 12, 16])
+def test_forward_other_widths(width):
+    P = synth.c1()
+    ref = ndft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid)
+    err = rel(host(plan_of(P, width=width).reconstruct(dev(P.g))), ref)
+    print(f"width {width}: rel L2 = {err:.3e}")
+    assert err <= (3e-4 if width == 6 else TOL)
+
+
+def test_sigma_three():
+    P = synth.c1()
+    ref = ndft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid)
+    err = rel(host(plan_of(P, sigma=3).reconstruct(dev(P.g))), ref)
+    assert err <= TOL
+
+
+# ----------------------------------------------------------- stage parity
+def test_spatial_spectrum_stage():
+    """G1 after the NED step against eq:NUDFT2 evaluated directly."""
+    P = synth.c1()
+    plan = plan_of(P)
+    plan.reconstruct(dev(P.g))
+    G1 = plan.buffer(0).cpu().numpy().astype(np.complex128)
+    ref = ndft.data_transform(P.xy, P.h, P.g, P.grid)      # [nx][ny][nt], j + h
+    nx, ny = P.grid.nx, P.grid.ny
+    hx, hy = nx // 2, ny // 2
+    exp = np.empty_like(G1)
+    for ix in range(2 * hx + 1):
+        jx = ix - hx
+        for jy in range(hy + 1):
+            if jx < nx - hx:
+                exp[ix, jy] = ref[jx + hx, jy + hy]
+            else:  # jx = +nx/2: Hermitian partner of (-jx, -jy)
+                exp[ix, jy] = np.conj(ref[-jx + hx, -jy + hy])
+    err = rel(G1, exp)
+    print(f"G1 rel L2 = {err:.3e}")
+    assert err <= TOL
+
+
+def test_time_frequency_stage():
+    """Spectrum after NER, weight, Hermitian symmetrisation and inverse DFT
+    over depth, against the direct sums of eq:disc_rec."""
+    P = synth.c1()
+    plan = plan_of(P)
+    plan.reconstruct(dev(P.g))
+    Fz = plan.buffer(1).cpu().numpy().astype(np.complex128)
+    _, aux = ndft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid, full=True)
+    F = aux["F"]
+    nx, ny, nz = P.grid.shape
+    hx, hy, hz = nx // 2, ny // 2, nz // 2
+    ia = (2 * hx - np.arange(nx)) % nx
+    ib = (2 * hy - np.arange(ny)) % ny
+    ic = (2 * hz - np.arange(nz)) % nz
+    Fneg = F[np.ix_(ia, ib, ic)]
+    Fsym = 0.5 * (F + np.conj(Fneg))
+    l = ndft.freqs(nz)
+    z = np.arange(nz)
+    E = np.exp(2j * np.pi * np.outer(l, z) / nz)            # [l][z]
+    exp = np.einsum("abl,lz->abz", Fsym[:, hy:, :], E) / (nx * ny * nz)
+    err = rel(Fz, exp)
+    print(f"Fz rel L2 = {err:.3e}")
+    assert err <= TOL
+
+
+# ------------------------------------------------------------------ adjoint
+@pytest.mark.parametrize("name", ["tiny", "c1"])
+def test_adjoint_matches_direct_transpose(name):
+    P = getattr(synth, name)()
+    rng = np.random.default_rng(3)
+    fb = rng.normal(size=P.grid.shape)
+    ref = ndft.reconstruct_adjoint(P.xy, P.h, fb, P.dt, P.c, P.grid, P.n_t)
+    got = host(plan_of(P).adjoint(dev(fb)))
+    err = rel(got, ref)
+    print(f"{name}: adjoint rel L2 = {err:.3e}")
+    assert err <= TOL
+
+
+def _dot_test(P, plan, seed=4):
+    rng = np.random.default_rng(seed)
+    g = rng.normal(size=(P.n_sensors, P.n_t))
+    fb = rng.normal(size=P.grid.shape)
+    Ag = host(plan.reconstruct(dev(g)))
+    Atf = host(plan.adjoint(dev(fb)))
+    g32 = g.astype(np.float32).astype(np.float64)
+    f32 = fb.astype(np.float32).astype(np.float64)
+    return abs(np.sum(Ag * f32) - np.sum(g32 * Atf)) / (np.linalg.norm(Ag) * np.linalg.norm(f32))
+
+
+@pytest.mark.parametrize("name", ["tiny", "c1"])
+def test_dot_product_small(name):
+    P = getattr(synth, name)()
+    d = _dot_test(P, plan_of(P))
+    print(f"{name}: dot test {d:.3e}")
+    assert d <= 1e-5
+
+
+def test_dot_product_odd_sizes():
+    P = custom_problem(15, 21, synth.Grid(15, 21, 25, 1e-4, 1e-4, 1e-4), 45)
+    assert _dot_test(P, plan_of(P)) <= 1e-5
+    P = custom_problem(12, 9, synth.Grid(12, 9, 10, 1e-4, 1.5e-4, 1e-4), 36)
+    assert _dot_test(P, plan_of(P)) <= 1e-5
+
+
+# ------------------------------------------------------ position gradient
+@pytest.mark.parametrize("name", ["tiny", "c1"])
+def test_position_gradient_matches_analytic(name):
+    P = getattr(synth, name)()
+    rng = np.random.default_rng(8)
+    fb = rng.normal(size=P.grid.shape)
+    ref = ndft.position_grad(P.xy, P.h, P.g, fb, P.dt, P.c, P.grid)
+    plan = plan_of(P)
+    gg, gxy = plan.position_grad(dev(P.g), dev(fb))
+    err = rel(host(gxy), ref)
+    print(f"{name}: position gradient rel L2 = {err:.3e}")
+    assert err <= TOL
+    ref_g = ndft.reconstruct_adjoint(P.xy, P.h, fb, P.dt, P.c, P.grid, P.n_t)
+    assert rel(host(gg), ref_g) <= TOL
+
+
+def test_autograd_function():
+    P = synth.c1()
+    plan = plan_of(P)
+    g = dev(P.g).requires_grad_(True)
+    xy = torch.tensor(P.xy, dtype=torch.float64, requires_grad=True)
+    f = pa().reconstruct(g, xy, plan)
+    rng = np.random.default_rng(12)
+    fb = dev(rng.normal(size=P.grid.shape))
+    (f * fb).sum().backward()
+    gg, gxy = plan.position_grad(dev(P.g), fb)
+    assert rel(host(g.grad), host(gg)) <= 1e-6
+    assert rel(xy.grad.numpy(), host(gxy)) <= 1e-6
+    ref = ndft.position_grad(P.xy, P.h, P.g, host(fb), P.dt, P.c, P.grid)
+    assert rel(xy.grad.numpy(), ref) <= TOL
+
+
+def test_update_positions_matches_new_plan():
+    P = synth.c1()
+    plan = plan_of(P)
+    rng = np.random.default_rng(21)
+    xy2 = P.xy + rng.normal(scale=2e-5, size=P.xy.shape)
+    plan.update_positions(xy2)
+    a = host(plan.reconstruct(dev(P.g)))
+    b = host(pa().Plan(xy2, P.n_t, P.dt, P.c, P.grid.as_tuple(), weights=P.h).reconstruct(dev(P.g)))
+    assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------- edge cases
+def test_positions_wrap_by_period():
+    P = synth.c1()
+    X = P.grid.nx * P.grid.dx
+    a = host(plan_of(P).reconstruct(dev(P.g)))
+    Q = synth.Problem("w", P.xy + np.array([X, -3 * X]), P.h, P.g, P.dt, P.c, P.grid)
+    b = host(plan_of(Q).reconstruct(dev(P.g)))
+    assert rel(b, a) <= 1e-5
+
+
+def test_single_sensor_and_one_cell():
+    grid = synth.Grid(8, 8, 16, 1e-4, 1e-4, 1e-4)
+    rng = np.random.default_rng(2)
+    for xy in (np.array([[1.3e-5, -2.2e-4]]), np.full((40, 2), 3.1e-5) + rng.uniform(0, 1e-6, (40, 2))):
+        g = rng.normal(size=(xy.shape[0], 32))
+        h = np.full(xy.shape[0], 6.4e-7 / xy.shape[0])
+        ref = ndft.reconstruct(xy, h, g, 40e-9, 1500.0, grid)
+        got = host(pa().Plan(xy, 32, 40e-9, 1500.0, grid.as_tuple(), weights=h).reconstruct(dev(g)))
+        assert rel(got, ref) <= TOL
+
+
+def test_zero_data_gives_zero_image():
+    P = synth.tiny()
+    f = host(plan_of(P).reconstruct(dev(np.zeros_like(P.g))))
+    assert np.all(f == 0.0)
+
+
+# ------------------------------------------------------ baseline and batch
+def test_cubic_baseline_is_less_accurate():
+    P = synth.c1()
+    ref = ndft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid)
+    plan = plan_of(P)
+    e_nufft = rel(host(plan.reconstruct(dev(P.g))), ref)
+    e_cubic = rel(host(plan.reconstruct_cubic(dev(P.g))), ref)
+    print(f"cubic baseline rel L2 = {e_cubic:.3e} (NUFFT {e_nufft:.3e})")
+    assert e_nufft < e_cubic < 1.0
+
+
+def test_batch_matches_single_plans():
+    rng = np.random.default_rng(5)
+    probs = [synth.batch_instance(rng, n, t, n_balls=2) for n, t in ((16, 32), (21, 48), (12, 64), (20, 40))]
+    plans = [plan_of(P) for P in probs]
+    gs = [dev(P.g) for P in probs]
+    singles = [host(p.reconstruct(g)) for p, g in zip(plans, gs)]
+    B = pa().Batch(plans)
+    fs = [torch.empty(p.image_shape, device="cuda") for p in plans]
+    for _ in range(3):  # first run captures the graph, later runs replay it
+        for f in fs:
+            f.zero_()
+        B.run(gs, fs)
+        for f, s in zip(fs, singles):
+            assert np.array_equal(host(f), s)
+    ref = ndft.reconstruct(probs[1].xy, probs[1].h, probs[1].g, probs[1].dt, probs[1].c, probs[1].grid)
+    assert rel(singles[1], ref) <= TOL
+
+
+# ----------------------------------------------------------- full size
+@pytest.fixture(scope="module")
+def c2():
+    return synth.c2()
+
+
+def test_c2_forward_matches_nufft_oracle(c2):
+    P = c2
+    ref = nufft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid, 2, 12)
+    f = host(plan_of(P).reconstruct(dev(P.g)))
+    err = rel(f, ref)
+    print(f"C2 forward rel L2 vs O2(w=12) = {err:.3e}")
+    assert err <= TOL
+
+
+def test_c2_adjoint_and_dot(c2):
+    P = c2
+    plan = plan_of(P)
+    rng = np.random.default_rng(6)
+    fb = rng.normal(size=P.grid.shape)
+    ref = nufft.reconstruct_adjoint(P.xy, P.h, fb, P.dt, P.c, P.grid, P.n_t, 2, 12)
+    err = rel(host(plan.adjoint(dev(fb))), ref)
+    print(f"C2 adjoint rel L2 = {err:.3e}")
+    assert err <= TOL
+    assert _dot_test(P, plan) <= 1e-5
