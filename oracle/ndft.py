@@ -51,21 +51,27 @@ def omega_and_weight(grid, c):
     return omega, W
 
 
-def spatial_factors(xy, grid):
-    """Ex[jx, m] = exp(-i kx x_m), Ey[jy, m] = exp(-i ky y_m)."""
-    kx, ky, _ = wavenumbers(grid)
+def spatial_factors(xy, grid, jx=None, jy=None):
+    """Ex[jx, m] = exp(-i kx x_m), Ey[jy, m] = exp(-i ky y_m), by default on
+    the index sets of Sec. 2; jx, jy select other integer frequencies."""
+    if jx is None:
+        kx, ky, _ = wavenumbers(grid)
+    else:
+        kx = 2 * np.pi * np.asarray(jx) / (grid.nx * grid.dx)
+        ky = 2 * np.pi * np.asarray(jy) / (grid.ny * grid.dy)
     Ex = np.exp(-1j * np.outer(kx, xy[:, 0]))
     Ey = np.exp(-1j * np.outer(ky, xy[:, 1]))
     return Ex, Ey
 
 
-def data_transform(xy, h, g, grid):
-    """G1(jx, jy, n) = sum_m (h_m/(dx dy)) g[m, n] exp(-i(kx x_m + ky y_m))."""
+def data_transform(xy, h, g, grid, jx=None, jy=None):
+    """G1(jx, jy, n) = sum_m (h_m/(dx dy)) g[m, n] exp(-i(kx x_m + ky y_m)),
+    on the index sets of Sec. 2 or on the integer frequencies jx, jy given."""
     a = h / (grid.dx * grid.dy)
     ga = (a[:, None] * g).astype(np.complex128)
-    Ex, Ey = spatial_factors(xy, grid)
-    G1 = np.empty((grid.nx, grid.ny, g.shape[1]), dtype=np.complex128)
-    for ix in range(grid.nx):
+    Ex, Ey = spatial_factors(xy, grid, jx, jy)
+    G1 = np.empty((Ex.shape[0], Ey.shape[0], g.shape[1]), dtype=np.complex128)
+    for ix in range(Ex.shape[0]):
         G1[ix] = (Ey * Ex[ix][None, :]) @ ga
     return G1
 

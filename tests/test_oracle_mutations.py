@@ -42,7 +42,7 @@ def test_mutation_weight_at_l0(patch):
 
 def test_mutation_spatial_sign(patch):
     f0 = _orig("spatial_factors")
-    patch.setattr(ndft, "spatial_factors", lambda xy, grid: tuple(E.conj() for E in f0(xy, grid)))
+    patch.setattr(ndft, "spatial_factors", lambda xy, grid, *a: tuple(E.conj() for E in f0(xy, grid, *a)))
     assert pinlib.pin_lattice_fft2() > 1e-2
     assert pinlib.pin_shift_roll() > 1e-2
 
@@ -50,8 +50,8 @@ def test_mutation_spatial_sign(patch):
 def test_mutation_transposed_axes(patch):
     f0 = _orig("spatial_factors")
 
-    def bad(xy, grid):
-        return f0(xy[:, ::-1].copy(), grid)
+    def bad(xy, grid, *a):
+        return f0(xy[:, ::-1].copy(), grid, *a)
     patch.setattr(ndft, "spatial_factors", bad)
     assert pinlib.pin_lattice_fft2() > 1e-2
 
