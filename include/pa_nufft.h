@@ -120,6 +120,32 @@ int pa_position_grad(pa_plan *plan, const float *g_dev, const float *grad_f_dev,
                      float *grad_g_dev, float *grad_xy_dev, void *stream);
 
 /*
+ * Position gradient without device allocation.  The paper has no counterpart;
+ * this is a library convenience.  Same result as pa_position_grad (same
+ * kernels), but the kernel's scratch -- the per-chunk partial sums of the
+ * gradient, ceil(n_t/8) * n_sensors float2 values -- lives in a static device
+ * array of the library (16 MiB, at most 2^21 partials; larger problems get
+ * PA_ERR_UNSUPPORTED_SIZE) instead of the plan's workspace.  For callers
+ * that may not call cudaMalloc at the time they need gradients: code running
+ * while a CUDA graph is being captured (cudaMalloc is not a stream operation
+ * and is refused or breaks the capture), or code whose device memory is owned
+ * by a fixed arena or an external allocator that forbids new allocations.
+ *   - The call allocates nothing: no cudaMalloc/cudaFree, no allocating
+ *     library routine.  It copies one plan descriptor (host to device) and
+ *     launches the same kernels as pa_position_grad.
+ *   - The first call on a device looks up the static array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.  The plan's device must be current.
+ *   - All calls share the one array and descriptor, which keep the last
+ *     call's contents; every partial is rewritten by each call, so nothing
+ *     needs clearing.  Calls that overlap on the GPU (different streams, or
+ *     host threads) race and must not be issued.
+ * Arguments as in pa_position_grad.
+ */
+int pa_position_grad_noalloc(pa_plan *plan, const float *g_dev, const float *grad_f_dev,
+                             float *grad_g_dev, float *grad_xy_dev, void *stream);
+
+/*
  * Replace the sensor positions (host [M][2] doubles, metres) of an existing
  * plan; the binning and window taps are rebuilt and uploaded on `stream`.
  * Weights stay as they were.

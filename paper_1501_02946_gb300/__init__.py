@@ -146,6 +146,20 @@ class Plan:
                                            c_void_p(grad_xy.data_ptr()), _stream_ptr(g.device)))
         return grad_g, grad_xy
 
+    def position_grad_noalloc(self, g, grad_f, want_grad_g=True):
+        """position_grad whose scratch is the library's static device array
+        (no device allocation in the call; see include/pa_nufft.h)."""
+        torch = _torch()
+        _check_tensor(g, self.data_shape, "g")
+        _check_tensor(grad_f, self.image_shape, "grad_f")
+        grad_xy = torch.empty((self.M, 2), dtype=torch.float32, device=g.device)
+        grad_g = torch.empty(self.data_shape, dtype=torch.float32, device=g.device) if want_grad_g else None
+        check(_lib.load().pa_position_grad_noalloc(
+            self.handle, c_void_p(g.data_ptr()), c_void_p(grad_f.data_ptr()),
+            c_void_p(grad_g.data_ptr()) if grad_g is not None else None, c_void_p(grad_xy.data_ptr()),
+            _stream_ptr(g.device)))
+        return grad_g, grad_xy
+
     def update_positions(self, xy):
         xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(-1, 2))
         if xy.shape[0] != self.M:

@@ -34,6 +34,7 @@ SIGNATURES = {
     "pa_reconstruct": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pa_reconstruct_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pa_position_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "pa_position_grad_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pa_plan_update_positions": (c_int, [c_void_p, c_void_p, c_void_p]),
     "pa_reconstruct_cubic": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pa_plan_destroy": (c_int, [c_void_p]),

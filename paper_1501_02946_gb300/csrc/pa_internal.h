@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+struct pa_plan;
+
 namespace pa {
 
 constexpr int kMaxStages = 12;
@@ -132,5 +134,17 @@ cudaError_t launch_imgx(const Launch &L, bool adjoint);
 cudaError_t launch_imgy(const Launch &L, bool adjoint);
 cudaError_t launch_interp_width(const Launch &L, int width, bool grad);
 cudaError_t launch_grad_reduce(const Launch &L, int M);
+
+// Read-only view of a plan for the other translation units of the library.
+struct PlanView {
+  const InstDesc *h;        // host copy of the descriptor (device pointers inside)
+  int width;
+  const HornerTable *ht;
+  int device;
+  long long n_sensors;
+};
+int plan_view(const pa_plan *P, PlanView *v);
+// Record an error message for pa_last_error() and return `code`.
+int set_error(int code, const char *msg);
 
 }  // namespace pa

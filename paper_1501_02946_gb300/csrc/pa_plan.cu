@@ -398,6 +398,19 @@ int run_adjoint(pa_plan *P, const IoPtrs &io, cudaStream_t s, bool grad) {
 
 }  // namespace
 
+namespace pa {
+int plan_view(const pa_plan *P, PlanView *v) {
+  if (!P || !v) return PA_ERR_INVALID_ARG;
+  v->h = &P->h;
+  v->width = P->w;
+  v->ht = &P->ht;
+  v->device = P->device;
+  v->n_sensors = P->M;
+  return PA_OK;
+}
+int set_error(int code, const char *msg) { return fail(code, msg ? msg : ""); }
+}  // namespace pa
+
 extern "C" {
 
 const char *pa_last_error(void) { return g_err.c_str(); }
