@@ -35,7 +35,7 @@ UNIT = "voxels/s"
 WORKLOAD = ("128x128 non-equispaced sensors over 12.8 mm (8192 jittered lattice + 8192 centre-dense), "
             "512 samples at 20 ns, 20 balls + 1% noise, output 128x128x256 at 100 um, sigma 2, width 8")
 STAGES = ["ned_spread_rowfft", "ned_colfft", "ner_fused", "image_x", "image_y_c2r", "image_y_adj",
-          "image_x_adj", "ner_adj", "ned_colfft_adj", "ned_rowifft_interp"]
+          "image_x_adj", "ner_adj", "ned_colfft_adj", "ned_rowifft", "ned_interp"]
 
 
 def stage_bytes(M, Nt, Nx, Ny, Nz, sigma=2):
@@ -50,7 +50,8 @@ def stage_bytes(M, Nt, Nx, Ny, Nz, sigma=2):
     f = 4 * Nx * Ny * Nz
     return {"ned_spread_rowfft": g + T, "ned_colfft": T + G1, "ner_fused": G1 + F, "image_x": 2 * F,
             "image_y_c2r": F + f, "image_y_adj": f + F, "image_x_adj": 2 * F, "ner_adj": F + G1,
-            "ned_colfft_adj": G1 + T, "ned_rowifft_interp": T + g}
+            "ned_colfft_adj": G1 + T, "ned_rowifft": T + 4 * Mx * (sigma * Ny) * Nt,
+            "ned_interp": 4 * Mx * (sigma * Ny) * Nt + g}
 
 
 def pipeline_min_bytes(M, Nt, Nx, Ny, Nz):
@@ -350,7 +351,7 @@ def run_ours(args):
                       "l2": "flushed between timed steps (256 MiB write outside the timed events)",
                       "parallelism": f"replicas x{world}", "wall_s": t_wall},
            "roofline": roofline, "pipeline_roofline": pipeline, "stages": stages, "cpu_baseline": cpu,
-           "e2e": e2e, "gpu_launches": 10 * args.steps, "clocks": clocks}
+           "e2e": e2e, "gpu_launches": sum(v[1] for v in prof.values()), "clocks": clocks}
     if rank == 0:
         print(json.dumps(out))
     plan.close()

@@ -123,7 +123,7 @@ int pa_position_grad(pa_plan *plan, const float *g_dev, const float *grad_f_dev,
  * Position gradient without device allocation.  The paper has no counterpart;
  * this is a library convenience.  Same result as pa_position_grad (same
  * kernels), but the kernel's scratch -- the per-chunk partial sums of the
- * gradient, ceil(n_t/8) * n_sensors float2 values -- lives in a static device
+ * gradient, ceil(n_t/32) * n_sensors float2 values -- lives in a static device
  * array of the library (16 MiB, at most 2^21 partials; larger problems get
  * PA_ERR_UNSUPPORTED_SIZE) instead of the plan's workspace.  For callers
  * that may not call cudaMalloc at the time they need gradients: code running
@@ -206,7 +206,7 @@ int pa_plan_buffer(const pa_plan *plan, int which, void *dst_dev, int64_t capaci
  * and the number of launches since the last read, and clears them.
  * Stages: see pa_profile_stage_name (0 .. PA_PROFILE_STAGES-1).
  */
-#define PA_PROFILE_STAGES 12
+#define PA_PROFILE_STAGES 13
 int pa_profile_enable(pa_plan *plan, int enable);
 int pa_profile_read(pa_plan *plan, double *ms_total, int64_t *launches);
 const char *pa_profile_stage_name(int stage);

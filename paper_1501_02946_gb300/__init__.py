@@ -197,7 +197,7 @@ class Plan:
         """{stage name: (total ms, launches)} since the last read (waits for
         the recorded events)."""
         lib = _lib.load()
-        n = 12
+        n = 13
         ms = (ctypes.c_double * n)()
         cnt = (ctypes.c_int64 * n)()
         check(lib.pa_profile_read(self.handle, ms, cnt))

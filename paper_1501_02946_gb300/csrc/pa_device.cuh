@@ -218,9 +218,19 @@ struct Ipt {
 // (j / Ns) Ns R + k + t Ns.  Sequences b < nb are interleaved with stride 1
 // (element i of sequence b at buf[i * estride + b]).  Reads of a round finish
 // (barrier) before its writes; rounds cover whole sequences.
+// Barrier of the threads that share one transform: the whole block
+// (bar_id = 0) or a named barrier over `nthr` threads (bar_id >= 1).
+__device__ __forceinline__ void group_sync(int bar_id, int nthr) {
+  if (bar_id == 0) {
+    __syncthreads();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthr) : "memory");
+  }
+}
+
 template <int R, int DIR>
 __device__ __forceinline__ void fft_stage(float2 *buf, int estride, int nb, int L, int Ns,
-                                          const float2 *__restrict__ tw, int tid, int nthr) {
+                                          const float2 *__restrict__ tw, int tid, int nthr, int bar_id = 0) {
   constexpr int IPT = Ipt<R>::v;
   const int nj = L / R;
   const int twstep = L / (Ns * R);
@@ -249,7 +259,7 @@ __device__ __forceinline__ void fft_stage(float2 *buf, int estride, int nb, int 
         }
       }
     }
-    __syncthreads();
+    group_sync(bar_id, nthr);
 #pragma unroll
     for (int it = 0; it < IPT; ++it) {
       const int item = tid + it * nthr;
@@ -263,7 +273,7 @@ __device__ __forceinline__ void fft_stage(float2 *buf, int estride, int nb, int 
         for (int t = 0; t < R; ++t) buf[(o + t * Ns) * estride + b] = v[it][t];
       }
     }
-    __syncthreads();
+    group_sync(bar_id, nthr);
   }
 }
 
@@ -271,7 +281,7 @@ __device__ __forceinline__ void fft_stage(float2 *buf, int estride, int nb, int 
 // in place in shared memory.  All threads of the block must call it.
 template <int DIR>
 __device__ void fft_smem(float2 *buf, int estride, int nb, const FftPlan &fp, const float2 *__restrict__ twbase,
-                         int tid, int nthr) {
+                         int tid, int nthr, int bar_id = 0) {
   const float2 *tw = twbase + fp.tw;
   const int L = fp.L;
   const int nst = fp.nst;
@@ -280,7 +290,7 @@ __device__ void fft_smem(float2 *buf, int estride, int nb, const FftPlan &fp, co
   // radix keeps the register allocation of each radix separate.
 #define PA_FFT_RUN(R)                                                   \
   while (s < nst && fp.radix[s] == R) {                                 \
-    fft_stage<R, DIR>(buf, estride, nb, L, Ns, tw, tid, nthr);          \
+    fft_stage<R, DIR>(buf, estride, nb, L, Ns, tw, tid, nthr, bar_id);  \
     Ns *= R;                                                            \
     ++s;                                                                \
   }
@@ -292,6 +302,65 @@ __device__ void fft_smem(float2 *buf, int estride, int nb, const FftPlan &fp, co
   PA_FFT_RUN(5)
   PA_FFT_RUN(7)
 #undef PA_FFT_RUN
+}
+
+// Out-of-place variant for single sequences (element stride 1): each stage
+// reads `src` and writes `dst` one butterfly at a time, so a thread holds only
+// R values at once; the buffers swap after every stage.  Returns the buffer
+// that holds the result (src or dst).
+template <int R, int DIR>
+__device__ __forceinline__ void fft_stage_oop(const float2 *src, float2 *dst, int L, int Ns,
+                                              const float2 *__restrict__ tw, int tid, int nthr) {
+  const int nj = L / R;
+  const int twstep = L / (Ns * R);
+#pragma unroll 1
+  for (int j = tid; j < nj; j += nthr) {
+    const int k = j % Ns;
+    float2 v[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      float2 x = src[j + t * nj];
+      if (t > 0 && k > 0) {
+        float2 w = __ldg(tw + t * k * twstep);
+        if (DIR > 0) w.y = -w.y;
+        x = cmul(x, w);
+      }
+      v[t] = x;
+    }
+    Dft<R, DIR>::run(v);
+    const int o = (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int t = 0; t < R; ++t) dst[o + t * Ns] = v[t];
+  }
+}
+
+template <int DIR>
+__device__ float2 *fft_pingpong(float2 *a, float2 *b, const FftPlan &fp, const float2 *__restrict__ twbase, int tid,
+                                int nthr, int bar_id) {
+  const float2 *tw = twbase + fp.tw;
+  const int L = fp.L;
+  const int nst = fp.nst;
+  int Ns = 1, s = 0;
+  float2 *src = a, *dst = b;
+#define PA_FFT_OOP(R)                                                \
+  while (s < nst && fp.radix[s] == R) {                              \
+    fft_stage_oop<R, DIR>(src, dst, L, Ns, tw, tid, nthr);           \
+    group_sync(bar_id, nthr);                                        \
+    float2 *x = src;                                                 \
+    src = dst;                                                       \
+    dst = x;                                                         \
+    Ns *= R;                                                         \
+    ++s;                                                             \
+  }
+  PA_FFT_OOP(16)
+  PA_FFT_OOP(8)
+  PA_FFT_OOP(4)
+  PA_FFT_OOP(2)
+  PA_FFT_OOP(3)
+  PA_FFT_OOP(5)
+  PA_FFT_OOP(7)
+#undef PA_FFT_OOP
+  return src;
 }
 
 // Instance and tile of this block.

@@ -42,8 +42,9 @@ struct InstDesc {
   int hx, hy, hz, nc;   // floor(N/2) of x, y, z, t
   int nX1, nY1;         // rows of the spatial spectrum: 2*hx+1 (jx) and hy+1 (jy)
   int nchunk_adj;       // n-chunks of the adjoint NED kernel (gradient partials)
+  int ner_group;        // threads per column in the NER kernels (64, 128 or 256)
 
-  FftPlan fMy, fMx, fMt, fNz, fNx, fNy, fNt;
+  FftPlan fMy, fMx, fMt, fNz, fNx, fNy, fNt, fMyh;  // fMyh: length My/2
   const float2 *tw;
 
   // sensors sorted by (bx, by); taps t = 0..w-1 cover cells base - w/2 + 1 + t
@@ -52,6 +53,27 @@ struct InstDesc {
   const float *wx, *wy; // [M][w]; wy carries a_m = h_m/(dx dy)
   const float *dwx, *dwy;  // [M][w] derivative taps d/dx_m and d/dy_m
   const int *cell_start;   // [Mx*My + 1] CSR offsets of the sorted sensors per cell
+  // forward spread visits: for strip s (kSpreadP grid rows) and q-group g
+  // (kSpreadQG columns), visits visit_start[s*NG+g] .. visit_start[s*NG+g+1]-1
+  // with NG = ceil(My / kSpreadQG); each visit is a sensor (caller index vm)
+  // and its tap products vprod[v*kSpreadQG + qi] = (row 0..3) for column qi.
+  const int *visit_start;
+  const int *vm;
+  const float4 *vprod;
+  // cluster spread (two blocks per strip, each half of the q range): for key
+  // = strip*2 + half, slots cl_slot_start[key] .. cl_slot_start[key+1]-1 are
+  // the sensors whose footprint meets the strip rows and the half's columns
+  // (caller index and base column in cl_meta, the strip rows' x taps in
+  // cl_wx, the y taps in cl_wy[slot*w + t]); q-group g of the half (QG
+  // columns) visits the slots cl_vslot[cl_vstart[key*NGH+g] ..] (local to key).
+  const int *cl_slot_start;
+  const int2 *cl_meta;
+  const float4 *cl_wx;
+  const float *cl_wy;
+  const int *cl_vstart;
+  const int *cl_vslot;
+  int cl_smax;          // most slots of any (strip, half)
+  int spread_mode;      // 0: one block per strip, 1: cluster of two
   // deconvolution factors 1/phihat (window normalised to phi(0) = 1)
   const float *invphx;  // [nX1], jx = ix - hx, at jx / Mx
   const float *invphy;  // [nY1], jy, at jy / My
@@ -73,6 +95,7 @@ struct InstDesc {
   float2 *Fz;           // [Nx][nY1][Nz]   after NER and the inverse depth DFT
   float2 *U;            // [Nx][nY1][Nz]   after the inverse x DFT
   float2 *grad_part;    // [nchunk_adj][M] per-chunk position-gradient partials
+  float *G0;            // [Mx][My][Nt] real oversampled-grid cotangent (adjoint)
   int *status;
 };
 
@@ -90,10 +113,9 @@ struct IoPtrs {
 constexpr int kSpreadP = 4;      // oversampled rows per forward NED strip
 constexpr int kSpreadNCP = 8;    // complex pairs of samples per forward strip
 constexpr int kSpreadGPW = 8;    // q-groups per warp
-constexpr int kSpreadSMax = 128; // sensors staged per pass
+constexpr int kSpreadQG = 32 / kSpreadNCP;  // grid columns per lane group
 constexpr int kColNC = 16;       // samples per column-FFT tile
-constexpr int kAdjPo = 4;        // owned sensor rows per adjoint NED tile
-constexpr int kAdjNCP = 4;       // sample pairs per adjoint NED tile
+constexpr int kInterpNC = 32;    // samples per adjoint interpolation tile
 constexpr int kImgZC = 16;       // depth samples per inverse-x tile
 constexpr int kImgZP = 16;       // depth pairs per y-C2R tile
 
@@ -113,6 +135,8 @@ struct Launch {
 int blocks_spread(const InstDesc &d);
 size_t smem_spread(const InstDesc &d);
 int threads_spread(const InstDesc &d);
+size_t smem_spread_cluster(const InstDesc &d);
+int threads_spread_cluster(const InstDesc &d);
 int blocks_colfft(const InstDesc &d);
 size_t smem_colfft(const InstDesc &d);
 int blocks_ner(const InstDesc &d);
@@ -125,14 +149,20 @@ int blocks_imgy(const InstDesc &d);
 size_t smem_imgy(const InstDesc &d);
 int blocks_interp(const InstDesc &d);
 size_t smem_interp(const InstDesc &d);
+int blocks_rowifft(const InstDesc &d);
+size_t smem_rowifft(const InstDesc &d);
 
 cudaError_t launch_spread(const Launch &L, int threads);
+cudaError_t launch_spread_cluster(const Launch &L, int threads, int width);
 cudaError_t launch_colfft(const Launch &L, bool adjoint);
 cudaError_t launch_ner(const Launch &L, int width, const HornerTable &ht, bool adjoint);
+// which: 0 forward, 1 adjoint
+cudaError_t launch_ner_stage(const Launch &L, int width, const HornerTable &ht, int which);
 cudaError_t launch_cubic(const Launch &L);
 cudaError_t launch_imgx(const Launch &L, bool adjoint);
 cudaError_t launch_imgy(const Launch &L, bool adjoint);
 cudaError_t launch_interp_width(const Launch &L, int width, bool grad);
+cudaError_t launch_rowifft(const Launch &L);
 cudaError_t launch_grad_reduce(const Launch &L, int M);
 
 // Read-only view of a plan for the other translation units of the library.

@@ -161,112 +161,88 @@ __device__ __forceinline__ ColInfo col_info(const InstDesc &d, int jx, int jy) {
   return c;
 }
 
-// Forward NER of one column into Fz.  CUBIC selects the baseline.
+// Threads that share one column: the smallest group for which every stage
+// of the column transforms fits one round (host-side check mirrors this).
+__device__ __forceinline__ int ner_group(const InstDesc &d) { return d.ner_group; }
+// Length of each of the two ping-pong buffers of a column.
+__host__ __device__ __forceinline__ int ner_buf_len(const InstDesc &d) {
+  int L = d.Mt > d.Nt ? d.Mt : d.Nt;
+  return L > d.Nz ? L : d.Nz;
+}
+
+// Forward NER: a group of G threads (G = 64/128/256, named barrier 1 + group
+// index) owns one column of the half spectrum and two ping-pong buffers for
+// out-of-place FFTs.  Columns on an unpaired Nyquist index (x or y) read two
+// sources (A, B) that are transformed one after the other.  CUBIC selects
+// the baseline (plain Nt-point FFT, 4-tap Lagrange interpolation, no window).
 template <int W, bool CUBIC>
-__global__ void __launch_bounds__(kThreadsNer) k_ner(const InstDesc *__restrict__ descs, const int2 *__restrict__ work,
-                                                     const __grid_constant__ HornerTable ht) {
+__global__ void __launch_bounds__(kThreadsNer, 3) k_ner(const InstDesc *__restrict__ descs,
+                                                        const int2 *__restrict__ work,
+                                                        const __grid_constant__ HornerTable ht) {
   extern __shared__ float4 smem_f4[];
   int inst, tile;
   block_work(work, inst, tile);
   const InstDesc &d = descs[inst];
+  const int G = ner_group(d);
+  const int ngrp = blockDim.x / G;
+  const int grp = threadIdx.x / G, t = threadIdx.x % G, bar = 1 + grp;
   const int Nt = d.Nt, Mt = d.Mt, Nz = d.Nz, nY1 = d.nY1, nc = d.nc, hz = d.hz;
-  if (tile >= d.Nx * nY1) return;
-  const int ix = tile / nY1, iy = tile % nY1;
+  const int ncols = d.Nx * nY1;
+  const int col = tile * ngrp + grp;
+  if (col >= ncols) return;  // the whole group leaves together
+  const int ix = col / nY1, iy = col % nY1;
   const ColInfo ci = col_info(d, ix - d.hx, iy);
   const bool nyq = ci.xnyq || ci.ynyq;
-  const int L = CUBIC ? Nt : Mt;
-  float2 *HA = reinterpret_cast<float2 *>(smem_f4);
-  float2 *HB = HA + L;
-  float2 *Fs = HB + L;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-
-  const float2 *srcA = d.G1 + ((size_t)ci.rowA * nY1 + iy) * Nt;
-  const float2 *srcB = d.G1 + ((size_t)ci.rowB * nY1 + iy) * Nt;
-  for (int n = tid; n < Nt; n += nthr) {
-    float2 a = srcA[n];
-    if (ci.ynyq) a.y = -a.y;
-    float2 b = nyq ? srcB[n] : make_float2(0.f, 0.f);
-    if (CUBIC) {
-      HA[n] = a;
-      HB[n] = b;
-    } else {
-      const float sc = __ldg(d.invpht + n);
-      const int pos = wrap(n - nc, Mt);
-      HA[pos] = cscale(a, sc);
-      HB[pos] = cscale(b, sc);
-    }
-  }
-  if (!CUBIC) {
-    for (int u = tid; u < Mt - Nt; u += nthr) {
-      HA[Nt - nc + u] = make_float2(0.f, 0.f);
-      HB[Nt - nc + u] = make_float2(0.f, 0.f);
-    }
-  }
-  __syncthreads();
-  const FftPlan &fp = CUBIC ? d.fNt : d.fMt;
-  fft_smem<-1>(HA, 1, 1, fp, d.tw, tid, nthr);
-  if (nyq) fft_smem<-1>(HB, 1, 1, fp, d.tw, tid, nthr);
-
+  const int LB = ner_buf_len(d);
+  float2 *bufA = reinterpret_cast<float2 *>(smem_f4) + (size_t)grp * (2 * LB + Nz);
+  float2 *bufB = bufA + LB;
+  float2 *Fs = bufB + LB;
   const float scale = d.scale;
-  for (int il = tid; il < Nz; il += nthr) {
-    const int l = il - hz;
-    float2 F = make_float2(0.f, 0.f);
-    if (!(l == 0 && (ci.jx != 0 || ci.jy != 0))) {
-      const ff tau = tau_of(d, ci.jx, ci.jy, l);
-      const float wgt = weight_of(d, tau, l) * scale;
-      const bool lnyq = ((Nz & 1) == 0) && (l == -hz);
-      float2 val = CUBIC ? cubic_interp(HA, tau, Nt) : ner_interp<W>(HA, tau, d, ht);
-      if (nyq || lnyq) {
-        const ff tb = lnyq ? ff_neg(tau) : tau;
-        const float2 *Hb = nyq ? HB : HA;
-        const float2 vb = CUBIC ? cubic_interp(Hb, tb, Nt) : ner_interp<W>(Hb, tb, d, ht);
-        val = make_float2(0.5f * (val.x + vb.x), 0.5f * (val.y + vb.y));
+
+  for (int pass = 0; pass < (nyq ? 2 : 1); ++pass) {
+    const float2 *src = d.G1 + ((size_t)(pass == 0 ? ci.rowA : ci.rowB) * nY1 + iy) * Nt;
+    const bool cj = (pass == 0) && ci.ynyq;
+    for (int n = t; n < Nt; n += G) {
+      float2 a = src[n];
+      if (cj) a.y = -a.y;
+      if (CUBIC) {
+        bufA[n] = a;
+      } else {
+        bufA[wrap(n - nc, Mt)] = cscale(a, __ldg(d.invpht + n));
       }
-      F = cscale(val, wgt);
     }
-    Fs[wrap(l, Nz)] = F;
+    if (!CUBIC)
+      for (int u = t; u < Mt - Nt; u += G) bufA[Nt - nc + u] = make_float2(0.f, 0.f);
+    group_sync(bar, G);
+    const float2 *H = fft_pingpong<-1>(bufA, bufB, CUBIC ? d.fNt : d.fMt, d.tw, t, G, bar);
+#pragma unroll 1
+    for (int il = t; il < Nz; il += G) {
+      const int l = il - hz;
+      float2 F = make_float2(0.f, 0.f);
+      if (!(l == 0 && (ci.jx != 0 || ci.jy != 0))) {
+        const ff tau = tau_of(d, ci.jx, ci.jy, l);
+        const float wgt = weight_of(d, tau, l) * scale;
+        const bool lnyq = ((Nz & 1) == 0) && (l == -hz);
+        // the second evaluation point: -tau on the depth Nyquist (single
+        // source), or the same tau for the B source of a Nyquist column
+        const bool two = !nyq && lnyq;
+        const ff tp = (nyq && pass == 1 && lnyq) ? ff_neg(tau) : tau;
+        float2 v = CUBIC ? cubic_interp(H, tp, Nt) : ner_interp<W>(H, tp, d, ht);
+        if (two) {
+          const ff tb = ff_neg(tau);
+          const float2 vb = CUBIC ? cubic_interp(H, tb, Nt) : ner_interp<W>(H, tb, d, ht);
+          v = cadd(v, vb);
+        }
+        F = cscale(v, (nyq || two) ? 0.5f * wgt : wgt);
+      }
+      const int pos = wrap(l, Nz);
+      Fs[pos] = pass == 0 ? F : cadd(Fs[pos], F);
+    }
+    group_sync(bar, G);
   }
-  __syncthreads();
-  fft_smem<+1>(Fs, 1, 1, d.fNz, d.tw, tid, nthr);
+  const float2 *R = fft_pingpong<+1>(Fs, bufA, d.fNz, d.tw, t, G, bar);
   float2 *dst = d.Fz + ((size_t)ix * nY1 + iy) * Nz;
-  for (int z = tid; z < Nz; z += nthr) dst[z] = Fs[z];
-}
-
-// Adjoint of one column: Fz cotangent -> A' (in HA) and B' (in HB), the
-// cotangents of the two G1 sources of the column, before the final
-// 1/phihat and un-centring (done by the caller).
-template <int W>
-__device__ void ner_adj_column(const InstDesc &d, const HornerTable &ht, const ColInfo &ci, int ix, int iy,
-                               float2 *HA, float2 *HB, float2 *Fs, int tid, int nthr) {
-  const int Mt = d.Mt, Nz = d.Nz, nY1 = d.nY1, hz = d.hz;
-  const bool nyq = ci.xnyq || ci.ynyq;
-  const float2 *src = d.Fz + ((size_t)ix * nY1 + iy) * Nz;
-  for (int z = tid; z < Nz; z += nthr) Fs[z] = src[z];
-  for (int p = tid; p < Mt; p += nthr) {
-    HA[p] = make_float2(0.f, 0.f);
-    HB[p] = make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  fft_smem<-1>(Fs, 1, 1, d.fNz, d.tw, tid, nthr);
-  const float scale = d.scale;
-  for (int il = tid; il < Nz; il += nthr) {
-    const int l = il - hz;
-    if (l == 0 && (ci.jx != 0 || ci.jy != 0)) continue;
-    const ff tau = tau_of(d, ci.jx, ci.jy, l);
-    const float wgt = weight_of(d, tau, l) * scale;
-    const bool lnyq = ((Nz & 1) == 0) && (l == -hz);
-    const float2 v = cscale(Fs[wrap(l, Nz)], wgt);
-    if (!nyq && !lnyq) {
-      ner_spread<W>(HA, tau, v, d, ht);
-    } else {
-      const float2 hv = cscale(v, 0.5f);
-      ner_spread<W>(HA, tau, hv, d, ht);
-      ner_spread<W>(nyq ? HB : HA, lnyq ? ff_neg(tau) : tau, hv, d, ht);
-    }
-  }
-  __syncthreads();
-  fft_smem<+1>(HA, 1, 1, d.fMt, d.tw, tid, nthr);
-  if (nyq) fft_smem<+1>(HB, 1, 1, d.fMt, d.tw, tid, nthr);
+  for (int z = t; z < Nz; z += G) dst[z] = R[z];
 }
 
 // Cotangent sample n of a transformed column (un-centre, 1/phihat).
@@ -274,86 +250,139 @@ __device__ __forceinline__ float2 adj_sample(const InstDesc &d, const float2 *H,
   return cscale(H[wrap(n - d.nc, d.Mt)], __ldg(d.invpht + n));
 }
 
-// Work items: every column of the rows jy < hy (all rows when Ny is odd) on
-// its own, then, for even Ny, the Nyquist row jy = hy in pairs {g, -g}
-// because both columns of a pair read the same two G1 sources.
+// Adjoint NER: Fz cotangent -> DFT over depth -> transposed weight and
+// window (spread in shared memory) -> inverse FFT -> un-centre, 1/phihat ->
+// G1.  Work items: every column off the y-Nyquist row jy = hy (all rows when
+// Ny is odd), then for even Ny the Nyquist row in pairs {g, -g}: both columns
+// of a pair read the same two G1 sources, so one group computes the four
+// contributions in turn and stores, then adds, into the two G1 rows.
 template <int W>
-__global__ void __launch_bounds__(kThreadsNer) k_ner_adj(const InstDesc *__restrict__ descs,
-                                                         const int2 *__restrict__ work,
-                                                         const __grid_constant__ HornerTable ht) {
+__global__ void __launch_bounds__(kThreadsNer, 3) k_ner_adj(const InstDesc *__restrict__ descs,
+                                                            const int2 *__restrict__ work,
+                                                            const __grid_constant__ HornerTable ht) {
   extern __shared__ float4 smem_f4[];
   int inst, tile;
   block_work(work, inst, tile);
   const InstDesc &d = descs[inst];
-  const int Nt = d.Nt, Mt = d.Mt, Nz = d.Nz, nY1 = d.nY1, hx = d.hx, hy = d.hy;
+  const int G = ner_group(d);
+  const int ngrp = blockDim.x / G;
+  const int grp = threadIdx.x / G, t = threadIdx.x % G, bar = 1 + grp;
+  const int Nt = d.Nt, Mt = d.Mt, Nz = d.Nz, nY1 = d.nY1, hz = d.hz, hx = d.hx, hy = d.hy;
   const bool ny_even = (d.Ny & 1) == 0;
   const int reg_rows = ny_even ? nY1 - 1 : nY1;
   const int nreg = d.Nx * reg_rows;
   const int npair = ny_even ? hx + 1 : 0;
-  if (tile >= nreg + npair) return;
-  float2 *H = reinterpret_cast<float2 *>(smem_f4);  // 4 arrays of Mt, then Fs
-  float2 *Fs = H + 4 * (size_t)Mt;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  float2 *G1 = d.G1;
+  // the y-Nyquist pairs take four passes each: schedule them first
+  const int slot = tile * ngrp + grp;
+  if (slot >= nreg + npair) return;
+  const int item = slot < npair ? nreg + slot : slot - npair;
+  const int LB = ner_buf_len(d);
+  float2 *bufA = reinterpret_cast<float2 *>(smem_f4) + (size_t)grp * (2 * LB + Nz);
+  float2 *bufB = bufA + LB;
+  float2 *Fs = bufB + LB;
+  const float scale = d.scale;
 
-  if (tile < nreg) {
-    const int ix = tile / reg_rows, iy = tile % reg_rows;
-    const ColInfo ci = col_info(d, ix - hx, iy);
-    ner_adj_column<W>(d, ht, ci, ix, iy, H, H + Mt, Fs, tid, nthr);
-    float2 *dA = G1 + ((size_t)ci.rowA * nY1 + iy) * Nt;
-    float2 *dB = G1 + ((size_t)ci.rowB * nY1 + iy) * Nt;
-    for (int n = tid; n < Nt; n += nthr) {
-      dA[n] = adj_sample(d, H, n);
-      if (ci.xnyq) dB[n] = adj_sample(d, H + Mt, n);
-    }
-    return;
-  }
-  // Nyquist row, pair {g, -g}
-  const int g = tile - nreg;
-  const int iy = hy;
-  const bool x_even = (d.Nx & 1) == 0;
-  const bool single_zero = (g == 0);
-  const bool single_nyq = x_even && (g == hx);
-  // first column: jx = g (or -hx for the even-Nx end), second: jx = -g
-  const int jx0 = single_nyq ? -hx : g;
-  {
-    const ColInfo ci = col_info(d, jx0, iy);
-    ner_adj_column<W>(d, ht, ci, jx0 + hx, iy, H, H + Mt, Fs, tid, nthr);
-  }
-  if (!single_zero && !single_nyq) {
-    const ColInfo ci = col_info(d, -g, iy);
-    ner_adj_column<W>(d, ht, ci, -g + hx, iy, H + 2 * Mt, H + 3 * Mt, Fs, tid, nthr);
-  }
-  // A' of column jx goes (conjugated) to row -jx, B' to row flip(jx).
-  for (int n = tid; n < Nt; n += nthr) {
-    const float2 A0 = adj_sample(d, H, n), B0 = adj_sample(d, H + Mt, n);
-    if (single_zero) {
-      G1[((size_t)hx * nY1 + iy) * Nt + n] = cadd(cconj(A0), B0);
-    } else if (single_nyq) {
-      G1[((size_t)(2 * hx) * nY1 + iy) * Nt + n] = cadd(cconj(A0), B0);
-      G1[((size_t)0 * nY1 + iy) * Nt + n] = make_float2(0.f, 0.f);
+  // columns handled by this item (one, or a pair on the y-Nyquist row)
+  int jxs[2], ncol, iy;
+  bool zero_row0 = false;
+  if (item < nreg) {
+    jxs[0] = item / reg_rows - hx;
+    iy = item % reg_rows;
+    ncol = 1;
+  } else {
+    const int g = item - nreg;
+    iy = hy;
+    if (g == 0) {
+      jxs[0] = 0;
+      ncol = 1;
+    } else if ((d.Nx & 1) == 0 && g == hx) {
+      jxs[0] = -hx;
+      ncol = 1;
+      zero_row0 = true;  // G1 row jx = -hx is read by no column of this row
     } else {
-      const float2 A1 = adj_sample(d, H + 2 * Mt, n), B1 = adj_sample(d, H + 3 * Mt, n);
-      // column g: A0 -> row -g, B0 -> row g; column -g: A1 -> row g, B1 -> row -g
-      G1[((size_t)(g + hx) * nY1 + iy) * Nt + n] = cadd(cconj(A1), B0);
-      G1[((size_t)(-g + hx) * nY1 + iy) * Nt + n] = cadd(cconj(A0), B1);
+      jxs[0] = g;
+      jxs[1] = -g;
+      ncol = 2;
     }
   }
-  (void)Nz;
+  // rows written so far by this item (to store first, then accumulate)
+  int written[4];
+  int nwritten = 0;
+  for (int c = 0; c < ncol; ++c) {
+    const ColInfo ci = col_info(d, jxs[c], iy);
+    const bool nyq = ci.xnyq || ci.ynyq;
+    const float2 *src = d.Fz + ((size_t)(jxs[c] + hx) * nY1 + iy) * Nz;
+    for (int z = t; z < Nz; z += G) Fs[z] = src[z];
+    group_sync(bar, G);
+    const float2 *Fr = fft_pingpong<-1>(Fs, bufB, d.fNz, d.tw, t, G, bar);
+    if (Fr != Fs) {  // keep the depth spectrum in Fs: both H buffers are needed below
+      for (int z = t; z < Nz; z += G) Fs[z] = Fr[z];
+      group_sync(bar, G);
+    }
+    for (int pass = 0; pass < (nyq ? 2 : 1); ++pass) {
+      for (int p = t; p < Mt; p += G) bufA[p] = make_float2(0.f, 0.f);
+      group_sync(bar, G);
+#pragma unroll 1
+      for (int il = t; il < Nz; il += G) {
+        const int l = il - hz;
+        if (l == 0 && (ci.jx != 0 || ci.jy != 0)) continue;
+        const ff tau = tau_of(d, ci.jx, ci.jy, l);
+        const float wgt = weight_of(d, tau, l) * scale;
+        const bool lnyq = ((Nz & 1) == 0) && (l == -hz);
+        const float2 v = cscale(Fs[wrap(l, Nz)], wgt);
+        if (!nyq) {
+          if (!lnyq) {
+            ner_spread<W>(bufA, tau, v, d, ht);
+          } else {
+            const float2 hv = cscale(v, 0.5f);
+            ner_spread<W>(bufA, tau, hv, d, ht);
+            ner_spread<W>(bufA, ff_neg(tau), hv, d, ht);
+          }
+        } else {
+          ner_spread<W>(bufA, (pass == 1 && lnyq) ? ff_neg(tau) : tau, cscale(v, 0.5f), d, ht);
+        }
+      }
+      group_sync(bar, G);
+      const float2 *H = fft_pingpong<+1>(bufA, bufB, d.fMt, d.tw, t, G, bar);
+      // the A source of a y-Nyquist column is the conjugate of its G1 row
+      const int row = pass == 0 ? ci.rowA : ci.rowB;
+      const bool cj = (pass == 0) && ci.ynyq;
+      bool first = true;
+      for (int k = 0; k < nwritten; ++k) first = first && (written[k] != row);
+      float2 *dst = d.G1 + ((size_t)row * nY1 + iy) * Nt;
+      for (int n = t; n < Nt; n += G) {
+        float2 v = adj_sample(d, H, n);
+        if (cj) v.y = -v.y;
+        dst[n] = first ? v : cadd(dst[n], v);
+      }
+      if (first) written[nwritten++] = row;
+      group_sync(bar, G);
+    }
+  }
+  if (zero_row0) {
+    float2 *dst = d.G1 + ((size_t)0 * nY1 + iy) * Nt;
+    for (int n = t; n < Nt; n += G) dst[n] = make_float2(0.f, 0.f);
+  }
 }
 
 }  // namespace
 
-int blocks_ner(const InstDesc &d) { return d.Nx * d.nY1; }
+int blocks_ner(const InstDesc &d) {
+  const int ngrp = kThreadsNer / d.ner_group;
+  return (d.Nx * d.nY1 + ngrp - 1) / ngrp;
+}
 size_t smem_ner(const InstDesc &d) {
-  const int L = d.Mt > d.Nt ? d.Mt : d.Nt;
-  return (2 * (size_t)L + d.Nz) * sizeof(float2);
+  return (size_t)(kThreadsNer / d.ner_group) * (2 * ner_buf_len(d) + d.Nz) * sizeof(float2);
 }
 int blocks_ner_adj(const InstDesc &d) {
+  const int ngrp = kThreadsNer / d.ner_group;
   const bool ny_even = (d.Ny & 1) == 0;
-  return d.Nx * (ny_even ? d.nY1 - 1 : d.nY1) + (ny_even ? d.hx + 1 : 0);
+  const int items = d.Nx * (ny_even ? d.nY1 - 1 : d.nY1) + (ny_even ? d.hx + 1 : 0);
+  return (items + ngrp - 1) / ngrp;
 }
-size_t smem_ner_adj(const InstDesc &d) { return (4 * (size_t)d.Mt + d.Nz) * sizeof(float2); }
+size_t smem_ner_adj(const InstDesc &d) {
+  return (size_t)(kThreadsNer / d.ner_group) * (2 * ner_buf_len(d) + d.Nz) * sizeof(float2);
+}
 
 template <typename K>
 static cudaError_t set_smem_ner(K kernel, size_t smem) {
@@ -362,9 +391,9 @@ static cudaError_t set_smem_ner(K kernel, size_t smem) {
 }
 
 template <int W>
-static cudaError_t launch_ner_w(const Launch &L, const HornerTable &ht, bool adjoint) {
+static cudaError_t launch_ner_w(const Launch &L, const HornerTable &ht, int which) {
   cudaError_t e;
-  if (adjoint) {
+  if (which == 1) {
     e = set_smem_ner(k_ner_adj<W>, L.smem);
     if (e != cudaSuccess) return e;
     k_ner_adj<W><<<L.nblocks, kThreadsNer, L.smem, L.stream>>>(L.descs, L.work, ht);
@@ -377,11 +406,15 @@ static cudaError_t launch_ner_w(const Launch &L, const HornerTable &ht, bool adj
 }
 
 cudaError_t launch_ner(const Launch &L, int width, const HornerTable &ht, bool adjoint) {
+  return launch_ner_stage(L, width, ht, adjoint ? 1 : 0);
+}
+
+cudaError_t launch_ner_stage(const Launch &L, int width, const HornerTable &ht, int which) {
   switch (width) {
-    case 6: return launch_ner_w<6>(L, ht, adjoint);
-    case 8: return launch_ner_w<8>(L, ht, adjoint);
-    case 12: return launch_ner_w<12>(L, ht, adjoint);
-    case 16: return launch_ner_w<16>(L, ht, adjoint);
+    case 6: return launch_ner_w<6>(L, ht, which);
+    case 8: return launch_ner_w<8>(L, ht, which);
+    case 12: return launch_ner_w<12>(L, ht, which);
+    case 16: return launch_ner_w<16>(L, ht, which);
     default: return cudaErrorInvalidValue;
   }
 }

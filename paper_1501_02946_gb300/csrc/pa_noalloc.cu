@@ -65,7 +65,7 @@ extern "C" int pa_position_grad_noalloc(pa_plan *plan, const float *g_dev, const
   if (need > kPartials)
     return pa::set_error(PA_ERR_UNSUPPORTED_SIZE,
                          ("pa_position_grad_noalloc: needs " + std::to_string(need) +
-                          " gradient partials (ceil(n_t/8) * n_sensors), the static limit is " +
+                          " gradient partials (ceil(n_t/32) * n_sensors), the static limit is " +
                           std::to_string(kPartials))
                              .c_str());
   int dev = 0;
@@ -100,10 +100,14 @@ extern "C" int pa_position_grad_noalloc(pa_plan *plan, const float *g_dev, const
   if ((rc = launched(pa::launch_imgx(L, true), "imgx_adj")) != PA_OK) return rc;
   L.nblocks = pa::blocks_ner_adj(h);
   L.smem = pa::smem_ner_adj(h);
-  if ((rc = launched(pa::launch_ner(L, v.width, *v.ht, true), "ner_adj")) != PA_OK) return rc;
+  if ((rc = launched(pa::launch_ner_stage(L, v.width, *v.ht, 1), "ner_adj")) != PA_OK) return rc;
+
   L.nblocks = pa::blocks_colfft(h);
   L.smem = pa::smem_colfft(h);
   if ((rc = launched(pa::launch_colfft(L, true), "colfft_adj")) != PA_OK) return rc;
+  L.nblocks = pa::blocks_rowifft(h);
+  L.smem = pa::smem_rowifft(h);
+  if ((rc = launched(pa::launch_rowifft(L), "rowifft")) != PA_OK) return rc;
   L.nblocks = pa::blocks_interp(h);
   L.smem = pa::smem_interp(h);
   if ((rc = launched(pa::launch_interp_width(L, v.width, true), "interp")) != PA_OK) return rc;

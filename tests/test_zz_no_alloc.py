@@ -62,10 +62,10 @@ def test_noalloc_gradient_rejects_problems_beyond_its_array(lib):
     import paper_1501_02946_gb300 as pa
     rng = np.random.default_rng(4)
     grid = (64, 64, 16, 1e-4, 1e-4, 1e-4)
-    M = 300000                                   # ceil(64/8) * M > 2^21 partials
+    M, nt = 70000, 1024                          # ceil(1024/32) * M > 2^21 partials
     xy = rng.uniform(-3.2e-3, 3.2e-3, size=(M, 2))
-    plan = pa.Plan(xy, 64, 20e-9, 1500.0, grid)
-    g = torch.zeros((M, 64), device="cuda")
+    plan = pa.Plan(xy, nt, 20e-9, 1500.0, grid)
+    g = torch.zeros((M, nt), device="cuda")
     fb = torch.zeros(grid[:3], device="cuda")
     gxy = torch.zeros((M, 2), device="cuda")
     stream = c_void_p(torch.cuda.current_stream().cuda_stream)
