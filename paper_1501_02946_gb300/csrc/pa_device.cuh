@@ -304,10 +304,15 @@ __device__ void fft_smem(float2 *buf, int estride, int nb, const FftPlan &fp, co
 #undef PA_FFT_RUN
 }
 
-// Out-of-place variant for single sequences (element stride 1): each stage
-// reads `src` and writes `dst` one butterfly at a time, so a thread holds only
-// R values at once; the buffers swap after every stage.  Returns the buffer
-// that holds the result (src or dst).
+// Out-of-place variant for single sequences stored with pad32 indexing: each
+// stage reads `src` and writes `dst` one butterfly at a time, so a thread
+// holds only R values at once; the buffers swap after every stage.  Returns
+// the buffer that holds the result (src or dst).
+// Shared-memory index with one pad element after every 32, which spreads the
+// strided Stockham writes over the banks.
+__host__ __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
+__host__ __device__ __forceinline__ int padded_len(int L) { return L + (L >> 5) + 1; }
+
 template <int R, int DIR>
 __device__ __forceinline__ void fft_stage_oop(const float2 *src, float2 *dst, int L, int Ns,
                                               const float2 *__restrict__ tw, int tid, int nthr) {
@@ -319,7 +324,7 @@ __device__ __forceinline__ void fft_stage_oop(const float2 *src, float2 *dst, in
     float2 v[R];
 #pragma unroll
     for (int t = 0; t < R; ++t) {
-      float2 x = src[j + t * nj];
+      float2 x = src[pad32(j + t * nj)];
       if (t > 0 && k > 0) {
         float2 w = __ldg(tw + t * k * twstep);
         if (DIR > 0) w.y = -w.y;
@@ -330,7 +335,7 @@ __device__ __forceinline__ void fft_stage_oop(const float2 *src, float2 *dst, in
     Dft<R, DIR>::run(v);
     const int o = (j / Ns) * Ns * R + k;
 #pragma unroll
-    for (int t = 0; t < R; ++t) dst[o + t * Ns] = v[t];
+    for (int t = 0; t < R; ++t) dst[pad32(o + t * Ns)] = v[t];
   }
 }
 
@@ -361,6 +366,25 @@ __device__ float2 *fft_pingpong(float2 *a, float2 *b, const FftPlan &fp, const f
   PA_FFT_OOP(7)
 #undef PA_FFT_OOP
   return src;
+}
+
+// n items moved by the block with U loads in flight per thread: every thread
+// first issues up to U independent loads ld(i), then stores them st(i, v).
+template <int U, typename T, typename LoadF, typename StoreF>
+__device__ __forceinline__ void copy_unrolled(int n, int tid, int nthr, LoadF ld, StoreF st) {
+  for (int base = tid; base < n; base += nthr * U) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * nthr;
+      if (i < n) v[u] = ld(i);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * nthr;
+      if (i < n) st(i, v[u]);
+    }
+  }
 }
 
 // Instance and tile of this block.

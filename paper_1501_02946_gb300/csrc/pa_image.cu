@@ -40,12 +40,17 @@ __global__ void __launch_bounds__(kThreadsImg) k_imgx(const InstDesc *__restrict
   const int tid = threadIdx.x, nthr = blockDim.x;
   const float2 *src = ADJ ? d.U : d.Fz;
   float2 *dst = ADJ ? d.Fz : d.U;
-  for (int idx = tid; idx < Nx * ZC; idx += nthr) {
-    const int zz = idx % ZC, a = idx / ZC;
-    const int z = z0 + zz;
-    const int m = wrap(a - hx, Nx);
-    buf[m * ZC + zz] = z < Nz ? src[((size_t)a * nY1 + iy) * Nz + z] : make_float2(0.f, 0.f);
-  }
+  copy_unrolled<8, float2>(
+      Nx * ZC, tid, nthr,
+      [&](int idx) {
+        const int zz = idx % ZC, a = idx / ZC;
+        const int z = z0 + zz;
+        return z < Nz ? src[((size_t)a * nY1 + iy) * Nz + z] : make_float2(0.f, 0.f);
+      },
+      [&](int idx, float2 v) {
+        const int zz = idx % ZC, a = idx / ZC;
+        buf[wrap(a - hx, Nx) * ZC + zz] = v;
+      });
   __syncthreads();
   if (ADJ) {
     fft_smem<-1>(buf, ZC, ZC, d.fNx, d.tw, tid, nthr);
@@ -81,31 +86,26 @@ __global__ void __launch_bounds__(kThreadsImg) k_imgy(const InstDesc *__restrict
   const IoPtrs io = io_of_img(io0, io_table, inst);
   const bool ny_even = (Ny & 1) == 0;
   if (!ADJ) {
-    for (int idx = tid; idx < Ny * ZP; idx += nthr) {
-      const int zp = idx % ZP, m = idx / ZP;
-      const int za = z0 + 2 * zp, zb = za + 1;
-      int jy;
-      bool upper;
-      if (m <= hy) {
-        jy = m;
-        upper = false;
-      } else {
-        jy = Ny - m;
-        upper = true;
-      }
-      const float2 *col = d.U + ((size_t)x * nY1 + jy) * Nz;
-      const float2 Ya = za < Nz ? col[za] : make_float2(0.f, 0.f);
-      const float2 Yb = zb < Nz ? col[zb] : make_float2(0.f, 0.f);
-      float2 S;
-      if (jy == 0 || (ny_even && jy == hy)) {
-        S = make_float2(Ya.x, Yb.x);
-      } else if (!upper) {
-        S = make_float2(Ya.x - Yb.y, Ya.y + Yb.x);
-      } else {
-        S = make_float2(Ya.x + Yb.y, Yb.x - Ya.y);
-      }
-      buf[m * ZP + zp] = S;
-    }
+    // one (jy, depth pair) item reads two samples and fills bins jy and Ny - jy
+    copy_unrolled<8, float4>(
+        nY1 * ZP, tid, nthr,
+        [&](int idx) {
+          const int zp = idx % ZP, jy = idx / ZP;
+          const int za = z0 + 2 * zp, zb = za + 1;
+          const float2 *col = d.U + ((size_t)x * nY1 + jy) * Nz;
+          const float2 Ya = za < Nz ? col[za] : make_float2(0.f, 0.f);
+          const float2 Yb = zb < Nz ? col[zb] : make_float2(0.f, 0.f);
+          return make_float4(Ya.x, Ya.y, Yb.x, Yb.y);
+        },
+        [&](int idx, float4 ab) {
+          const int zp = idx % ZP, jy = idx / ZP;
+          if (jy == 0 || (ny_even && jy == hy)) {
+            buf[jy * ZP + zp] = make_float2(ab.x, ab.z);
+          } else {
+            buf[jy * ZP + zp] = make_float2(ab.x - ab.w, ab.y + ab.z);
+            buf[(Ny - jy) * ZP + zp] = make_float2(ab.x + ab.w, ab.z - ab.y);
+          }
+        });
     __syncthreads();
     fft_smem<+1>(buf, ZP, ZP, d.fNy, d.tw, tid, nthr);
     for (int idx = tid; idx < Ny * 2 * ZP; idx += nthr) {
@@ -116,14 +116,18 @@ __global__ void __launch_bounds__(kThreadsImg) k_imgy(const InstDesc *__restrict
       if (z < Nz) io.f_out[((size_t)x * Ny + y) * Nz + z] = (zz & 1) ? v.y : v.x;
     }
   } else {
-    for (int idx = tid; idx < Ny * ZP; idx += nthr) {
-      const int zp = idx % ZP, y = idx / ZP;
-      const int za = z0 + 2 * zp, zb = za + 1;
-      const float *row = io.f_in + ((size_t)x * Ny + y) * Nz;
-      const float fa = za < Nz ? row[za] : 0.f;
-      const float fb = zb < Nz ? row[zb] : 0.f;
-      buf[wrap(y - hy, Ny) * ZP + zp] = make_float2(fa, fb);
-    }
+    copy_unrolled<8, float2>(
+        Ny * ZP, tid, nthr,
+        [&](int idx) {
+          const int zp = idx % ZP, y = idx / ZP;
+          const int za = z0 + 2 * zp, zb = za + 1;
+          const float *row = io.f_in + ((size_t)x * Ny + y) * Nz;
+          return make_float2(za < Nz ? row[za] : 0.f, zb < Nz ? row[zb] : 0.f);
+        },
+        [&](int idx, float2 v) {
+          const int zp = idx % ZP, y = idx / ZP;
+          buf[wrap(y - hy, Ny) * ZP + zp] = v;
+        });
     __syncthreads();
     fft_smem<-1>(buf, ZP, ZP, d.fNy, d.tw, tid, nthr);
     for (int idx = tid; idx < nY1 * 2 * ZP; idx += nthr) {

@@ -205,26 +205,31 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 1)
   // stage the slots of this (strip, half)
   const int sbase = __ldg(d.cl_slot_start + key);
   const int ns = __ldg(d.cl_slot_start + key + 1) - sbase;
-  for (int i = tid; i < ns; i += nthr) {
-    s_meta[i] = d.cl_meta[sbase + i];
-    s_wx[i] = __ldg(d.cl_wx + sbase + i);
-  }
-  for (int i = tid; i < ns * W; i += nthr) s_wy[i] = __ldg(d.cl_wy + (size_t)sbase * W + i);
+  copy_unrolled<4, int2>(
+      ns, tid, nthr, [&](int i) { return d.cl_meta[sbase + i]; }, [&](int i, int2 v) { s_meta[i] = v; });
+  copy_unrolled<4, float4>(
+      ns, tid, nthr, [&](int i) { return __ldg(d.cl_wx + sbase + i); }, [&](int i, float4 v) { s_wx[i] = v; });
+  copy_unrolled<8, float>(
+      ns * W, tid, nthr, [&](int i) { return __ldg(d.cl_wy + (size_t)sbase * W + i); },
+      [&](int i, float v) { s_wy[i] = v; });
   __syncthreads();
   const bool pair_ok = (Nt & 1) == 0;
-  for (int i = tid; i < ns * NCP; i += nthr) {
-    const int slot = i / NCP, kk = i % NCP;
-    const int n = n0 + 2 * kk;
-    const float *row = g + (size_t)s_meta[slot].x * Nt;
-    float2 v;
-    if (pair_ok && n + 1 < Nt) {
-      v = __ldg(reinterpret_cast<const float2 *>(row + n));
-    } else {
-      v.x = n < Nt ? __ldg(row + n) : 0.f;
-      v.y = n + 1 < Nt ? __ldg(row + n + 1) : 0.f;
-    }
-    s_g[i] = v;
-  }
+  copy_unrolled<8, float2>(
+      ns * NCP, tid, nthr,
+      [&](int i) {
+        const int slot = i / NCP, kk = i % NCP;
+        const int n = n0 + 2 * kk;
+        const float *row = g + (size_t)s_meta[slot].x * Nt;
+        float2 v;
+        if (pair_ok && n + 1 < Nt) {
+          v = __ldg(reinterpret_cast<const float2 *>(row + n));
+        } else {
+          v.x = n < Nt ? __ldg(row + n) : 0.f;
+          v.y = n + 1 < Nt ? __ldg(row + n + 1) : 0.f;
+        }
+        return v;
+      },
+      [&](int i, float2 v) { s_g[i] = v; });
   __syncthreads();
 
   float2 acc[GPW][P];
@@ -355,11 +360,15 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft(const InstDesc *__restri
   const int n0 = (tile / nY1) * NC;
   const int tid = threadIdx.x, nthr = blockDim.x;
   if (!ADJ) {
-    for (int idx = tid; idx < Mx * NC; idx += nthr) {
-      const int kk = idx % NC, p = idx / NC;
-      const int n = n0 + kk;
-      buf[idx] = n < Nt ? d.T[((size_t)p * nY1 + jy) * Nt + n] : make_float2(0.f, 0.f);
-    }
+    const float2 *Tsrc = d.T + (size_t)jy * Nt + n0;
+    const size_t pstride = (size_t)nY1 * Nt;
+    copy_unrolled<8, float2>(
+        Mx * NC, tid, nthr,
+        [&](int idx) {
+          const int kk = idx % NC, p = idx / NC;
+          return n0 + kk < Nt ? Tsrc[p * pstride + kk] : make_float2(0.f, 0.f);
+        },
+        [&](int idx, float2 v) { buf[idx] = v; });
     __syncthreads();
     fft_smem<-1>(buf, NC, NC, d.fMx, d.tw, tid, nthr);
     for (int idx = tid; idx < nX1 * NC; idx += nthr) {
@@ -373,13 +382,18 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft(const InstDesc *__restri
   } else {
     for (int idx = tid; idx < Mx * NC; idx += nthr) buf[idx] = make_float2(0.f, 0.f);
     __syncthreads();
-    for (int idx = tid; idx < nX1 * NC; idx += nthr) {
-      const int kk = idx % NC, ix = idx / NC;
-      const int n = n0 + kk;
-      const int b = wrap(ix - hx, Mx);
-      buf[b * NC + kk] = n < Nt ? cscale(d.G1[((size_t)ix * nY1 + jy) * Nt + n], __ldg(d.invphx + ix))
-                                : make_float2(0.f, 0.f);
-    }
+    copy_unrolled<8, float2>(
+        nX1 * NC, tid, nthr,
+        [&](int idx) {
+          const int kk = idx % NC, ix = idx / NC;
+          const int n = n0 + kk;
+          return n < Nt ? cscale(d.G1[((size_t)ix * nY1 + jy) * Nt + n], __ldg(d.invphx + ix))
+                        : make_float2(0.f, 0.f);
+        },
+        [&](int idx, float2 v) {
+          const int kk = idx % NC, ix = idx / NC;
+          buf[wrap(ix - hx, Mx) * NC + kk] = v;
+        });
     __syncthreads();
     fft_smem<+1>(buf, NC, NC, d.fMx, d.tw, tid, nthr);
     for (int idx = tid; idx < Mx * NC; idx += nthr) {
@@ -412,33 +426,29 @@ __global__ void __launch_bounds__(kThreadsCol) k_rowifft(const InstDesc *__restr
   const int n0 = (tile / Mx) * 2 * NCP;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const float2 *Trow = d.T + (size_t)p * nY1 * Nt;
-  for (int idx = tid; idx < My * NCP; idx += nthr) {
-    const int kk = idx % NCP, q = idx / NCP;
-    float2 v = make_float2(0.f, 0.f);
-    int jy = -1;
-    bool lower = true;
-    if (q <= hy) {
-      jy = q;
-    } else if (q >= My - hy) {
-      jy = My - q;
-      lower = false;
-    }
-    if (jy >= 0) {
-      const int n = n0 + 2 * kk;
-      const float sc = __ldg(d.invphy + jy);
-      const float2 *src = Trow + (size_t)jy * Nt;
-      const float2 a = n < Nt ? cscale(src[n], sc) : make_float2(0.f, 0.f);
-      const float2 b = n + 1 < Nt ? cscale(src[n + 1], sc) : make_float2(0.f, 0.f);
-      if (jy == 0) {
-        v = make_float2(a.x, b.x);
-      } else if (lower) {
-        v = make_float2(0.5f * (a.x - b.y), 0.5f * (a.y + b.x));
-      } else {
-        v = make_float2(0.5f * (a.x + b.y), 0.5f * (b.x - a.y));
-      }
-    }
-    S[idx] = v;
-  }
+  for (int idx = tid; idx < My * NCP; idx += nthr) S[idx] = make_float2(0.f, 0.f);
+  __syncthreads();
+  // one (jy, pair) item reads two samples and fills bins jy and My - jy
+  copy_unrolled<8, float4>(
+      nY1 * NCP, tid, nthr,
+      [&](int idx) {
+        const int kk = idx % NCP, jy = idx / NCP;
+        const int n = n0 + 2 * kk;
+        const float sc = __ldg(d.invphy + jy);
+        const float2 *src = Trow + (size_t)jy * Nt;
+        const float2 a = n < Nt ? cscale(src[n], sc) : make_float2(0.f, 0.f);
+        const float2 b = n + 1 < Nt ? cscale(src[n + 1], sc) : make_float2(0.f, 0.f);
+        return make_float4(a.x, a.y, b.x, b.y);
+      },
+      [&](int idx, float4 ab) {
+        const int kk = idx % NCP, jy = idx / NCP;
+        if (jy == 0) {
+          S[kk] = make_float2(ab.x, ab.z);
+        } else {
+          S[jy * NCP + kk] = make_float2(0.5f * (ab.x - ab.w), 0.5f * (ab.y + ab.z));
+          S[(My - jy) * NCP + kk] = make_float2(0.5f * (ab.x + ab.w), 0.5f * (ab.z - ab.y));
+        }
+      });
   __syncthreads();
   fft_smem<+1>(S, NCP, NCP, d.fMy, d.tw, tid, nthr);
   float *G0 = d.G0 + (size_t)p * My * Nt;
@@ -501,23 +511,27 @@ __global__ void __launch_bounds__(kThreadsInterp) k_interp(const InstDesc *__res
   }
   // G0b tile with halo, 128-byte rows of 32 samples
   const float *G0 = d.G0;
-  for (int idx = tid; idx < HX * HY * (NC / 4); idx += nthr) {
-    const int v4 = idx % (NC / 4), cell = idx / (NC / 4);
-    const int hr = cell / HY, hc = cell % HY;
-    const int p = wrap(p0 - W / 2 + 1 + hr, Mx), q = wrap(q0 - W / 2 + 1 + hc, My);
-    const int n = n0 + 4 * v4;
-    const float *src = G0 + ((size_t)p * My + q) * Nt + n;
-    float4 v;
-    if (n + 3 < Nt && (Nt & 3) == 0) {
-      v = __ldg(reinterpret_cast<const float4 *>(src));
-    } else {
-      v.x = n < Nt ? __ldg(src) : 0.f;
-      v.y = n + 1 < Nt ? __ldg(src + 1) : 0.f;
-      v.z = n + 2 < Nt ? __ldg(src + 2) : 0.f;
-      v.w = n + 3 < Nt ? __ldg(src + 3) : 0.f;
-    }
-    reinterpret_cast<float4 *>(Gs)[idx] = v;
-  }
+  const bool vec4 = (Nt & 3) == 0;
+  copy_unrolled<8, float4>(
+      HX * HY * (NC / 4), tid, nthr,
+      [&](int idx) {
+        const int v4 = idx % (NC / 4), cell = idx / (NC / 4);
+        const int hr = cell / HY, hc = cell % HY;
+        const int p = wrap(p0 - W / 2 + 1 + hr, Mx), q = wrap(q0 - W / 2 + 1 + hc, My);
+        const int n = n0 + 4 * v4;
+        const float *src = G0 + ((size_t)p * My + q) * Nt + n;
+        float4 v;
+        if (vec4 && n + 3 < Nt) {
+          v = __ldg(reinterpret_cast<const float4 *>(src));
+        } else {
+          v.x = n < Nt ? __ldg(src) : 0.f;
+          v.y = n + 1 < Nt ? __ldg(src + 1) : 0.f;
+          v.z = n + 2 < Nt ? __ldg(src + 2) : 0.f;
+          v.w = n + 3 < Nt ? __ldg(src + 3) : 0.f;
+        }
+        return v;
+      },
+      [&](int idx, float4 v) { reinterpret_cast<float4 *>(Gs)[idx] = v; });
   __syncthreads();
   const int ns = row_pref[TX];
   const int n = n0 + lane;

@@ -93,7 +93,7 @@ __device__ __forceinline__ float2 ner_interp(const float2 *H, ff tau, const Inst
   const int Mt = d.Mt;
 #pragma unroll
   for (int t = 0; t < W; ++t) {
-    const float2 h = H[idx];
+    const float2 h = H[pad32(idx)];
     acc.x = fmaf(wt[t], h.x, acc.x);
     acc.y = fmaf(wt[t], h.y, acc.y);
     idx = (idx + 1 == Mt) ? 0 : idx + 1;
@@ -114,8 +114,8 @@ __device__ __forceinline__ void ner_spread(float2 *H, ff tau, float2 v, const In
   const int Mt = d.Mt;
 #pragma unroll
   for (int t = 0; t < W; ++t) {
-    atomicAdd(&H[idx].x, wt[t] * vv.x);
-    atomicAdd(&H[idx].y, wt[t] * vv.y);
+    atomicAdd(&H[pad32(idx)].x, wt[t] * vv.x);
+    atomicAdd(&H[pad32(idx)].y, wt[t] * vv.y);
     idx = (idx + 1 == Mt) ? 0 : idx + 1;
   }
 }
@@ -136,7 +136,7 @@ __device__ __forceinline__ float2 cubic_interp(const float2 *H, ff tau, int Nt) 
   int idx = p0;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
-    const float2 h = H[idx];
+    const float2 h = H[pad32(idx)];
     acc.x = fmaf(wt[t], h.x, acc.x);
     acc.y = fmaf(wt[t], h.y, acc.y);
     idx = (idx + 1 == Nt) ? 0 : idx + 1;
@@ -167,7 +167,7 @@ __device__ __forceinline__ int ner_group(const InstDesc &d) { return d.ner_group
 // Length of each of the two ping-pong buffers of a column.
 __host__ __device__ __forceinline__ int ner_buf_len(const InstDesc &d) {
   int L = d.Mt > d.Nt ? d.Mt : d.Nt;
-  return L > d.Nz ? L : d.Nz;
+  return padded_len(L > d.Nz ? L : d.Nz);
 }
 
 // Forward NER: a group of G threads (G = 64/128/256, named barrier 1 + group
@@ -194,7 +194,8 @@ __global__ void __launch_bounds__(kThreadsNer, 3) k_ner(const InstDesc *__restri
   const ColInfo ci = col_info(d, ix - d.hx, iy);
   const bool nyq = ci.xnyq || ci.ynyq;
   const int LB = ner_buf_len(d);
-  float2 *bufA = reinterpret_cast<float2 *>(smem_f4) + (size_t)grp * (2 * LB + Nz);
+  const int LZ = padded_len(Nz);
+  float2 *bufA = reinterpret_cast<float2 *>(smem_f4) + (size_t)grp * (2 * LB + LZ);
   float2 *bufB = bufA + LB;
   float2 *Fs = bufB + LB;
   const float scale = d.scale;
@@ -202,17 +203,16 @@ __global__ void __launch_bounds__(kThreadsNer, 3) k_ner(const InstDesc *__restri
   for (int pass = 0; pass < (nyq ? 2 : 1); ++pass) {
     const float2 *src = d.G1 + ((size_t)(pass == 0 ? ci.rowA : ci.rowB) * nY1 + iy) * Nt;
     const bool cj = (pass == 0) && ci.ynyq;
-    for (int n = t; n < Nt; n += G) {
-      float2 a = src[n];
-      if (cj) a.y = -a.y;
-      if (CUBIC) {
-        bufA[n] = a;
-      } else {
-        bufA[wrap(n - nc, Mt)] = cscale(a, __ldg(d.invpht + n));
-      }
-    }
+    copy_unrolled<4, float2>(
+        Nt, t, G,
+        [&](int n) {
+          float2 a = src[n];
+          if (cj) a.y = -a.y;
+          return CUBIC ? a : cscale(a, __ldg(d.invpht + n));
+        },
+        [&](int n, float2 a) { bufA[pad32(CUBIC ? n : wrap(n - nc, Mt))] = a; });
     if (!CUBIC)
-      for (int u = t; u < Mt - Nt; u += G) bufA[Nt - nc + u] = make_float2(0.f, 0.f);
+      for (int u = t; u < Mt - Nt; u += G) bufA[pad32(Nt - nc + u)] = make_float2(0.f, 0.f);
     group_sync(bar, G);
     const float2 *H = fft_pingpong<-1>(bufA, bufB, CUBIC ? d.fNt : d.fMt, d.tw, t, G, bar);
 #pragma unroll 1
@@ -235,19 +235,19 @@ __global__ void __launch_bounds__(kThreadsNer, 3) k_ner(const InstDesc *__restri
         }
         F = cscale(v, (nyq || two) ? 0.5f * wgt : wgt);
       }
-      const int pos = wrap(l, Nz);
+      const int pos = pad32(wrap(l, Nz));
       Fs[pos] = pass == 0 ? F : cadd(Fs[pos], F);
     }
     group_sync(bar, G);
   }
   const float2 *R = fft_pingpong<+1>(Fs, bufA, d.fNz, d.tw, t, G, bar);
   float2 *dst = d.Fz + ((size_t)ix * nY1 + iy) * Nz;
-  for (int z = t; z < Nz; z += G) dst[z] = R[z];
+  for (int z = t; z < Nz; z += G) dst[z] = R[pad32(z)];
 }
 
 // Cotangent sample n of a transformed column (un-centre, 1/phihat).
 __device__ __forceinline__ float2 adj_sample(const InstDesc &d, const float2 *H, int n) {
-  return cscale(H[wrap(n - d.nc, d.Mt)], __ldg(d.invpht + n));
+  return cscale(H[pad32(wrap(n - d.nc, d.Mt))], __ldg(d.invpht + n));
 }
 
 // Adjoint NER: Fz cotangent -> DFT over depth -> transposed weight and
@@ -277,7 +277,8 @@ __global__ void __launch_bounds__(kThreadsNer, 3) k_ner_adj(const InstDesc *__re
   if (slot >= nreg + npair) return;
   const int item = slot < npair ? nreg + slot : slot - npair;
   const int LB = ner_buf_len(d);
-  float2 *bufA = reinterpret_cast<float2 *>(smem_f4) + (size_t)grp * (2 * LB + Nz);
+  const int LZ = padded_len(Nz);
+  float2 *bufA = reinterpret_cast<float2 *>(smem_f4) + (size_t)grp * (2 * LB + LZ);
   float2 *bufB = bufA + LB;
   float2 *Fs = bufB + LB;
   const float scale = d.scale;
@@ -312,15 +313,16 @@ __global__ void __launch_bounds__(kThreadsNer, 3) k_ner_adj(const InstDesc *__re
     const ColInfo ci = col_info(d, jxs[c], iy);
     const bool nyq = ci.xnyq || ci.ynyq;
     const float2 *src = d.Fz + ((size_t)(jxs[c] + hx) * nY1 + iy) * Nz;
-    for (int z = t; z < Nz; z += G) Fs[z] = src[z];
+    copy_unrolled<4, float2>(
+        Nz, t, G, [&](int z) { return src[z]; }, [&](int z, float2 v) { Fs[pad32(z)] = v; });
     group_sync(bar, G);
     const float2 *Fr = fft_pingpong<-1>(Fs, bufB, d.fNz, d.tw, t, G, bar);
     if (Fr != Fs) {  // keep the depth spectrum in Fs: both H buffers are needed below
-      for (int z = t; z < Nz; z += G) Fs[z] = Fr[z];
+      for (int z = t; z < Nz; z += G) Fs[pad32(z)] = Fr[pad32(z)];
       group_sync(bar, G);
     }
     for (int pass = 0; pass < (nyq ? 2 : 1); ++pass) {
-      for (int p = t; p < Mt; p += G) bufA[p] = make_float2(0.f, 0.f);
+      for (int p = t; p < padded_len(Mt); p += G) bufA[p] = make_float2(0.f, 0.f);
       group_sync(bar, G);
 #pragma unroll 1
       for (int il = t; il < Nz; il += G) {
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(kThreadsNer, 3) k_ner_adj(const InstDesc *__re
         const ff tau = tau_of(d, ci.jx, ci.jy, l);
         const float wgt = weight_of(d, tau, l) * scale;
         const bool lnyq = ((Nz & 1) == 0) && (l == -hz);
-        const float2 v = cscale(Fs[wrap(l, Nz)], wgt);
+        const float2 v = cscale(Fs[pad32(wrap(l, Nz))], wgt);
         if (!nyq) {
           if (!lnyq) {
             ner_spread<W>(bufA, tau, v, d, ht);
@@ -372,7 +374,7 @@ int blocks_ner(const InstDesc &d) {
   return (d.Nx * d.nY1 + ngrp - 1) / ngrp;
 }
 size_t smem_ner(const InstDesc &d) {
-  return (size_t)(kThreadsNer / d.ner_group) * (2 * ner_buf_len(d) + d.Nz) * sizeof(float2);
+  return (size_t)(kThreadsNer / d.ner_group) * (2 * ner_buf_len(d) + padded_len(d.Nz)) * sizeof(float2);
 }
 int blocks_ner_adj(const InstDesc &d) {
   const int ngrp = kThreadsNer / d.ner_group;
@@ -381,7 +383,7 @@ int blocks_ner_adj(const InstDesc &d) {
   return (items + ngrp - 1) / ngrp;
 }
 size_t smem_ner_adj(const InstDesc &d) {
-  return (size_t)(kThreadsNer / d.ner_group) * (2 * ner_buf_len(d) + d.Nz) * sizeof(float2);
+  return (size_t)(kThreadsNer / d.ner_group) * (2 * ner_buf_len(d) + padded_len(d.Nz)) * sizeof(float2);
 }
 
 template <typename K>
