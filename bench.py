@@ -34,7 +34,7 @@ METRIC = "voxels/s (NEDNER-NUFFT fwd+adjoint, FP32, ≤1e-4 rel L2 vs FP64) and 
 UNIT = "voxels/s"
 WORKLOAD = ("128x128 non-equispaced sensors over 12.8 mm (8192 jittered lattice + 8192 centre-dense), "
             "512 samples at 20 ns, 20 balls + 1% noise, output 128x128x256 at 100 um, sigma 2, width 8")
-STAGES = ["ned_spread_rowfft", "ned_colfft", "ner_fused", "image_x", "image_y_c2r", "image_y_adj",
+STAGES = ["ned_spread", "ned_rowfft", "ned_colfft", "ner_fused", "image_x", "image_y_c2r", "image_y_adj",
           "image_x_adj", "ner_adj", "ned_colfft_adj", "ned_rowifft", "ned_interp"]
 
 
@@ -48,10 +48,11 @@ def stage_bytes(M, Nt, Nx, Ny, Nz, sigma=2):
     G1 = 8 * nX1 * nY1 * Nt
     F = 8 * Nx * nY1 * Nz
     f = 4 * Nx * Ny * Nz
-    return {"ned_spread_rowfft": g + T, "ned_colfft": T + G1, "ner_fused": G1 + F, "image_x": 2 * F,
+    G0 = 4 * Mx * (sigma * Ny) * Nt
+    return {"ned_spread": g + G0, "ned_rowfft": G0 + T, "ned_colfft": T + G1, "ner_fused": G1 + F, "image_x": 2 * F,
             "image_y_c2r": F + f, "image_y_adj": f + F, "image_x_adj": 2 * F, "ner_adj": F + G1,
-            "ned_colfft_adj": G1 + T, "ned_rowifft": T + 4 * Mx * (sigma * Ny) * Nt,
-            "ned_interp": 4 * Mx * (sigma * Ny) * Nt + g}
+            "ned_colfft_adj": G1 + T, "ned_rowifft": T + G0,
+            "ned_interp": G0 + g}
 
 
 def pipeline_min_bytes(M, Nt, Nx, Ny, Nz):

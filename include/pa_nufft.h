@@ -206,7 +206,7 @@ int pa_plan_buffer(const pa_plan *plan, int which, void *dst_dev, int64_t capaci
  * and the number of launches since the last read, and clears them.
  * Stages: see pa_profile_stage_name (0 .. PA_PROFILE_STAGES-1).
  */
-#define PA_PROFILE_STAGES 13
+#define PA_PROFILE_STAGES 14
 int pa_profile_enable(pa_plan *plan, int enable);
 int pa_profile_read(pa_plan *plan, double *ms_total, int64_t *launches);
 const char *pa_profile_stage_name(int stage);

@@ -197,7 +197,9 @@ class Plan:
         """{stage name: (total ms, launches)} since the last read (waits for
         the recorded events)."""
         lib = _lib.load()
-        n = 13
+        n = 0
+        while lib.pa_profile_stage_name(n):  # names run out after the last stage
+            n += 1
         ms = (ctypes.c_double * n)()
         cnt = (ctypes.c_int64 * n)()
         check(lib.pa_profile_read(self.handle, ms, cnt))

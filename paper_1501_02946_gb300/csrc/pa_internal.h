@@ -44,7 +44,7 @@ struct InstDesc {
   int nchunk_adj;       // n-chunks of the adjoint NED kernel (gradient partials)
   int ner_group;        // threads per column in the NER kernels (64, 128 or 256)
 
-  FftPlan fMy, fMx, fMt, fNz, fNx, fNy, fNt, fMyh;  // fMyh: length My/2
+  FftPlan fMy, fMx, fMt, fNz, fNx, fNy, fNt;
   const float2 *tw;
 
   // sensors sorted by (bx, by); taps t = 0..w-1 cover cells base - w/2 + 1 + t
@@ -53,27 +53,14 @@ struct InstDesc {
   const float *wx, *wy; // [M][w]; wy carries a_m = h_m/(dx dy)
   const float *dwx, *dwy;  // [M][w] derivative taps d/dx_m and d/dy_m
   const int *cell_start;   // [Mx*My + 1] CSR offsets of the sorted sensors per cell
-  // forward spread visits: for strip s (kSpreadP grid rows) and q-group g
-  // (kSpreadQG columns), visits visit_start[s*NG+g] .. visit_start[s*NG+g+1]-1
-  // with NG = ceil(My / kSpreadQG); each visit is a sensor (caller index vm)
-  // and its tap products vprod[v*kSpreadQG + qi] = (row 0..3) for column qi.
-  const int *visit_start;
-  const int *vm;
-  const float4 *vprod;
-  // cluster spread (two blocks per strip, each half of the q range): for key
-  // = strip*2 + half, slots cl_slot_start[key] .. cl_slot_start[key+1]-1 are
-  // the sensors whose footprint meets the strip rows and the half's columns
-  // (caller index and base column in cl_meta, the strip rows' x taps in
-  // cl_wx, the y taps in cl_wy[slot*w + t]); q-group g of the half (QG
-  // columns) visits the slots cl_vslot[cl_vstart[key*NGH+g] ..] (local to key).
-  const int *cl_slot_start;
-  const int2 *cl_meta;
-  const float4 *cl_wx;
-  const float *cl_wy;
-  const int *cl_vstart;
-  const int *cl_vslot;
-  int cl_smax;          // most slots of any (strip, half)
-  int spread_mode;      // 0: one block per strip, 1: cluster of two
+  // forward spread entries: strip s (kSpreadP grid rows p0 = s*kSpreadP ..)
+  // and column q own the entries sp_start[s*My + q] .. sp_start[s*My + q + 1]-1;
+  // entry e is a sensor (caller index sp_m[e]) with its tap products
+  // sp_w[e] = wy(q) * (wx(p0), wx(p0+1), wx(p0+2), wx(p0+3)), zero off the
+  // footprint.  Within a list the sensors follow the sorted (cell) order.
+  const int *sp_start;
+  const int *sp_m;
+  const float4 *sp_w;
   // deconvolution factors 1/phihat (window normalised to phi(0) = 1)
   const float *invphx;  // [nX1], jx = ix - hx, at jx / Mx
   const float *invphy;  // [nY1], jy, at jy / My
@@ -95,7 +82,7 @@ struct InstDesc {
   float2 *Fz;           // [Nx][nY1][Nz]   after NER and the inverse depth DFT
   float2 *U;            // [Nx][nY1][Nz]   after the inverse x DFT
   float2 *grad_part;    // [nchunk_adj][M] per-chunk position-gradient partials
-  float *G0;            // [Mx][My][Nt] real oversampled-grid cotangent (adjoint)
+  float *G0;            // [Mx][My][Nt] real oversampled grid (forward) or its cotangent (adjoint)
   int *status;
 };
 
@@ -110,10 +97,7 @@ struct IoPtrs {
 };
 
 // Tile shapes (chosen on the host; kernels are templated on them).
-constexpr int kSpreadP = 4;      // oversampled rows per forward NED strip
-constexpr int kSpreadNCP = 8;    // complex pairs of samples per forward strip
-constexpr int kSpreadGPW = 8;    // q-groups per warp
-constexpr int kSpreadQG = 32 / kSpreadNCP;  // grid columns per lane group
+constexpr int kSpreadP = 4;      // oversampled rows per forward spread strip
 constexpr int kColNC = 16;       // samples per column-FFT tile
 constexpr int kInterpNC = 32;    // samples per adjoint interpolation tile
 constexpr int kImgZC = 16;       // depth samples per inverse-x tile
@@ -132,11 +116,10 @@ struct Launch {
 };
 
 // Block counts and shared-memory sizes per stage for one instance.
-int blocks_spread(const InstDesc &d);
-size_t smem_spread(const InstDesc &d);
-int threads_spread(const InstDesc &d);
-size_t smem_spread_cluster(const InstDesc &d);
-int threads_spread_cluster(const InstDesc &d);
+int spread_spl(const InstDesc &d);  // samples per lane of the spread (4 or 8)
+int blocks_spread(const InstDesc &d, int spl);
+int blocks_rowfft(const InstDesc &d);
+size_t smem_rowfft(const InstDesc &d);
 int blocks_colfft(const InstDesc &d);
 size_t smem_colfft(const InstDesc &d);
 int blocks_ner(const InstDesc &d);
@@ -152,8 +135,8 @@ size_t smem_interp(const InstDesc &d);
 int blocks_rowifft(const InstDesc &d);
 size_t smem_rowifft(const InstDesc &d);
 
-cudaError_t launch_spread(const Launch &L, int threads);
-cudaError_t launch_spread_cluster(const Launch &L, int threads, int width);
+cudaError_t launch_spread(const Launch &L, int spl);
+cudaError_t launch_rowfft(const Launch &L);
 cudaError_t launch_colfft(const Launch &L, bool adjoint);
 cudaError_t launch_ner(const Launch &L, int width, const HornerTable &ht, bool adjoint);
 // which: 0 forward, 1 adjoint

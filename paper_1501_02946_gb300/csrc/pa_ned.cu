@@ -1,29 +1,23 @@
-// pa_ned.cu -- NED-NUFFT stage (eq:NED_NUFFT, Sec. 3) on sm_103a.
+// pa_ned.cu -- NED-NUFFT stage (the spatial type-1 NUFFT of Sec. 3) on sm_103a.
 //
 // Forward:  g[m][n] --spread--> G0[p][q][n] (real, oversampled sigma*nx x
 // sigma*ny grid) --FFT over q, keep jy = 0..hy--> T[p][jy][n] --FFT over p,
 // keep jx = -hx..hx, divide by phihat--> G1[jx][jy][n].
-//   k_spread_rowfft  spreads one strip of P grid rows x (2*NCP) samples in
-//                    registers (no atomics: each warp owns cells and gathers
-//                    the sensors that touch them), then runs the row FFT of
-//                    the strip in shared memory; G0 never reaches HBM.
-//   k_colfft         column FFT + truncation + deconvolution (and its adjoint).
-// Adjoint:  the exact transposes, fused into k_rowifft_interp, which rebuilds
-// the G0 cotangent rows a sensor strip needs (with a halo of w-1 rows) by an
-// inverse row FFT in shared memory and interpolates at the sensors, and
-// optionally accumulates the sensor-position gradient through the window
-// derivative.
-#include <cooperative_groups.h>
-
+//   k_spread    gather-form spread (sparse x dense), sums in registers.
+//   k_rowfft    row FFT over q of two samples at once, deconvolution in y.
+//   k_colfft    column FFT + truncation + deconvolution (and its adjoint).
+// Adjoint:  the exact transposes: k_colfft<true>, k_rowifft (inverse row
+// FFT back to the G0 cotangent) and k_interp (interpolation at the sensors,
+// optionally with the sensor-position gradient through the window
+// derivative).
 #include "pa_device.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace pa {
 
 namespace {
 
 constexpr int kThreadsCol = 256;
+constexpr int kThreadsSpread = 256;  // 8 warps = 8 grid columns of one strip
 constexpr int kThreadsInterp = 256;
 
 __device__ __forceinline__ IoPtrs io_of(const IoPtrs &io, const IoPtrs *table, int inst) {
@@ -31,310 +25,181 @@ __device__ __forceinline__ IoPtrs io_of(const IoPtrs &io, const IoPtrs *table, i
 }
 
 // ------------------------------------------------------------------ spread
-// One tile: a strip of P oversampled grid rows x 2*NCP samples.  Warp w owns
-// the q-groups w*GPW .. w*GPW+GPW-1 (QG columns each); lane (qi, k) owns
-// column qi of the group and the sample pair k for all P rows, in registers.
-// It streams the group's visits (precomputed by the plan: caller index of the
-// sensor and the tap products for its QG columns x P rows) and reads the
-// sample pair straight from g (L2-resident), so the accumulation needs no
-// shared memory and no barrier.  The strip is then FFT'd over q in shared
-// memory (float2 [My][P][NCP], element stride P*NCP) and written as T.
-template <int P, int NCP, int GPW>
-__global__ void __launch_bounds__(512, 1) k_spread_rowfft(const InstDesc *__restrict__ descs,
-                                                        const int2 *__restrict__ work, IoPtrs io0,
-                                                        const IoPtrs *__restrict__ io_table) {
-  constexpr int QG = 32 / NCP;  // q columns per lane group
-  static_assert(P == 4, "visit products hold four rows");
-  extern __shared__ float4 smem_f4[];
+// Gather form of the forward spread, a sparse-times-dense product:
+//   G0[p][q][n] = sum_e sp_w[e][p - p0] * g[sp_m[e]][n]
+// over the entries e of (strip p0 / P, column q), where sp_w holds the tap
+// products wy(q) wx(p) of the sensor for the strip's P rows.  A warp owns one
+// column of one strip and lane l the S consecutive samples n0 + l*S ..; an
+// entry costs two warp-uniform loads (caller index, four products) and S/4
+// vector loads of g for 4*S FMAs, and the P x S sums stay in registers (no
+// shared memory, no atomics, no barrier).  The warps of a block own
+// neighbouring columns of the same strip, which walk nearly the same sensors
+// in the same order, so their reads of g mostly hit in L1.
+template <int S>
+__device__ __forceinline__ void load_samples(const float *__restrict__ row, int n, int Nt, bool vec, float (&v)[S]) {
+  if (vec) {
+#pragma unroll
+    for (int u = 0; u < S / 4; ++u) {
+      const float4 t = __ldg(reinterpret_cast<const float4 *>(row + n) + u);
+      v[4 * u] = t.x;
+      v[4 * u + 1] = t.y;
+      v[4 * u + 2] = t.z;
+      v[4 * u + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < S; ++u) v[u] = n + u < Nt ? __ldg(row + n + u) : 0.f;
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void fma_entry(float (&acc)[kSpreadP][S], const float4 &w, const float (&v)[S]) {
+#pragma unroll
+  for (int u = 0; u < S; ++u) {
+    acc[0][u] = fmaf(w.x, v[u], acc[0][u]);
+    acc[1][u] = fmaf(w.y, v[u], acc[1][u]);
+    acc[2][u] = fmaf(w.z, v[u], acc[2][u]);
+    acc[3][u] = fmaf(w.w, v[u], acc[3][u]);
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreadsSpread, 2) k_spread(const InstDesc *__restrict__ descs,
+                                                              const int2 *__restrict__ work, IoPtrs io0,
+                                                              const IoPtrs *__restrict__ io_table) {
+  constexpr int P = kSpreadP, QC = kThreadsSpread / 32, CH = 32 * S;
+  static_assert(P == 4, "tap products hold four rows");
+  static_assert(S % 4 == 0, "samples per lane load as float4");
   int inst, tile;
   block_work(work, inst, tile);
   const InstDesc &d = descs[inst];
   const int Mx = d.Mx, My = d.My, Nt = d.Nt;
-  const int nstrips = (Mx + P - 1) / P;
-  const int nchunks = (Nt + 2 * NCP - 1) / (2 * NCP);
-  if (tile >= nstrips * nchunks) return;
-  const int s = tile % nstrips;
-  const int c = tile / nstrips;
-  const int p0 = s * P;
-  const int n0 = c * 2 * NCP;
+  const int nstrips = (Mx + P - 1) / P, ncb = (My + QC - 1) / QC, nch = (Nt + CH - 1) / CH;
+  if (tile >= nstrips * ncb * nch) return;
+  const int st = tile % nstrips;
+  const int cb = (tile / nstrips) % ncb;
+  const int c = tile / (nstrips * ncb);
+  const int q = cb * QC + (threadIdx.x >> 5);
+  if (q >= My) return;  // whole warps leave; the kernel has no block barrier
+  const int lane = threadIdx.x & 31;
+  const int p0 = st * P;
+  const int n = c * CH + lane * S;
   const IoPtrs io = io_of(io0, io_table, inst);
   const float *__restrict__ g = io.g_in;
-  float2 *strip = reinterpret_cast<float2 *>(smem_f4);
+  const bool rows16 = (Nt & 3) == 0;
+  const bool vec = rows16 && ((reinterpret_cast<uintptr_t>(g) & 15u) == 0) && (n + S <= Nt);
+  const int *__restrict__ em = d.sp_m;
+  const float4 *__restrict__ ew = d.sp_w;
+  const int e0 = __ldg(d.sp_start + (size_t)st * My + q), e1 = __ldg(d.sp_start + (size_t)st * My + q + 1);
 
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  const int qi = lane / NCP, k = lane % NCP;
-  const int n = n0 + 2 * k;
-  const bool pair_ok = ((Nt & 1) == 0) && (n + 1 < Nt);
-  const int NG = (My + QG - 1) / QG;
-  const int *__restrict__ vstart = d.visit_start + (size_t)s * NG;
-  const int *__restrict__ vm = d.vm;
-  const float4 *__restrict__ vprod = d.vprod;
+  float acc[P][S];
+#pragma unroll
+  for (int r = 0; r < P; ++r)
+#pragma unroll
+    for (int u = 0; u < S; ++u) acc[r][u] = 0.f;
 
-  float2 acc[GPW][P];
+  constexpr int B = 4;  // entries in flight per warp
+  int e = e0;
+  for (; e + B <= e1; e += B) {
+    int m[B];
+    float4 w[B];
+    float v[B][S];
 #pragma unroll
-  for (int gi = 0; gi < GPW; ++gi)
-#pragma unroll
-    for (int r = 0; r < P; ++r) acc[gi][r] = make_float2(0.f, 0.f);
-
-#pragma unroll
-  for (int gi = 0; gi < GPW; ++gi) {
-    const int grp = warp * GPW + gi;
-    if (grp < NG) {
-      const int v0 = __ldg(vstart + grp), v1 = __ldg(vstart + grp + 1);
-#pragma unroll 4
-      for (int v = v0; v < v1; ++v) {
-        const int m = __ldg(vm + v);
-        const float4 pr = __ldg(vprod + (size_t)v * QG + qi);
-        const float *row = g + (size_t)m * Nt;
-        float2 gv;
-        if (pair_ok) {
-          gv = __ldg(reinterpret_cast<const float2 *>(row + n));
-        } else {
-          gv.x = n < Nt ? __ldg(row + n) : 0.f;
-          gv.y = n + 1 < Nt ? __ldg(row + n + 1) : 0.f;
-        }
-        acc[gi][0].x = fmaf(pr.x, gv.x, acc[gi][0].x);
-        acc[gi][0].y = fmaf(pr.x, gv.y, acc[gi][0].y);
-        acc[gi][1].x = fmaf(pr.y, gv.x, acc[gi][1].x);
-        acc[gi][1].y = fmaf(pr.y, gv.y, acc[gi][1].y);
-        acc[gi][2].x = fmaf(pr.z, gv.x, acc[gi][2].x);
-        acc[gi][2].y = fmaf(pr.z, gv.y, acc[gi][2].y);
-        acc[gi][3].x = fmaf(pr.w, gv.x, acc[gi][3].x);
-        acc[gi][3].y = fmaf(pr.w, gv.y, acc[gi][3].y);
-      }
+    for (int b = 0; b < B; ++b) {
+      m[b] = __ldg(em + e + b);
+      w[b] = __ldg(ew + e + b);
     }
-  }
-  // the strip rows in shared memory, layout [q][r][k]; every q < My is
-  // owned by exactly one lane group
 #pragma unroll
-  for (int gi = 0; gi < GPW; ++gi) {
-    const int q = (warp * GPW + gi) * QG + qi;
-    if (q < My) {
+    for (int b = 0; b < B; ++b) load_samples<S>(g + (size_t)m[b] * Nt, n, Nt, vec, v[b]);
 #pragma unroll
-      for (int r = 0; r < P; ++r) strip[(q * P + r) * NCP + k] = acc[gi][r];
-    }
+    for (int b = 0; b < B; ++b) fma_entry<S>(acc, w[b], v[b]);
   }
-  __syncthreads();
-  // FFT along q of the P*NCP packed sequences (element stride P*NCP)
-  fft_smem<-1>(strip, P * NCP, P * NCP, d.fMy, d.tw, tid, nthr);
-  // unpack the two real transforms, deconvolve in y, write T[p][jy][n]
-  const int nY1 = d.nY1;
-  const int total = P * nY1 * NCP * 2;
-  for (int idx = tid; idx < total; idx += nthr) {
-    const int par = idx & 1;
-    const int kk = (idx >> 1) % NCP;
-    const int rest = (idx >> 1) / NCP;
-    const int jy = rest % nY1;
-    const int r = rest / nY1;
+  for (; e < e1; ++e) {
+    const int m = __ldg(em + e);
+    const float4 w = __ldg(ew + e);
+    float v[S];
+    load_samples<S>(g + (size_t)m * Nt, n, Nt, vec, v);
+    fma_entry<S>(acc, w, v);
+  }
+  if (n >= Nt) return;
+  const bool vst = rows16 && (n + S <= Nt);
+#pragma unroll
+  for (int r = 0; r < P; ++r) {
     const int p = p0 + r;
-    const int nn = n0 + 2 * kk + par;
-    if (p < Mx && nn < Nt) {
-      const float2 Z = strip[(jy * P + r) * NCP + kk];
-      const int jm = jy == 0 ? 0 : My - jy;
-      const float2 Zm = strip[(jm * P + r) * NCP + kk];
-      float2 v;
-      if (par == 0) {
-        v = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
-      } else {
-        v = make_float2(0.5f * (Z.y + Zm.y), -0.5f * (Z.x - Zm.x));
-      }
-      const float sc = __ldg(d.invphy + jy);
-      d.T[((size_t)p * nY1 + jy) * Nt + nn] = cscale(v, sc);
+    if (p >= Mx) break;
+    float *dst = d.G0 + ((size_t)p * My + q) * Nt + n;
+    if (vst) {
+#pragma unroll
+      for (int u = 0; u < S / 4; ++u)
+        reinterpret_cast<float4 *>(dst)[u] =
+            make_float4(acc[r][4 * u], acc[r][4 * u + 1], acc[r][4 * u + 2], acc[r][4 * u + 3]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < S; ++u)
+        if (n + u < Nt) dst[u] = acc[r][u];
     }
   }
 }
 
-// ---------------------------------------------------------- cluster spread
-// A cluster of two blocks owns one strip (P grid rows) and 2*NCP samples; the
-// block of rank h owns the columns [h*My/2, (h+1)*My/2).  Each block stages
-// the sensors whose footprint meets its rows and columns (taps and sample
-// pairs) in shared memory once, then every warp accumulates its q-groups in
-// registers from those staged values (lane = (column qi, sample pair k)).
-// The length-My FFT over q then starts with one radix-2 decimation-in-
-// frequency step across the pair through distributed shared memory
-//   y_h[q] = x[q] + x[q + My/2]               (h = 0)
-//   y_h[q] = (x[q] - x[q + My/2]) W_My^q      (h = 1),
-// after which block h holds, by a local length-My/2 FFT, the bins jy = 2k+h.
-// Bins jy and My - jy have the same parity, so the real-pair unpack and the
-// deconvolution stay local.
-template <int P, int NCP, int GPW, int W>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 1)
-    k_spread_cl(const InstDesc *__restrict__ descs, const int2 *__restrict__ work, IoPtrs io0,
-                const IoPtrs *__restrict__ io_table) {
-  constexpr int QG = 32 / NCP;
-  static_assert(P == 4, "staged x taps hold four rows");
+// Row transform of the spread grid, the transpose of k_rowifft:
+//   T[p][jy][n] = (1/phihat_y(jy)) sum_q G0[p][q][n] exp(-2 pi i jy q / My),  jy = 0..hy,
+// two real samples per complex FFT (n in the real part, n + 1 in the
+// imaginary part), separated afterwards through the Hermitian symmetry.
+template <int NCP>
+__global__ void __launch_bounds__(kThreadsCol) k_rowfft(const InstDesc *__restrict__ descs,
+                                                        const int2 *__restrict__ work) {
   extern __shared__ float4 smem_f4[];
-  cg::cluster_group cluster = cg::this_cluster();
-  const int h = int(cluster.block_rank());
+  float2 *S = reinterpret_cast<float2 *>(smem_f4);  // [My][NCP]
+  static_assert(NCP % 2 == 0, "pairs load as float4");
   int inst, tile;
-  if (work) {
-    const int2 wv = work[blockIdx.x >> 1];
-    inst = wv.x;
-    tile = wv.y;
-  } else {
-    inst = 0;
-    tile = blockIdx.x >> 1;
-  }
+  block_work(work, inst, tile);
   const InstDesc &d = descs[inst];
-  const int Mx = d.Mx, My = d.My, Nt = d.Nt;
-  const int H = My / 2;
-  const int nstrips = (Mx + P - 1) / P;
+  const int Mx = d.Mx, My = d.My, Nt = d.Nt, nY1 = d.nY1;
   const int nchunks = (Nt + 2 * NCP - 1) / (2 * NCP);
-  if (tile >= nstrips * nchunks) return;  // both blocks of the cluster leave together
-  const int s = tile % nstrips;
-  const int c = tile / nstrips;
-  const int p0 = s * P;
-  const int n0 = c * 2 * NCP;
-  const IoPtrs io = io_of(io0, io_table, inst);
-  const float *__restrict__ g = io.g_in;
-  const int key = s * 2 + h;
-  const int NGH = (H + QG - 1) / QG;
-  const int smax = d.cl_smax;
-
-  float2 *strip = reinterpret_cast<float2 *>(smem_f4);          // [H][P][NCP]
-  float4 *s_wx = reinterpret_cast<float4 *>(strip + (size_t)H * P * NCP);
-  float2 *s_g = reinterpret_cast<float2 *>(s_wx + smax);        // [smax][NCP]
-  int2 *s_meta = reinterpret_cast<int2 *>(s_g + (size_t)smax * NCP);
-  float *s_wy = reinterpret_cast<float *>(s_meta + smax);       // [smax][W]
-
+  if (tile >= Mx * nchunks) return;
+  const int p = tile % Mx;
+  const int n0 = (tile / Mx) * 2 * NCP;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  const int qi = lane / NCP, k = lane % NCP;
-
-  // stage the slots of this (strip, half)
-  const int sbase = __ldg(d.cl_slot_start + key);
-  const int ns = __ldg(d.cl_slot_start + key + 1) - sbase;
-  copy_unrolled<4, int2>(
-      ns, tid, nthr, [&](int i) { return d.cl_meta[sbase + i]; }, [&](int i, int2 v) { s_meta[i] = v; });
-  copy_unrolled<4, float4>(
-      ns, tid, nthr, [&](int i) { return __ldg(d.cl_wx + sbase + i); }, [&](int i, float4 v) { s_wx[i] = v; });
-  copy_unrolled<8, float>(
-      ns * W, tid, nthr, [&](int i) { return __ldg(d.cl_wy + (size_t)sbase * W + i); },
-      [&](int i, float v) { s_wy[i] = v; });
-  __syncthreads();
-  const bool pair_ok = (Nt & 1) == 0;
-  copy_unrolled<8, float2>(
-      ns * NCP, tid, nthr,
-      [&](int i) {
-        const int slot = i / NCP, kk = i % NCP;
-        const int n = n0 + 2 * kk;
-        const float *row = g + (size_t)s_meta[slot].x * Nt;
-        float2 v;
-        if (pair_ok && n + 1 < Nt) {
-          v = __ldg(reinterpret_cast<const float2 *>(row + n));
+  const float *G0 = d.G0 + (size_t)p * My * Nt;
+  const bool vec4 = (Nt & 3) == 0;
+  constexpr int K2 = NCP / 2;
+  copy_unrolled<8, float4>(
+      My * K2, tid, nthr,
+      [&](int idx) {
+        const int k2 = idx % K2, q = idx / K2;
+        const int n = n0 + 4 * k2;
+        const float *src = G0 + (size_t)q * Nt + n;
+        float4 v;
+        if (vec4 && n + 3 < Nt) {
+          v = __ldg(reinterpret_cast<const float4 *>(src));
         } else {
-          v.x = n < Nt ? __ldg(row + n) : 0.f;
-          v.y = n + 1 < Nt ? __ldg(row + n + 1) : 0.f;
+          v.x = n < Nt ? __ldg(src) : 0.f;
+          v.y = n + 1 < Nt ? __ldg(src + 1) : 0.f;
+          v.z = n + 2 < Nt ? __ldg(src + 2) : 0.f;
+          v.w = n + 3 < Nt ? __ldg(src + 3) : 0.f;
         }
         return v;
       },
-      [&](int i, float2 v) { s_g[i] = v; });
+      [&](int idx, float4 v) { reinterpret_cast<float4 *>(S)[idx] = v; });
   __syncthreads();
-
-  float2 acc[GPW][P];
-#pragma unroll
-  for (int gi = 0; gi < GPW; ++gi)
-#pragma unroll
-    for (int r = 0; r < P; ++r) acc[gi][r] = make_float2(0.f, 0.f);
-  const int *__restrict__ vst = d.cl_vstart + (size_t)key * NGH;
-#pragma unroll
-  for (int gi = 0; gi < GPW; ++gi) {
-    const int grp = warp * GPW + gi;
-    if (grp < NGH) {
-      const int ql = grp * QG + qi;       // column within the half
-      const int q = h * H + ql;
-      const bool qok = ql < H;
-      const int v0 = __ldg(vst + grp), v1 = __ldg(vst + grp + 1);
-      for (int vb = v0; vb < v1; vb += 32) {
-        const int mine = vb + lane < v1 ? __ldg(d.cl_vslot + vb + lane) : 0;
-        const int cnt = min(32, v1 - vb);
-#pragma unroll 2
-        for (int j = 0; j < cnt; ++j) {
-          const int slot = __shfl_sync(0xffffffffu, mine, j);
-          int tq = q - s_meta[slot].y + W / 2 - 1;
-          if (tq < 0) tq += My;
-          if (tq >= My) tq -= My;
-          const float wyq = (qok && tq < W) ? s_wy[slot * W + tq] : 0.f;
-          const float4 wx4 = s_wx[slot];
-          const float2 gv = s_g[slot * NCP + k];
-          const float p0w = wyq * wx4.x, p1w = wyq * wx4.y, p2w = wyq * wx4.z, p3w = wyq * wx4.w;
-          acc[gi][0].x = fmaf(p0w, gv.x, acc[gi][0].x);
-          acc[gi][0].y = fmaf(p0w, gv.y, acc[gi][0].y);
-          acc[gi][1].x = fmaf(p1w, gv.x, acc[gi][1].x);
-          acc[gi][1].y = fmaf(p1w, gv.y, acc[gi][1].y);
-          acc[gi][2].x = fmaf(p2w, gv.x, acc[gi][2].x);
-          acc[gi][2].y = fmaf(p2w, gv.y, acc[gi][2].y);
-          acc[gi][3].x = fmaf(p3w, gv.x, acc[gi][3].x);
-          acc[gi][3].y = fmaf(p3w, gv.y, acc[gi][3].y);
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int gi = 0; gi < GPW; ++gi) {
-    const int ql = (warp * GPW + gi) * QG + qi;
-    if (ql < H) {
-#pragma unroll
-      for (int r = 0; r < P; ++r) strip[(ql * P + r) * NCP + k] = acc[gi][r];
-    }
-  }
-  // radix-2 decimation in frequency across the pair
-  cluster.sync();
-  float2 *peer = cluster.map_shared_rank(strip, 1 - h);
-  const float2 *tw = d.tw + d.fMy.tw;
-  constexpr int PER = 16;  // values per thread per round (H*P*NCP / nthr for My = 256)
-  const int total = H * P * NCP;
-  for (int base = 0; base < total; base += nthr * PER) {
-    float2 y[PER];
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-      const int idx = base + j * nthr + tid;
-      if (idx < total) {
-        const float2 mine = strip[idx], other = peer[idx];
-        const float2 a = h == 0 ? mine : other, b = h == 0 ? other : mine;  // x[q], x[q + H]
-        if (h == 0) {
-          y[j] = cadd(a, b);
-        } else {
-          const int ql = idx / (P * NCP);
-          y[j] = cmul(csub(a, b), __ldg(tw + ql));
-        }
-      }
-    }
-    cluster.sync();  // the peer has read this block's values
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-      const int idx = base + j * nthr + tid;
-      if (idx < total) strip[idx] = y[j];
-    }
-    cluster.sync();  // next round reads values untouched by this round's writes
-  }
-  __syncthreads();
-  fft_smem<-1>(strip, P * NCP, P * NCP, d.fMyh, d.tw, tid, nthr);
-  // unpack (bins jy = 2k + h and My - jy live in this block), deconvolve, write
-  const int nY1 = d.nY1;
-  const int nk = (d.hy - h) / 2 + 1;  // jy = 2k + h <= hy
-  const int tot = P * nk * NCP * 2;
-  for (int idx = tid; idx < tot; idx += nthr) {
-    const int par = idx & 1;
-    const int kk = (idx >> 1) % NCP;
-    const int rest = (idx >> 1) / NCP;
-    const int kb = rest % nk;
-    const int r = rest / nk;
-    const int jy = 2 * kb + h;
-    const int p = p0 + r;
-    const int nn = n0 + 2 * kk + par;
-    if (p < Mx && nn < Nt && jy <= d.hy) {
-      const float2 Z = strip[(kb * P + r) * NCP + kk];
-      const int km = h == 0 ? (kb == 0 ? 0 : H - kb) : H - kb - 1;
-      const float2 Zm = strip[(km * P + r) * NCP + kk];
-      float2 v;
-      if (par == 0) {
-        v = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
-      } else {
-        v = make_float2(0.5f * (Z.y + Zm.y), -0.5f * (Z.x - Zm.x));
-      }
-      d.T[((size_t)p * nY1 + jy) * Nt + nn] = cscale(v, __ldg(d.invphy + jy));
+  fft_smem<-1>(S, NCP, NCP, d.fMy, d.tw, tid, nthr);
+  float2 *Trow = d.T + (size_t)p * nY1 * Nt;
+  const bool vst = (Nt & 1) == 0;
+  for (int idx = tid; idx < nY1 * NCP; idx += nthr) {
+    const int k = idx % NCP, jy = idx / NCP;
+    const int n = n0 + 2 * k;
+    if (n >= Nt) continue;
+    const float2 Z = S[jy * NCP + k];
+    const float2 Zm = S[(jy == 0 ? 0 : My - jy) * NCP + k];
+    const float sc = 0.5f * __ldg(d.invphy + jy);
+    const float2 a = make_float2(sc * (Z.x + Zm.x), sc * (Z.y - Zm.y));
+    const float2 b = make_float2(sc * (Z.y + Zm.y), -sc * (Z.x - Zm.x));
+    float2 *dst = Trow + (size_t)jy * Nt + n;
+    if (vst) {
+      *reinterpret_cast<float4 *>(dst) = make_float4(a.x, a.y, b.x, b.y);
+    } else {
+      dst[0] = a;
+      if (n + 1 < Nt) dst[1] = b;
     }
   }
 }
@@ -419,7 +284,7 @@ __global__ void __launch_bounds__(kThreadsCol) k_rowifft(const InstDesc *__restr
   int inst, tile;
   block_work(work, inst, tile);
   const InstDesc &d = descs[inst];
-  const int Mx = d.Mx, My = d.My, Nt = d.Nt, hy = d.hy, nY1 = d.nY1;
+  const int Mx = d.Mx, My = d.My, Nt = d.Nt, nY1 = d.nY1;
   const int nchunks = (Nt + 2 * NCP - 1) / (2 * NCP);
   if (tile >= Mx * nchunks) return;
   const int p = tile % Mx;
@@ -607,28 +472,15 @@ __global__ void k_grad_reduce(const InstDesc *__restrict__ descs, IoPtrs io0, co
 }  // namespace
 
 // ------------------------------------------------------------------ host side
-int threads_spread(const InstDesc &d) {
-  constexpr int QG = 32 / kSpreadNCP;
-  int warps = (d.My + QG * kSpreadGPW - 1) / (QG * kSpreadGPW);
-  if (warps < 8) warps = 8;
-  return warps * 32;
+int spread_spl(const InstDesc &d) { return d.Nt > 128 ? 8 : 4; }
+int blocks_spread(const InstDesc &d, int spl) {
+  constexpr int QC = kThreadsSpread / 32;
+  const int ch = 32 * spl;
+  return ((d.Mx + kSpreadP - 1) / kSpreadP) * ((d.My + QC - 1) / QC) * ((d.Nt + ch - 1) / ch);
 }
-int blocks_spread(const InstDesc &d) {
-  return ((d.Mx + kSpreadP - 1) / kSpreadP) * ((d.Nt + 2 * kSpreadNCP - 1) / (2 * kSpreadNCP));
-}
-size_t smem_spread(const InstDesc &d) { return (size_t)d.My * kSpreadP * kSpreadNCP * sizeof(float2); }
-constexpr int kClGPW = 4;
-int threads_spread_cluster(const InstDesc &d) {
-  const int ngh = (d.My / 2 + kSpreadQG - 1) / kSpreadQG;
-  int warps = (ngh + kClGPW - 1) / kClGPW;
-  if (warps < 8) warps = 8;
-  return warps * 32;
-}
-size_t smem_spread_cluster(const InstDesc &d) {
-  const size_t smax = (size_t)d.cl_smax;
-  return (size_t)(d.My / 2) * kSpreadP * kSpreadNCP * sizeof(float2) + smax * sizeof(float4) +
-         smax * kSpreadNCP * sizeof(float2) + smax * sizeof(int2) + smax * d.w * sizeof(float);
-}
+constexpr int kRowFftNCP = 16;
+int blocks_rowfft(const InstDesc &d) { return d.Mx * ((d.Nt + 2 * kRowFftNCP - 1) / (2 * kRowFftNCP)); }
+size_t smem_rowfft(const InstDesc &d) { return (size_t)d.My * kRowFftNCP * sizeof(float2); }
 int blocks_colfft(const InstDesc &d) { return d.nY1 * ((d.Nt + kColNC - 1) / kColNC); }
 size_t smem_colfft(const InstDesc &d) { return (size_t)d.Mx * kColNC * sizeof(float2); }
 constexpr int kRowIfftNCP = 16;
@@ -650,31 +502,23 @@ static cudaError_t set_smem(K kernel, size_t smem) {
   return cudaSuccess;
 }
 
-cudaError_t launch_spread(const Launch &L, int threads) {
-  auto kern = k_spread_rowfft<kSpreadP, kSpreadNCP, kSpreadGPW>;
-  cudaError_t e = set_smem(kern, L.smem);
-  if (e != cudaSuccess) return e;
-  kern<<<L.nblocks, threads, L.smem, L.stream>>>(L.descs, L.work, L.io, L.io_table);
-  return cudaGetLastError();
-}
-
-template <int W>
-static cudaError_t launch_spread_cl_w(const Launch &L, int threads) {
-  auto kern = k_spread_cl<kSpreadP, kSpreadNCP, kClGPW, W>;
-  cudaError_t e = set_smem(kern, L.smem);
-  if (e != cudaSuccess) return e;
-  kern<<<L.nblocks, threads, L.smem, L.stream>>>(L.descs, L.work, L.io, L.io_table);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_spread_cluster(const Launch &L, int threads, int width) {
-  switch (width) {
-    case 6: return launch_spread_cl_w<6>(L, threads);
-    case 8: return launch_spread_cl_w<8>(L, threads);
-    case 12: return launch_spread_cl_w<12>(L, threads);
-    case 16: return launch_spread_cl_w<16>(L, threads);
-    default: return cudaErrorInvalidValue;
+cudaError_t launch_spread(const Launch &L, int spl) {
+  if (spl == 8) {
+    k_spread<8><<<L.nblocks, kThreadsSpread, 0, L.stream>>>(L.descs, L.work, L.io, L.io_table);
+  } else if (spl == 4) {
+    k_spread<4><<<L.nblocks, kThreadsSpread, 0, L.stream>>>(L.descs, L.work, L.io, L.io_table);
+  } else {
+    return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rowfft(const Launch &L) {
+  auto kern = k_rowfft<kRowFftNCP>;
+  cudaError_t e = set_smem(kern, L.smem);
+  if (e != cudaSuccess) return e;
+  kern<<<L.nblocks, kThreadsCol, L.smem, L.stream>>>(L.descs, L.work);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_colfft(const Launch &L, bool adjoint) {

@@ -195,11 +195,10 @@ struct pa_plan {
   char *d_work = nullptr;
   size_t static_bytes = 0, work_bytes = 0;
   std::vector<double> weights;  // h_m
-  int spread_threads = 256;
   size_t smem_limit = 0;
-  // forward-spread visit lists (device), reallocated when they outgrow it
-  char *d_visits = nullptr;
-  size_t visits_bytes = 0;
+  // forward-spread entry lists (device), reallocated when they outgrow it
+  char *d_entries = nullptr;
+  size_t entries_bytes = 0;
   // optional per-stage event timing
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -215,9 +214,8 @@ struct pa_batch {
     size_t off = 0;
     int nblocks = 0;
     size_t smem = 0;
-  } st_spread, st_col, st_ner, st_imgx, st_imgy;
-  int spread_threads = 256;
-  bool spread_cluster = false;
+  } st_spread, st_rowfft, st_col, st_ner, st_imgx, st_imgy;
+  int spread_spl = 4;
   HornerTable ht{};
   int width = 8;
   cudaGraphExec_t exec = nullptr;
@@ -284,175 +282,84 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
   PA_CUDA(cudaMemcpyAsync((void *)P->h.cell_start, cs.data(), sizeof(int) * cs.size(), cudaMemcpyHostToDevice,
                           stream));
 
-  // Forward-spread visits.  Strip s covers grid rows p0 = s*P .. p0+P-1; a
-  // sensor visits the strip when its w-row footprint meets those rows, and
-  // within the strip each q-group of QG columns its w-column footprint meets.
-  constexpr int P_ = pa::kSpreadP, QG = pa::kSpreadQG;
+  // Forward-spread entries.  Strip st covers grid rows p0 = st*P .. p0+P-1;
+  // a sensor contributes to (st, q) for each column q of its w-column
+  // footprint when its w-row footprint meets the strip, with the tap
+  // products of the strip's rows.  Candidates are the sensors whose base row
+  // lies within P + w - 1 rows of the strip, taken in sorted (cell) order,
+  // so every list follows the same sensor order.
+  constexpr int P_ = pa::kSpreadP;
   const int nstrips = (Mx + P_ - 1) / P_;
-  const int NG = (My + QG - 1) / QG;
-  std::vector<int> vstart(size_t(nstrips) * NG + 1, 0);
   const int nrows = std::min(P_ + w - 1, Mx);
-  auto for_each_visit = [&](auto &&fn) {
+  auto for_each_entry = [&](auto &&fn) {
     for (int st = 0; st < nstrips; ++st) {
       const int p0 = st * P_;
       for (int dr = 0; dr < nrows; ++dr) {
         const int row = ((p0 - w / 2 + dr) % Mx + Mx) % Mx;
         for (int i = cs[size_t(row) * My]; i < cs[size_t(row) * My + My]; ++i) {
-          // groups met by the footprint columns by - w/2 + 1 .. by + w/2 (mod My)
+          float wxr[P_];
+          bool any = false;
+          for (int r = 0; r < P_; ++r) {
+            const int p = p0 + r;
+            const int tx = ((p - sbx[i] + w / 2 - 1) % Mx + Mx) % Mx;
+            wxr[r] = (tx < w && p < Mx) ? wx[size_t(i) * w + tx] : 0.f;
+            any = any || (tx < w && p < Mx);
+          }
+          if (!any) continue;
           const int q0 = sby[i] - w / 2 + 1;
-          int glast = -1;
           for (int t = 0; t < w; ++t) {
             const int q = ((q0 + t) % My + My) % My;
-            const int g = q / QG;
-            if (g == glast) continue;
-            bool seen = false;  // a group met twice (wrap-around) is visited once
-            for (int t2 = 0; t2 < t; ++t2) seen = seen || (((q0 + t2) % My + My) % My) / QG == g;
-            glast = g;
-            if (!seen) fn(st, p0, g, i);
+            fn(st, q, i, wy[size_t(i) * w + t], wxr);
           }
         }
       }
     }
   };
-  for_each_visit([&](int st, int, int g, int) { vstart[size_t(st) * NG + g + 1]++; });
-  for (size_t k = 0; k + 1 < vstart.size(); ++k) vstart[k + 1] += vstart[k];
-  const size_t nvis = size_t(vstart.back());
-  std::vector<int> vm(nvis);
-  std::vector<float4> vprod(nvis * QG);
+  std::vector<int> sp_start(size_t(nstrips) * My + 1, 0);
+  for_each_entry([&](int st, int q, int, float, const float *) { sp_start[size_t(st) * My + q + 1]++; });
+  for (size_t k = 0; k + 1 < sp_start.size(); ++k) sp_start[k + 1] += sp_start[k];
+  const size_t nent = size_t(sp_start.back());
+  std::vector<int> sp_m(nent);
+  std::vector<float4> sp_w(nent);
   {
-    std::vector<int> fillp(vstart.begin(), vstart.end() - 1);
-    for_each_visit([&](int st, int p0, int g, int i) {
-      const size_t v = size_t(fillp[size_t(st) * NG + g]++);
-      vm[v] = perm[i];
-      float wxr[P_];
-      for (int r = 0; r < P_; ++r) {
-        const int p = p0 + r;
-        const int tx = ((p - sbx[i] + w / 2 - 1) % Mx + Mx) % Mx;
-        wxr[r] = (tx < w && p < Mx) ? wx[size_t(i) * w + tx] : 0.f;
-      }
-      for (int qi = 0; qi < QG; ++qi) {
-        const int q = g * QG + qi;
-        const int ty = ((q - sby[i] + w / 2 - 1) % My + My) % My;
-        const float wyq = (ty < w && q < My) ? wy[size_t(i) * w + ty] : 0.f;
-        vprod[v * QG + qi] = make_float4(wyq * wxr[0], wyq * wxr[1], wyq * wxr[2], wyq * wxr[3]);
-      }
+    std::vector<int> fill(sp_start.begin(), sp_start.end() - 1);
+    for_each_entry([&](int st, int q, int i, float wyq, const float *wxr) {
+      const size_t e = size_t(fill[size_t(st) * My + q]++);
+      sp_m[e] = perm[i];
+      sp_w[e] = make_float4(wyq * wxr[0], wyq * wxr[1], wyq * wxr[2], wyq * wxr[3]);
     });
   }
-  // Cluster spread: per (strip, half) slot lists and per (strip, half, group)
-  // visit lists of slot indices.
-  std::vector<int> cl_sstart, cl_vstart, cl_vslot;
-  std::vector<int2> cl_meta;
-  std::vector<float4> cl_wx;
-  std::vector<float> cl_wy;
-  int cl_smax = 0;
-  const bool cl_ok = (My % 2 == 0);
-  const int Hh = My / 2, NGH = (Hh + QG - 1) / QG;
-  if (cl_ok) {
-    cl_sstart.assign(size_t(nstrips) * 2 + 1, 0);
-    std::vector<std::pair<int, int>> bucket_slot;  // (key*NGH + g, slot within key)
-    for (int st = 0; st < nstrips; ++st) {
-      const int p0 = st * P_;
-      for (int hh = 0; hh < 2; ++hh) {
-        const int key = st * 2 + hh;
-        int nslot = 0;
-        for (int dr = 0; dr < nrows; ++dr) {
-          const int row = ((p0 - w / 2 + dr) % Mx + Mx) % Mx;
-          for (int i = cs[size_t(row) * My]; i < cs[size_t(row) * My + My]; ++i) {
-            const int q0 = sby[i] - w / 2 + 1;
-            int glast = -1;
-            bool any = false;
-            for (int t = 0; t < w; ++t) {
-              const int q = ((q0 + t) % My + My) % My;
-              if (q / Hh != hh) continue;
-              const int g = (q - hh * Hh) / QG;
-              if (!any) {
-                any = true;
-                cl_meta.push_back(make_int2(perm[i], sby[i]));
-                float wxr[P_];
-                for (int r = 0; r < P_; ++r) {
-                  const int p = p0 + r;
-                  const int tx = ((p - sbx[i] + w / 2 - 1) % Mx + Mx) % Mx;
-                  wxr[r] = (tx < w && p < Mx) ? wx[size_t(i) * w + tx] : 0.f;
-                }
-                cl_wx.push_back(make_float4(wxr[0], wxr[1], wxr[2], wxr[3]));
-                for (int t2 = 0; t2 < w; ++t2) cl_wy.push_back(wy[size_t(i) * w + t2]);
-              }
-              if (g != glast) {
-                bool seen = false;
-                for (auto it = bucket_slot.rbegin(); it != bucket_slot.rend() && it->second == nslot; ++it)
-                  seen = seen || it->first == key * NGH + g;
-                if (!seen) bucket_slot.push_back({key * NGH + g, nslot});
-                glast = g;
-              }
-            }
-            if (any) ++nslot;
-          }
-        }
-        cl_sstart[key + 1] = cl_sstart[key] + nslot;
-        cl_smax = std::max(cl_smax, nslot);
-      }
-    }
-    cl_vstart.assign(size_t(nstrips) * 2 * NGH + 1, 0);
-    for (auto &bs : bucket_slot) cl_vstart[size_t(bs.first) + 1]++;
-    for (size_t k = 0; k + 1 < cl_vstart.size(); ++k) cl_vstart[k + 1] += cl_vstart[k];
-    cl_vslot.resize(bucket_slot.size());
-    std::vector<int> fillc(cl_vstart.begin(), cl_vstart.end() - 1);
-    for (auto &bs : bucket_slot) cl_vslot[size_t(fillc[size_t(bs.first)]++)] = bs.second;
-  }
-  P->h.cl_smax = cl_smax;
-
   size_t off = 0;
   auto place = [&](size_t bytes) {
     const size_t o = off;
     off = align_up(off + std::max<size_t>(bytes, 16));
     return o;
   };
-  const size_t o_vs = place(sizeof(int) * vstart.size());
-  const size_t o_vm = place(sizeof(int) * nvis);
-  const size_t o_vp = place(sizeof(float4) * nvis * QG);
-  const size_t o_cs = place(sizeof(int) * cl_sstart.size());
-  const size_t o_cm = place(sizeof(int2) * cl_meta.size());
-  const size_t o_cx = place(sizeof(float4) * cl_wx.size());
-  const size_t o_cy = place(sizeof(float) * cl_wy.size());
-  const size_t o_cv = place(sizeof(int) * cl_vstart.size());
-  const size_t o_cl = place(sizeof(int) * cl_vslot.size());
+  const size_t o_ss = place(sizeof(int) * sp_start.size());
+  const size_t o_sm = place(sizeof(int) * nent);
+  const size_t o_sw = place(sizeof(float4) * nent);
   const size_t need = off;
-  (void)o_vs;
-  if (need > P->visits_bytes) {
-    if (P->d_visits) {
+  if (need > P->entries_bytes) {
+    if (P->d_entries) {
       PA_CUDA(cudaStreamSynchronize(stream));
-      cudaFree(P->d_visits);
-      P->d_visits = nullptr;
-      P->visits_bytes = 0;
+      cudaFree(P->d_entries);
+      P->d_entries = nullptr;
+      P->entries_bytes = 0;
     }
-    PA_CUDA(cudaMalloc(&P->d_visits, need));
-    P->visits_bytes = need;
+    PA_CUDA(cudaMalloc(&P->d_entries, need));
+    P->entries_bytes = need;
   }
-  char *V = P->d_visits;
-  P->h.visit_start = reinterpret_cast<const int *>(V + o_vs);
-  P->h.vm = reinterpret_cast<const int *>(V + o_vm);
-  P->h.vprod = reinterpret_cast<const float4 *>(V + o_vp);
-  P->h.cl_slot_start = reinterpret_cast<const int *>(V + o_cs);
-  P->h.cl_meta = reinterpret_cast<const int2 *>(V + o_cm);
-  P->h.cl_wx = reinterpret_cast<const float4 *>(V + o_cx);
-  P->h.cl_wy = reinterpret_cast<const float *>(V + o_cy);
-  P->h.cl_vstart = reinterpret_cast<const int *>(V + o_cv);
-  P->h.cl_vslot = reinterpret_cast<const int *>(V + o_cl);
+  char *V = P->d_entries;
+  P->h.sp_start = reinterpret_cast<const int *>(V + o_ss);
+  P->h.sp_m = reinterpret_cast<const int *>(V + o_sm);
+  P->h.sp_w = reinterpret_cast<const float4 *>(V + o_sw);
   auto upv = [&](const void *dst, const void *src, size_t bytes) {
     return bytes ? cudaMemcpyAsync(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice, stream)
                  : cudaSuccess;
   };
-  PA_CUDA(upv(P->h.visit_start, vstart.data(), sizeof(int) * vstart.size()));
-  PA_CUDA(upv(P->h.vm, vm.data(), sizeof(int) * nvis));
-  PA_CUDA(upv(P->h.vprod, vprod.data(), sizeof(float4) * nvis * QG));
-  PA_CUDA(upv(P->h.cl_slot_start, cl_sstart.data(), sizeof(int) * cl_sstart.size()));
-  PA_CUDA(upv(P->h.cl_meta, cl_meta.data(), sizeof(int2) * cl_meta.size()));
-  PA_CUDA(upv(P->h.cl_wx, cl_wx.data(), sizeof(float4) * cl_wx.size()));
-  PA_CUDA(upv(P->h.cl_wy, cl_wy.data(), sizeof(float) * cl_wy.size()));
-  PA_CUDA(upv(P->h.cl_vstart, cl_vstart.data(), sizeof(int) * cl_vstart.size()));
-  PA_CUDA(upv(P->h.cl_vslot, cl_vslot.data(), sizeof(int) * cl_vslot.size()));
-  // the cluster path needs an even My and its staging area within the limit
-  P->h.spread_mode = (cl_ok && pa::smem_spread_cluster(P->h) <= P->smem_limit) ? 1 : 0;
+  PA_CUDA(upv(P->h.sp_start, sp_start.data(), sizeof(int) * sp_start.size()));
+  PA_CUDA(upv(P->h.sp_m, sp_m.data(), sizeof(int) * nent));
+  PA_CUDA(upv(P->h.sp_w, sp_w.data(), sizeof(float4) * nent));
   // pageable sources: the copies above are complete when they return
   return PA_OK;
 }
@@ -467,7 +374,7 @@ void free_plan(pa_plan *P) {
   cudaFree(P->d_desc);
   cudaFree(P->d_static);
   cudaFree(P->d_work);
-  cudaFree(P->d_visits);
+  cudaFree(P->d_entries);
   delete P;
 }
 
@@ -486,8 +393,9 @@ int check_launch(cudaError_t e, const char *what) {
 }
 
 const char *const kStageNames[PA_PROFILE_STAGES] = {
-    "ned_spread_rowfft", "ned_colfft", "ner_fused", "image_x", "image_y_c2r", "image_y_adj",
-    "image_x_adj", "ner_adj", "ned_colfft_adj", "ned_interp", "grad_reduce", "cubic_baseline", "ned_rowifft"};
+    "ned_spread", "ned_colfft", "ner_fused", "image_x", "image_y_c2r", "image_y_adj",
+    "image_x_adj", "ner_adj", "ned_colfft_adj", "ned_interp", "grad_reduce", "cubic_baseline", "ned_rowifft",
+    "ned_rowfft"};
 
 cudaEvent_t take_event(pa_plan *P) {
   if (!P->ev_pool.empty()) {
@@ -522,17 +430,12 @@ int run_forward(pa_plan *P, const IoPtrs &io, cudaStream_t s, bool cubic) {
   L.io = io;
   const InstDesc &h = P->h;
   int rc;
-  if (h.spread_mode == 1) {
-    L.nblocks = 2 * pa::blocks_spread(h);
-    L.smem = pa::smem_spread_cluster(h);
-    if ((rc = timed(P, 0, s, [&] { return pa::launch_spread_cluster(L, pa::threads_spread_cluster(h), P->w); },
-                    "spread")) != PA_OK)
-      return rc;
-  } else {
-    L.nblocks = pa::blocks_spread(h);
-    L.smem = pa::smem_spread(h);
-    if ((rc = timed(P, 0, s, [&] { return pa::launch_spread(L, P->spread_threads); }, "spread")) != PA_OK) return rc;
-  }
+  L.nblocks = pa::blocks_spread(h, pa::spread_spl(h));
+  L.smem = 0;
+  if ((rc = timed(P, 0, s, [&] { return pa::launch_spread(L, pa::spread_spl(h)); }, "spread")) != PA_OK) return rc;
+  L.nblocks = pa::blocks_rowfft(h);
+  L.smem = pa::smem_rowfft(h);
+  if ((rc = timed(P, 13, s, [&] { return pa::launch_rowfft(L); }, "rowfft")) != PA_OK) return rc;
   L.nblocks = pa::blocks_colfft(h);
   L.smem = pa::smem_colfft(h);
   if ((rc = timed(P, 1, s, [&] { return pa::launch_colfft(L, false); }, "colfft")) != PA_OK) return rc;
@@ -677,21 +580,19 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
   h.nY1 = h.hy + 1;
   h.nchunk_adj = int((Nt + pa::kInterpNC - 1) / pa::kInterpNC);
   h.sigma = sigma;
-  P->spread_threads = pa::threads_spread(h);
 
   // FFT schedules and twiddles
   struct Len {
     FftPlan *fp;
     int L;
     int nthr;
-  } lens[] = {{&h.fMy, int(My), P->spread_threads < 256 ? P->spread_threads : 256},
+  } lens[] = {{&h.fMy, int(My), 256},
               {&h.fMx, int(Mx), 256},
               {&h.fMt, int(Mt), 256},
               {&h.fNz, int(Nz), 256},
               {&h.fNx, int(Nx), 256},
               {&h.fNy, int(Ny), 256},
-              {&h.fNt, int(Nt), 256},
-              {&h.fMyh, int(My % 2 == 0 ? My / 2 : My), 256}};
+              {&h.fNt, int(Nt), 256}};
   std::vector<float2> tw;
   for (auto &ln : lens) {
     if (!make_fft_plan(ln.L, ln.nthr, *ln.fp)) {
@@ -740,10 +641,8 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
   fit_horner(kb, horner_degree(width), P->ht);
 
   // shared-memory limits
-  const size_t smems[] = {pa::smem_spread(h), pa::smem_colfft(h), pa::smem_ner(h), pa::smem_ner_adj(h),
-                          pa::smem_rowifft(h),
-
-                          pa::smem_imgx(h), pa::smem_imgy(h), pa::smem_interp(h)};
+  const size_t smems[] = {pa::smem_rowfft(h), pa::smem_colfft(h),  pa::smem_ner(h),  pa::smem_ner_adj(h),
+                          pa::smem_rowifft(h), pa::smem_imgx(h), pa::smem_imgy(h), pa::smem_interp(h)};
   for (size_t sm : smems)
     if (sm > P->smem_limit) {
       delete P;
@@ -837,7 +736,7 @@ int pa_plan_update_positions(pa_plan *plan, const double *sensor_xy, void *strea
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int rc = upload_sensors(plan, sensor_xy, s);
   if (rc != PA_OK) return rc;
-  // the visit lists may have moved: refresh the device descriptor
+  // the spread entry lists may have moved: refresh the device descriptor
   PA_CUDA(cudaMemcpyAsync(plan->d_desc, &plan->h, sizeof(InstDesc), cudaMemcpyHostToDevice, s));
   return PA_OK;
 }
@@ -993,16 +892,19 @@ int pa_batch_create(pa_batch **out, int n, pa_plan *const *plans, void *stream) 
     }
     st.nblocks = int(work.size() - st.off);
   };
-  B->spread_cluster = true;
-  for (int i = 0; i < n; ++i) B->spread_cluster = B->spread_cluster && descs[i].spread_mode == 1;
-  add_stage(B->st_spread, pa::blocks_spread, B->spread_cluster ? pa::smem_spread_cluster : pa::smem_spread);
+  // one spread instantiation (samples per lane) serves the whole batch
+  for (int i = 0; i < n; ++i) B->spread_spl = std::max(B->spread_spl, pa::spread_spl(descs[i]));
+  B->st_spread.off = work.size();
+  for (int i = 0; i < n; ++i) {
+    const int cnt = pa::blocks_spread(descs[i], B->spread_spl);
+    for (int t = 0; t < cnt; ++t) work.push_back(make_int2(i, t));
+  }
+  B->st_spread.nblocks = int(work.size() - B->st_spread.off);
+  add_stage(B->st_rowfft, pa::blocks_rowfft, pa::smem_rowfft);
   add_stage(B->st_col, pa::blocks_colfft, pa::smem_colfft);
   add_stage(B->st_ner, pa::blocks_ner, pa::smem_ner);
   add_stage(B->st_imgx, pa::blocks_imgx, pa::smem_imgx);
   add_stage(B->st_imgy, pa::blocks_imgy, pa::smem_imgy);
-  for (int i = 0; i < n; ++i)
-    B->spread_threads = std::max(B->spread_threads, B->spread_cluster ? pa::threads_spread_cluster(descs[i])
-                                                                      : plans[i]->spread_threads);
   cudaError_t ce = cudaMalloc(&B->d_descs, sizeof(InstDesc) * n);
   if (ce == cudaSuccess) ce = cudaMalloc(&B->d_io, sizeof(IoPtrs) * n);
   if (ce == cudaSuccess) ce = cudaMalloc(&B->d_work, sizeof(int2) * work.size());
@@ -1030,15 +932,13 @@ static int batch_launches(pa_batch *B, cudaStream_t s) {
   L.stream = s;
   int rc;
   L.work = B->d_work + B->st_spread.off;
-  L.smem = B->st_spread.smem;
-  if (B->spread_cluster) {
-    L.nblocks = 2 * B->st_spread.nblocks;  // two blocks (one cluster) per work item
-    if ((rc = check_launch(pa::launch_spread_cluster(L, B->spread_threads, B->width), "batch spread")) != PA_OK)
-      return rc;
-  } else {
-    L.nblocks = B->st_spread.nblocks;
-    if ((rc = check_launch(pa::launch_spread(L, B->spread_threads), "batch spread")) != PA_OK) return rc;
-  }
+  L.nblocks = B->st_spread.nblocks;
+  L.smem = 0;
+  if ((rc = check_launch(pa::launch_spread(L, B->spread_spl), "batch spread")) != PA_OK) return rc;
+  L.work = B->d_work + B->st_rowfft.off;
+  L.nblocks = B->st_rowfft.nblocks;
+  L.smem = B->st_rowfft.smem;
+  if ((rc = check_launch(pa::launch_rowfft(L), "batch rowfft")) != PA_OK) return rc;
   L.work = B->d_work + B->st_col.off;
   L.nblocks = B->st_col.nblocks;
   L.smem = B->st_col.smem;
