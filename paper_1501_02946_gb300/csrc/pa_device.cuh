@@ -219,10 +219,13 @@ struct Ipt {
 // (element i of sequence b at buf[i * estride + b]).  Reads of a round finish
 // (barrier) before its writes; rounds cover whole sequences.
 // Barrier of the threads that share one transform: the whole block
-// (bar_id = 0) or a named barrier over `nthr` threads (bar_id >= 1).
+// (bar_id = 0), one whole warp (nthr = 32; the group must be warp-aligned) or
+// a named barrier over `nthr` threads (bar_id >= 1).
 __device__ __forceinline__ void group_sync(int bar_id, int nthr) {
   if (bar_id == 0) {
     __syncthreads();
+  } else if (nthr == 32) {
+    __syncwarp();
   } else {
     asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthr) : "memory");
   }

@@ -35,8 +35,8 @@ __global__ void __launch_bounds__(kThreadsImg) k_imgx(const InstDesc *__restrict
   constexpr int ZC = kImgZC;
   const int nzc = (Nz + ZC - 1) / ZC;
   if (tile >= nY1 * nzc) return;
-  const int iy = tile % nY1;
-  const int z0 = (tile / nY1) * ZC;
+  const int iy = tile / nzc;
+  const int z0 = (tile % nzc) * ZC;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const float2 *src = ADJ ? d.U : d.Fz;
   float2 *dst = ADJ ? d.Fz : d.U;
@@ -80,8 +80,8 @@ __global__ void __launch_bounds__(kThreadsImg) k_imgy(const InstDesc *__restrict
   constexpr int ZP = kImgZP;
   const int nzc = (Nz + 2 * ZP - 1) / (2 * ZP);
   if (tile >= Nx * nzc) return;
-  const int x = tile % Nx;
-  const int z0 = (tile / Nx) * 2 * ZP;
+  const int x = tile / nzc;
+  const int z0 = (tile % nzc) * 2 * ZP;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const IoPtrs io = io_of_img(io0, io_table, inst);
   const bool ny_even = (Ny & 1) == 0;

@@ -42,7 +42,8 @@ struct InstDesc {
   int hx, hy, hz, nc;   // floor(N/2) of x, y, z, t
   int nX1, nY1;         // rows of the spatial spectrum: 2*hx+1 (jx) and hy+1 (jy)
   int nchunk_adj;       // n-chunks of the adjoint NED kernel (gradient partials)
-  int ner_group;        // threads per column in the NER kernels (64, 128 or 256)
+  int ner_cb;           // columns per block of the NER kernels (1, 2 or 4)
+  int ner_threads;      // block size of the NER kernels (128 or 256)
 
   FftPlan fMy, fMx, fMt, fNz, fNx, fNy, fNt;
   const float2 *tw;
@@ -113,6 +114,7 @@ struct Launch {
   int nblocks;
   size_t smem;
   cudaStream_t stream;
+  int threads;            // block size, for kernels that take it from the host
 };
 
 // Block counts and shared-memory sizes per stage for one instance.
@@ -123,9 +125,8 @@ size_t smem_rowfft(const InstDesc &d);
 int blocks_colfft(const InstDesc &d);
 size_t smem_colfft(const InstDesc &d);
 int blocks_ner(const InstDesc &d);
-size_t smem_ner(const InstDesc &d);
 int blocks_ner_adj(const InstDesc &d);
-size_t smem_ner_adj(const InstDesc &d);
+size_t smem_ner(const InstDesc &d);  // forward and adjoint
 int blocks_imgx(const InstDesc &d);
 size_t smem_imgx(const InstDesc &d);
 int blocks_imgy(const InstDesc &d);

@@ -157,8 +157,9 @@ __global__ void __launch_bounds__(kThreadsCol) k_rowfft(const InstDesc *__restri
   const int Mx = d.Mx, My = d.My, Nt = d.Nt, nY1 = d.nY1;
   const int nchunks = (Nt + 2 * NCP - 1) / (2 * NCP);
   if (tile >= Mx * nchunks) return;
-  const int p = tile % Mx;
-  const int n0 = (tile / Mx) * 2 * NCP;
+  // chunk fastest: blocks that run together cover contiguous runs of each row
+  const int p = tile / nchunks;
+  const int n0 = (tile % nchunks) * 2 * NCP;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const float *G0 = d.G0 + (size_t)p * My * Nt;
   const bool vec4 = (Nt & 3) == 0;
@@ -221,8 +222,8 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft(const InstDesc *__restri
   constexpr int NC = kColNC;
   const int nchunks = (Nt + NC - 1) / NC;
   if (tile >= nY1 * nchunks) return;
-  const int jy = tile % nY1;
-  const int n0 = (tile / nY1) * NC;
+  const int jy = tile / nchunks;
+  const int n0 = (tile % nchunks) * NC;
   const int tid = threadIdx.x, nthr = blockDim.x;
   if (!ADJ) {
     const float2 *Tsrc = d.T + (size_t)jy * Nt + n0;
@@ -287,8 +288,9 @@ __global__ void __launch_bounds__(kThreadsCol) k_rowifft(const InstDesc *__restr
   const int Mx = d.Mx, My = d.My, Nt = d.Nt, nY1 = d.nY1;
   const int nchunks = (Nt + 2 * NCP - 1) / (2 * NCP);
   if (tile >= Mx * nchunks) return;
-  const int p = tile % Mx;
-  const int n0 = (tile / Mx) * 2 * NCP;
+  // chunk fastest: blocks that run together cover contiguous runs of each row
+  const int p = tile / nchunks;
+  const int n0 = (tile % nchunks) * 2 * NCP;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const float2 *Trow = d.T + (size_t)p * nY1 * Nt;
   for (int idx = tid; idx < My * NCP; idx += nthr) S[idx] = make_float2(0.f, 0.f);
@@ -350,9 +352,9 @@ __global__ void __launch_bounds__(kThreadsInterp) k_interp(const InstDesc *__res
   const int ntx = (Mx + TX - 1) / TX, nty = (My + TY - 1) / TY;
   const int nchunks = (Nt + NC - 1) / NC;
   if (tile >= ntx * nty * nchunks) return;
-  const int tx = tile % ntx;
-  const int ty = (tile / ntx) % nty;
-  const int c = tile / (ntx * nty);
+  const int c = tile % nchunks;
+  const int tx = (tile / nchunks) % ntx;
+  const int ty = tile / (nchunks * ntx);
   const int p0 = tx * TX, q0 = ty * TY, n0 = c * NC;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;

@@ -1,17 +1,22 @@
-// pa_ner.cu -- NER-NUFFT stage (eq:NER_NUFFT, Sec. 3), the weight of
-// eq:exact and the inverse DFT over depth, on sm_103a.
+// pa_ner.cu -- NER-NUFFT stage (the temporal type-2 NUFFT of Sec. 3), the
+// weight W(j, l) of the exact reconstruction formula and the inverse DFT over
+// depth, on sm_103a.
 //
-// One block owns one column j = (jx, jy) of the half spectrum.  Forward:
+// A block owns CB columns j = (jx, jy) of the half spectrum and transforms
+// them together (batched in-place FFTs in shared memory, element n of slot b
+// at [n*CB + b]).  Forward, per column:
 //   load G1(j, n) / phihat((n - nc)/Mt) at n' = n - nc (the paper's centred
-//   theta = 2 pi n / N - pi), zero-pad to Mt = sigma Nt, FFT in shared memory,
-//   evaluate at the nz non-integer frequencies tau(j, l) = omega Nt dt / (2 pi)
-//   with w window taps (Horner polynomials, tau in double-float) times the
-//   centring phase exp(-2 pi i tau nc / Nt), multiply by (dt/dz) W(j, l), and
-//   take the inverse DFT over l, all without leaving shared memory.
+//   theta = 2 pi n / N - pi), zero-pad to Mt = sigma Nt, FFT, evaluate at the
+//   nz non-integer frequencies tau(j, l) = omega Nt dt / (2 pi) with w window
+//   taps (Horner polynomials, tau in double-float) times the centring phase
+//   exp(-2 pi i tau nc / Nt), multiply by (dt/dz) W(j, l), and take the
+//   inverse DFT over l, all without leaving shared memory.
 // Columns and depths on the unpaired Nyquist index of an even length are
 // replaced by the Hermitian part F_sym(k) = (F(k) + conj F(-k mod N)) / 2,
 // which makes the half-spectrum real inverse DFT equal to the real part of the
 // full inverse DFT; it needs the spectrum at +N/2 as well, which G1 holds.
+// Such columns take two passes (one per source); the work items are ordered
+// so that one-pass columns fill most blocks.
 // The adjoint kernel is the exact transpose (spread <-> interpolate).
 #include "pa_device.cuh"
 
@@ -19,7 +24,8 @@ namespace pa {
 
 namespace {
 
-constexpr int kThreadsNer = 256;
+constexpr int kNerMaxCB = 4;  // most columns per block
+
 
 template <int W>
 struct HornerDeg {
@@ -81,8 +87,10 @@ __device__ __forceinline__ void window_taps(float fr, const HornerTable &ht, flo
   }
 }
 
+// H: element k of the transformed column at H[k * CB] (slot-offset pointer).
 template <int W>
-__device__ __forceinline__ float2 ner_interp(const float2 *H, ff tau, const InstDesc &d, const HornerTable &ht) {
+__device__ __forceinline__ float2 ner_interp(const float2 *H, int CB, ff tau, const InstDesc &d,
+                                             const HornerTable &ht) {
   int p0;
   float fr;
   footprint(tau, d.sigma, d.Mt, W / 2, p0, fr);
@@ -93,7 +101,7 @@ __device__ __forceinline__ float2 ner_interp(const float2 *H, ff tau, const Inst
   const int Mt = d.Mt;
 #pragma unroll
   for (int t = 0; t < W; ++t) {
-    const float2 h = H[pad32(idx)];
+    const float2 h = H[idx * CB];
     acc.x = fmaf(wt[t], h.x, acc.x);
     acc.y = fmaf(wt[t], h.y, acc.y);
     idx = (idx + 1 == Mt) ? 0 : idx + 1;
@@ -103,7 +111,8 @@ __device__ __forceinline__ float2 ner_interp(const float2 *H, ff tau, const Inst
 
 // Transpose of ner_interp: H[p_t] += phi_t conj(phase) v.
 template <int W>
-__device__ __forceinline__ void ner_spread(float2 *H, ff tau, float2 v, const InstDesc &d, const HornerTable &ht) {
+__device__ __forceinline__ void ner_spread(float2 *H, int CB, ff tau, float2 v, const InstDesc &d,
+                                           const HornerTable &ht) {
   int p0;
   float fr;
   footprint(tau, d.sigma, d.Mt, W / 2, p0, fr);
@@ -114,15 +123,15 @@ __device__ __forceinline__ void ner_spread(float2 *H, ff tau, float2 v, const In
   const int Mt = d.Mt;
 #pragma unroll
   for (int t = 0; t < W; ++t) {
-    atomicAdd(&H[pad32(idx)].x, wt[t] * vv.x);
-    atomicAdd(&H[pad32(idx)].y, wt[t] * vv.y);
+    atomicAdd(&H[idx * CB].x, wt[t] * vv.x);
+    atomicAdd(&H[idx * CB].y, wt[t] * vv.y);
     idx = (idx + 1 == Mt) ? 0 : idx + 1;
   }
 }
 
 // 4-tap cubic Lagrange interpolation of the uniform Nt-point spectrum at tau
 // (the polynomial-interpolation baseline of Sec. 2).
-__device__ __forceinline__ float2 cubic_interp(const float2 *H, ff tau, int Nt) {
+__device__ __forceinline__ float2 cubic_interp(const float2 *H, int CB, ff tau, int Nt) {
   int p0;
   float fr;
   footprint(tau, 1, Nt, 2, p0, fr);  // taps base-1 .. base+2
@@ -136,7 +145,7 @@ __device__ __forceinline__ float2 cubic_interp(const float2 *H, ff tau, int Nt) 
   int idx = p0;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
-    const float2 h = H[pad32(idx)];
+    const float2 h = H[idx * CB];
     acc.x = fmaf(wt[t], h.x, acc.x);
     acc.y = fmaf(wt[t], h.y, acc.y);
     idx = (idx + 1 == Nt) ? 0 : idx + 1;
@@ -161,230 +170,308 @@ __device__ __forceinline__ ColInfo col_info(const InstDesc &d, int jx, int jy) {
   return c;
 }
 
-// Threads that share one column: the smallest group for which every stage
-// of the column transforms fits one round (host-side check mirrors this).
-__device__ __forceinline__ int ner_group(const InstDesc &d) { return d.ner_group; }
-// Length of each of the two ping-pong buffers of a column.
-__host__ __device__ __forceinline__ int ner_buf_len(const InstDesc &d) {
-  int L = d.Mt > d.Nt ? d.Mt : d.Nt;
-  return padded_len(L > d.Nz ? L : d.Nz);
+// Slot of a NER block: one (column, source) transform.  A column on an
+// unpaired Nyquist index has two sources (A, B); transforms whose results add
+// into one output take two adjacent slots, the first (even) one leading.
+struct NerSlot {
+  int kind;   // 0 empty, 1 alone, 2 leads a group of two, 3 second of a group
+  int jx, iy;
+  int src;    // 0: source A, 1: source B
+  int zero_row0;  // adjoint: G1 row jx = -hx of the y-Nyquist row is read by no column
+};
+
+// Forward slots: the one-source columns, (padding to an even count), then the
+// two sources of every Nyquist column (x-Nyquist row ix = 0 for even Nx,
+// y-Nyquist row iy = hy for even Ny).
+__host__ __device__ __forceinline__ int ner_fwd_slots(const InstDesc &d) {
+  const int xe = (d.Nx & 1) == 0, ye = (d.Ny & 1) == 0;
+  const int R = (d.Nx - xe) * (d.nY1 - ye);
+  return R + (R & 1) + 2 * (xe * d.nY1 + ye * (d.Nx - xe));
+}
+__device__ __forceinline__ NerSlot fwd_slot(const InstDesc &d, int v) {
+  NerSlot sl{};
+  const int xe = (d.Nx & 1) == 0, ye = (d.Ny & 1) == 0;
+  const int ry = d.nY1 - ye;
+  const int R = (d.Nx - xe) * ry;
+  if (v < R) {
+    sl.kind = 1;
+    sl.jx = xe + v / ry - d.hx;
+    sl.iy = v % ry;
+    return sl;
+  }
+  const int O1 = R + (R & 1);
+  if (v < O1) return sl;
+  const int k = v - O1;
+  int q = k >> 1;
+  sl.src = k & 1;
+  if (xe) {
+    if (q < d.nY1) {
+      sl.kind = 2 + sl.src;
+      sl.jx = -d.hx;
+      sl.iy = q;
+      return sl;
+    }
+    q -= d.nY1;
+  }
+  if (ye && q < d.Nx - xe) {
+    sl.kind = 2 + sl.src;
+    sl.jx = xe + q - d.hx;
+    sl.iy = d.hy;
+  }
+  return sl;
 }
 
-// Forward NER: a group of G threads (G = 64/128/256, named barrier 1 + group
-// index) owns one column of the half spectrum and two ping-pong buffers for
-// out-of-place FFTs.  Columns on an unpaired Nyquist index (x or y) read two
-// sources (A, B) that are transformed one after the other.  CUBIC selects
-// the baseline (plain Nt-point FFT, 4-tap Lagrange interpolation, no window).
+// Adjoint slots: the one-source columns, (padding), the two sources of the
+// x-Nyquist columns (even Nx, jy < hy; they feed two different G1 rows), then
+// for even Ny the y-Nyquist row, whose G1 rows each take two transforms:
+// row hx from both sources of jx = 0, row 2hx from both sources of the corner
+// jx = -hx (even Nx), and for each g > 0 of a pair {g, -g} row hx - g from
+// (g, A) + (-g, B) and row hx + g from (g, B) + (-g, A).
+__host__ __device__ __forceinline__ int ner_adj_slots(const InstDesc &d) {
+  const int xe = (d.Nx & 1) == 0, ye = (d.Ny & 1) == 0;
+  const int ry = d.nY1 - ye;
+  const int R = (d.Nx - xe) * ry;
+  const int npairs = xe ? d.hx - 1 : d.hx;
+  return R + (R & 1) + 2 * xe * ry + ye * (2 + 2 * xe + 4 * (npairs > 0 ? npairs : 0));
+}
+__device__ __forceinline__ NerSlot adj_slot(const InstDesc &d, int v) {
+  NerSlot sl{};
+  const int xe = (d.Nx & 1) == 0, ye = (d.Ny & 1) == 0;
+  const int ry = d.nY1 - ye, hx = d.hx;
+  const int R = (d.Nx - xe) * ry;
+  if (v < R) {
+    sl.kind = 1;
+    sl.jx = xe + v / ry - hx;
+    sl.iy = v % ry;
+    return sl;
+  }
+  int k = v - (R + (R & 1));
+  if (k < 0) return sl;
+  if (xe) {
+    if (k < 2 * ry) {
+      sl.kind = 1;
+      sl.jx = -hx;
+      sl.iy = k >> 1;
+      sl.src = k & 1;
+      return sl;
+    }
+    k -= 2 * ry;
+  }
+  if (!ye) return sl;
+  sl.iy = d.hy;
+  if (k < 2) {
+    sl.kind = 2 + k;
+    sl.jx = 0;
+    sl.src = k;
+    return sl;
+  }
+  k -= 2;
+  if (xe) {
+    if (k < 2) {
+      sl.kind = 2 + k;
+      sl.jx = -hx;
+      sl.src = k;
+      sl.zero_row0 = k == 0;
+      return sl;
+    }
+    k -= 2;
+  }
+  const int npairs = xe ? hx - 1 : hx;
+  const int p = k >> 2, r = k & 3;
+  if (p >= npairs) return NerSlot{};
+  const int g = 1 + p;
+  sl.kind = 2 + (r & 1);
+  sl.jx = (r == 0 || r == 2) ? g : -g;
+  sl.src = (r == 0 || r == 3) ? 0 : 1;
+  return sl;
+}
+
+// Forward NER: slot b of the block transforms slot tile*CB + b.
 template <int W, bool CUBIC>
-__global__ void __launch_bounds__(kThreadsNer, 3) k_ner(const InstDesc *__restrict__ descs,
-                                                        const int2 *__restrict__ work,
-                                                        const __grid_constant__ HornerTable ht) {
+__global__ void __launch_bounds__(256, 2) k_ner(const InstDesc *__restrict__ descs,
+                                                const int2 *__restrict__ work,
+                                                const __grid_constant__ HornerTable ht) {
   extern __shared__ float4 smem_f4[];
+  __shared__ NerSlot slots[kNerMaxCB];
   int inst, tile;
   block_work(work, inst, tile);
   const InstDesc &d = descs[inst];
-  const int G = ner_group(d);
-  const int ngrp = blockDim.x / G;
-  const int grp = threadIdx.x / G, t = threadIdx.x % G, bar = 1 + grp;
-  const int Nt = d.Nt, Mt = d.Mt, Nz = d.Nz, nY1 = d.nY1, nc = d.nc, hz = d.hz;
-  const int ncols = d.Nx * nY1;
-  const int col = tile * ngrp + grp;
-  if (col >= ncols) return;  // the whole group leaves together
-  const int ix = col / nY1, iy = col % nY1;
-  const ColInfo ci = col_info(d, ix - d.hx, iy);
-  const bool nyq = ci.xnyq || ci.ynyq;
-  const int LB = ner_buf_len(d);
-  const int LZ = padded_len(Nz);
-  float2 *bufA = reinterpret_cast<float2 *>(smem_f4) + (size_t)grp * (2 * LB + LZ);
-  float2 *bufB = bufA + LB;
-  float2 *Fs = bufB + LB;
-  const float scale = d.scale;
-
-  for (int pass = 0; pass < (nyq ? 2 : 1); ++pass) {
-    const float2 *src = d.G1 + ((size_t)(pass == 0 ? ci.rowA : ci.rowB) * nY1 + iy) * Nt;
-    const bool cj = (pass == 0) && ci.ynyq;
-    copy_unrolled<4, float2>(
-        Nt, t, G,
-        [&](int n) {
-          float2 a = src[n];
-          if (cj) a.y = -a.y;
-          return CUBIC ? a : cscale(a, __ldg(d.invpht + n));
-        },
-        [&](int n, float2 a) { bufA[pad32(CUBIC ? n : wrap(n - nc, Mt))] = a; });
-    if (!CUBIC)
-      for (int u = t; u < Mt - Nt; u += G) bufA[pad32(Nt - nc + u)] = make_float2(0.f, 0.f);
-    group_sync(bar, G);
-    const float2 *H = fft_pingpong<-1>(bufA, bufB, CUBIC ? d.fNt : d.fMt, d.tw, t, G, bar);
-#pragma unroll 1
-    for (int il = t; il < Nz; il += G) {
-      const int l = il - hz;
-      float2 F = make_float2(0.f, 0.f);
-      if (!(l == 0 && (ci.jx != 0 || ci.jy != 0))) {
-        const ff tau = tau_of(d, ci.jx, ci.jy, l);
-        const float wgt = weight_of(d, tau, l) * scale;
-        const bool lnyq = ((Nz & 1) == 0) && (l == -hz);
-        // the second evaluation point: -tau on the depth Nyquist (single
-        // source), or the same tau for the B source of a Nyquist column
-        const bool two = !nyq && lnyq;
-        const ff tp = (nyq && pass == 1 && lnyq) ? ff_neg(tau) : tau;
-        float2 v = CUBIC ? cubic_interp(H, tp, Nt) : ner_interp<W>(H, tp, d, ht);
-        if (two) {
-          const ff tb = ff_neg(tau);
-          const float2 vb = CUBIC ? cubic_interp(H, tb, Nt) : ner_interp<W>(H, tb, d, ht);
-          v = cadd(v, vb);
-        }
-        F = cscale(v, (nyq || two) ? 0.5f * wgt : wgt);
-      }
-      const int pos = pad32(wrap(l, Nz));
-      Fs[pos] = pass == 0 ? F : cadd(Fs[pos], F);
-    }
-    group_sync(bar, G);
+  const int CB = d.ner_cb;
+  const int Nt = d.Nt, Mt = d.Mt, Nz = d.Nz, nY1 = d.nY1, nc = d.nc, hz = d.hz, hx = d.hx;
+  const int nslots = ner_fwd_slots(d);
+  if (tile * CB >= nslots) return;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int L = CUBIC ? Nt : Mt;
+  float2 *H = reinterpret_cast<float2 *>(smem_f4);  // [L][CB]
+  float2 *Fs = H + (size_t)L * CB;                  // [Nz][CB]
+  if (tid < CB) {
+    const int v = tile * CB + tid;
+    slots[tid] = v < nslots ? fwd_slot(d, v) : NerSlot{};
   }
-  const float2 *R = fft_pingpong<+1>(Fs, bufA, d.fNz, d.tw, t, G, bar);
-  float2 *dst = d.Fz + ((size_t)ix * nY1 + iy) * Nz;
-  for (int z = t; z < Nz; z += G) dst[z] = R[pad32(z)];
-}
-
-// Cotangent sample n of a transformed column (un-centre, 1/phihat).
-__device__ __forceinline__ float2 adj_sample(const InstDesc &d, const float2 *H, int n) {
-  return cscale(H[pad32(wrap(n - d.nc, d.Mt))], __ldg(d.invpht + n));
+  __syncthreads();
+  copy_unrolled<4, float2>(
+      Nt * CB, tid, nthr,
+      [&](int idx) {
+        const int b = idx / Nt, n = idx - b * Nt;
+        const NerSlot sl = slots[b];
+        if (sl.kind == 0) return make_float2(0.f, 0.f);
+        const ColInfo ci = col_info(d, sl.jx, sl.iy);
+        const float2 *src = d.G1 + ((size_t)(sl.src == 0 ? ci.rowA : ci.rowB) * nY1 + sl.iy) * Nt;
+        float2 a = src[n];
+        if (sl.src == 0 && ci.ynyq) a.y = -a.y;
+        return CUBIC ? a : cscale(a, __ldg(d.invpht + n));
+      },
+      [&](int idx, float2 a) {
+        const int b = idx / Nt, n = idx - b * Nt;
+        H[(CUBIC ? n : wrap(n - nc, Mt)) * CB + b] = a;
+      });
+  if (!CUBIC)
+    for (int idx = tid; idx < (Mt - Nt) * CB; idx += nthr) H[(Nt - nc) * CB + idx] = make_float2(0.f, 0.f);
+  __syncthreads();
+  if (CUBIC) {
+    fft_smem<-1>(H, CB, CB, d.fNt, d.tw, tid, nthr);
+  } else {
+    fft_smem<-1>(H, CB, CB, d.fMt, d.tw, tid, nthr);
+  }
+#pragma unroll 1
+  for (int idx = tid; idx < Nz * CB; idx += nthr) {
+    const int il = idx / CB, b = idx - il * CB;
+    const NerSlot sl = slots[b];
+    if (sl.kind == 0) continue;
+    const ColInfo ci = col_info(d, sl.jx, sl.iy);
+    const bool nyq = sl.kind >= 2;
+    const int l = il - hz;
+    float2 F = make_float2(0.f, 0.f);
+    if (!(l == 0 && (ci.jx != 0 || ci.jy != 0))) {
+      const ff tau = tau_of(d, ci.jx, ci.jy, l);
+      const float wgt = weight_of(d, tau, l) * d.scale;
+      const bool lnyq = ((Nz & 1) == 0) && (l == -hz);
+      // the second evaluation point: -tau on the depth Nyquist (one source),
+      // or -tau for the B source of a Nyquist column there
+      const bool two = !nyq && lnyq;
+      const ff tp = (nyq && sl.src == 1 && lnyq) ? ff_neg(tau) : tau;
+      const float2 *Hb = H + b;
+      float2 v = CUBIC ? cubic_interp(Hb, CB, tp, Nt) : ner_interp<W>(Hb, CB, tp, d, ht);
+      if (two) {
+        const ff tb = ff_neg(tau);
+        const float2 vb = CUBIC ? cubic_interp(Hb, CB, tb, Nt) : ner_interp<W>(Hb, CB, tb, d, ht);
+        v = cadd(v, vb);
+      }
+      F = cscale(v, (nyq || two) ? 0.5f * wgt : wgt);
+    }
+    Fs[wrap(l, Nz) * CB + b] = F;
+  }
+  __syncthreads();
+  // a two-source column: the leading slot takes the sum
+  for (int idx = tid; idx < Nz * CB; idx += nthr) {
+    const int b = idx % CB;
+    if (slots[b].kind == 2) Fs[idx] = cadd(Fs[idx], Fs[idx + 1]);
+  }
+  __syncthreads();
+  // slots without an output hold stale values: transformed, never stored
+  fft_smem<+1>(Fs, CB, CB, d.fNz, d.tw, tid, nthr);
+  for (int idx = tid; idx < Nz * CB; idx += nthr) {
+    const int b = idx / Nz, z = idx - b * Nz;
+    const NerSlot sl = slots[b];
+    if (sl.kind == 1 || sl.kind == 2) d.Fz[((size_t)(sl.jx + hx) * nY1 + sl.iy) * Nz + z] = Fs[z * CB + b];
+  }
 }
 
 // Adjoint NER: Fz cotangent -> DFT over depth -> transposed weight and
 // window (spread in shared memory) -> inverse FFT -> un-centre, 1/phihat ->
-// G1.  Work items: every column off the y-Nyquist row jy = hy (all rows when
-// Ny is odd), then for even Ny the Nyquist row in pairs {g, -g}: both columns
-// of a pair read the same two G1 sources, so one group computes the four
-// contributions in turn and stores, then adds, into the two G1 rows.
+// G1 row (the sum of a group's two slots).
 template <int W>
-__global__ void __launch_bounds__(kThreadsNer, 3) k_ner_adj(const InstDesc *__restrict__ descs,
-                                                            const int2 *__restrict__ work,
-                                                            const __grid_constant__ HornerTable ht) {
+__global__ void __launch_bounds__(256, 2) k_ner_adj(const InstDesc *__restrict__ descs,
+                                                    const int2 *__restrict__ work,
+                                                    const __grid_constant__ HornerTable ht) {
   extern __shared__ float4 smem_f4[];
+  __shared__ NerSlot slots[kNerMaxCB];
   int inst, tile;
   block_work(work, inst, tile);
   const InstDesc &d = descs[inst];
-  const int G = ner_group(d);
-  const int ngrp = blockDim.x / G;
-  const int grp = threadIdx.x / G, t = threadIdx.x % G, bar = 1 + grp;
-  const int Nt = d.Nt, Mt = d.Mt, Nz = d.Nz, nY1 = d.nY1, hz = d.hz, hx = d.hx, hy = d.hy;
-  const bool ny_even = (d.Ny & 1) == 0;
-  const int reg_rows = ny_even ? nY1 - 1 : nY1;
-  const int nreg = d.Nx * reg_rows;
-  const int npair = ny_even ? hx + 1 : 0;
-  // the y-Nyquist pairs take four passes each: schedule them first
-  const int slot = tile * ngrp + grp;
-  if (slot >= nreg + npair) return;
-  const int item = slot < npair ? nreg + slot : slot - npair;
-  const int LB = ner_buf_len(d);
-  const int LZ = padded_len(Nz);
-  float2 *bufA = reinterpret_cast<float2 *>(smem_f4) + (size_t)grp * (2 * LB + LZ);
-  float2 *bufB = bufA + LB;
-  float2 *Fs = bufB + LB;
-  const float scale = d.scale;
-
-  // columns handled by this item (one, or a pair on the y-Nyquist row)
-  int jxs[2], ncol, iy;
-  bool zero_row0 = false;
-  if (item < nreg) {
-    jxs[0] = item / reg_rows - hx;
-    iy = item % reg_rows;
-    ncol = 1;
-  } else {
-    const int g = item - nreg;
-    iy = hy;
-    if (g == 0) {
-      jxs[0] = 0;
-      ncol = 1;
-    } else if ((d.Nx & 1) == 0 && g == hx) {
-      jxs[0] = -hx;
-      ncol = 1;
-      zero_row0 = true;  // G1 row jx = -hx is read by no column of this row
-    } else {
-      jxs[0] = g;
-      jxs[1] = -g;
-      ncol = 2;
-    }
+  const int CB = d.ner_cb;
+  const int Nt = d.Nt, Mt = d.Mt, Nz = d.Nz, nY1 = d.nY1, nc = d.nc, hz = d.hz, hx = d.hx;
+  const int nslots = ner_adj_slots(d);
+  if (tile * CB >= nslots) return;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  float2 *H = reinterpret_cast<float2 *>(smem_f4);  // [Mt][CB]
+  float2 *Fs = H + (size_t)Mt * CB;                 // [Nz][CB]
+  if (tid < CB) {
+    const int v = tile * CB + tid;
+    slots[tid] = v < nslots ? adj_slot(d, v) : NerSlot{};
   }
-  // rows written so far by this item (to store first, then accumulate)
-  int written[4];
-  int nwritten = 0;
-  for (int c = 0; c < ncol; ++c) {
-    const ColInfo ci = col_info(d, jxs[c], iy);
-    const bool nyq = ci.xnyq || ci.ynyq;
-    const float2 *src = d.Fz + ((size_t)(jxs[c] + hx) * nY1 + iy) * Nz;
-    copy_unrolled<4, float2>(
-        Nz, t, G, [&](int z) { return src[z]; }, [&](int z, float2 v) { Fs[pad32(z)] = v; });
-    group_sync(bar, G);
-    const float2 *Fr = fft_pingpong<-1>(Fs, bufB, d.fNz, d.tw, t, G, bar);
-    if (Fr != Fs) {  // keep the depth spectrum in Fs: both H buffers are needed below
-      for (int z = t; z < Nz; z += G) Fs[pad32(z)] = Fr[pad32(z)];
-      group_sync(bar, G);
-    }
-    for (int pass = 0; pass < (nyq ? 2 : 1); ++pass) {
-      for (int p = t; p < padded_len(Mt); p += G) bufA[p] = make_float2(0.f, 0.f);
-      group_sync(bar, G);
+  __syncthreads();
+  copy_unrolled<4, float2>(
+      Nz * CB, tid, nthr,
+      [&](int idx) {
+        const int b = idx / Nz, z = idx - b * Nz;
+        const NerSlot sl = slots[b];
+        if (sl.kind == 0) return make_float2(0.f, 0.f);
+        return d.Fz[((size_t)(sl.jx + hx) * nY1 + sl.iy) * Nz + z];
+      },
+      [&](int idx, float2 v) {
+        const int b = idx / Nz, z = idx - b * Nz;
+        Fs[z * CB + b] = v;
+      });
+  for (int idx = tid; idx < Mt * CB; idx += nthr) H[idx] = make_float2(0.f, 0.f);
+  __syncthreads();
+  fft_smem<-1>(Fs, CB, CB, d.fNz, d.tw, tid, nthr);
 #pragma unroll 1
-      for (int il = t; il < Nz; il += G) {
-        const int l = il - hz;
-        if (l == 0 && (ci.jx != 0 || ci.jy != 0)) continue;
-        const ff tau = tau_of(d, ci.jx, ci.jy, l);
-        const float wgt = weight_of(d, tau, l) * scale;
-        const bool lnyq = ((Nz & 1) == 0) && (l == -hz);
-        const float2 v = cscale(Fs[pad32(wrap(l, Nz))], wgt);
-        if (!nyq) {
-          if (!lnyq) {
-            ner_spread<W>(bufA, tau, v, d, ht);
-          } else {
-            const float2 hv = cscale(v, 0.5f);
-            ner_spread<W>(bufA, tau, hv, d, ht);
-            ner_spread<W>(bufA, ff_neg(tau), hv, d, ht);
-          }
-        } else {
-          ner_spread<W>(bufA, (pass == 1 && lnyq) ? ff_neg(tau) : tau, cscale(v, 0.5f), d, ht);
-        }
+  for (int idx = tid; idx < Nz * CB; idx += nthr) {
+    const int il = idx / CB, b = idx - il * CB;
+    const NerSlot sl = slots[b];
+    if (sl.kind == 0) continue;
+    const ColInfo ci = col_info(d, sl.jx, sl.iy);
+    const bool nyq = ci.xnyq || ci.ynyq;
+    const int l = il - hz;
+    if (l == 0 && (ci.jx != 0 || ci.jy != 0)) continue;
+    const ff tau = tau_of(d, ci.jx, ci.jy, l);
+    const float wgt = weight_of(d, tau, l) * d.scale;
+    const bool lnyq = ((Nz & 1) == 0) && (l == -hz);
+    const float2 v = cscale(Fs[wrap(l, Nz) * CB + b], wgt);
+    float2 *Hb = H + b;
+    if (!nyq) {
+      if (!lnyq) {
+        ner_spread<W>(Hb, CB, tau, v, d, ht);
+      } else {
+        const float2 hv = cscale(v, 0.5f);
+        ner_spread<W>(Hb, CB, tau, hv, d, ht);
+        ner_spread<W>(Hb, CB, ff_neg(tau), hv, d, ht);
       }
-      group_sync(bar, G);
-      const float2 *H = fft_pingpong<+1>(bufA, bufB, d.fMt, d.tw, t, G, bar);
-      // the A source of a y-Nyquist column is the conjugate of its G1 row
-      const int row = pass == 0 ? ci.rowA : ci.rowB;
-      const bool cj = (pass == 0) && ci.ynyq;
-      bool first = true;
-      for (int k = 0; k < nwritten; ++k) first = first && (written[k] != row);
-      float2 *dst = d.G1 + ((size_t)row * nY1 + iy) * Nt;
-      for (int n = t; n < Nt; n += G) {
-        float2 v = adj_sample(d, H, n);
-        if (cj) v.y = -v.y;
-        dst[n] = first ? v : cadd(dst[n], v);
-      }
-      if (first) written[nwritten++] = row;
-      group_sync(bar, G);
+    } else {
+      ner_spread<W>(Hb, CB, (sl.src == 1 && lnyq) ? ff_neg(tau) : tau, cscale(v, 0.5f), d, ht);
     }
   }
-  if (zero_row0) {
-    float2 *dst = d.G1 + ((size_t)0 * nY1 + iy) * Nt;
-    for (int n = t; n < Nt; n += G) dst[n] = make_float2(0.f, 0.f);
+  __syncthreads();
+  fft_smem<+1>(H, CB, CB, d.fMt, d.tw, tid, nthr);
+  for (int idx = tid; idx < Nt * CB; idx += nthr) {
+    const int b = idx / Nt, n = idx - b * Nt;
+    const NerSlot sl = slots[b];
+    if (sl.kind != 1 && sl.kind != 2) continue;
+    const int p = wrap(n - nc, Mt);
+    const float sc = __ldg(d.invpht + n);
+    // the A source of a y-Nyquist column is the conjugate of its G1 row
+    const ColInfo ci = col_info(d, sl.jx, sl.iy);
+    float2 v = cscale(H[p * CB + b], sc);
+    if (sl.src == 0 && ci.ynyq) v.y = -v.y;
+    if (sl.kind == 2) {
+      const NerSlot s2 = slots[b + 1];
+      const ColInfo c2 = col_info(d, s2.jx, s2.iy);
+      float2 v2 = cscale(H[p * CB + b + 1], sc);
+      if (s2.src == 0 && c2.ynyq) v2.y = -v2.y;
+      v = cadd(v, v2);
+    }
+    const int row = sl.src == 0 ? ci.rowA : ci.rowB;
+    d.G1[((size_t)row * nY1 + sl.iy) * Nt + n] = v;
+    if (sl.zero_row0) d.G1[((size_t)0 * nY1 + sl.iy) * Nt + n] = make_float2(0.f, 0.f);
   }
 }
 
 }  // namespace
 
-int blocks_ner(const InstDesc &d) {
-  const int ngrp = kThreadsNer / d.ner_group;
-  return (d.Nx * d.nY1 + ngrp - 1) / ngrp;
-}
-size_t smem_ner(const InstDesc &d) {
-  return (size_t)(kThreadsNer / d.ner_group) * (2 * ner_buf_len(d) + padded_len(d.Nz)) * sizeof(float2);
-}
-int blocks_ner_adj(const InstDesc &d) {
-  const int ngrp = kThreadsNer / d.ner_group;
-  const bool ny_even = (d.Ny & 1) == 0;
-  const int items = d.Nx * (ny_even ? d.nY1 - 1 : d.nY1) + (ny_even ? d.hx + 1 : 0);
-  return (items + ngrp - 1) / ngrp;
-}
-size_t smem_ner_adj(const InstDesc &d) {
-  return (size_t)(kThreadsNer / d.ner_group) * (2 * ner_buf_len(d) + padded_len(d.Nz)) * sizeof(float2);
-}
+int blocks_ner(const InstDesc &d) { return (ner_fwd_slots(d) + d.ner_cb - 1) / d.ner_cb; }
+int blocks_ner_adj(const InstDesc &d) { return (ner_adj_slots(d) + d.ner_cb - 1) / d.ner_cb; }
+size_t smem_ner(const InstDesc &d) { return (size_t)(d.Mt + d.Nz) * d.ner_cb * sizeof(float2); }
 
 template <typename K>
 static cudaError_t set_smem_ner(K kernel, size_t smem) {
@@ -398,11 +485,11 @@ static cudaError_t launch_ner_w(const Launch &L, const HornerTable &ht, int whic
   if (which == 1) {
     e = set_smem_ner(k_ner_adj<W>, L.smem);
     if (e != cudaSuccess) return e;
-    k_ner_adj<W><<<L.nblocks, kThreadsNer, L.smem, L.stream>>>(L.descs, L.work, ht);
+    k_ner_adj<W><<<L.nblocks, L.threads, L.smem, L.stream>>>(L.descs, L.work, ht);
   } else {
     e = set_smem_ner(k_ner<W, false>, L.smem);
     if (e != cudaSuccess) return e;
-    k_ner<W, false><<<L.nblocks, kThreadsNer, L.smem, L.stream>>>(L.descs, L.work, ht);
+    k_ner<W, false><<<L.nblocks, L.threads, L.smem, L.stream>>>(L.descs, L.work, ht);
   }
   return cudaGetLastError();
 }
@@ -425,7 +512,7 @@ cudaError_t launch_cubic(const Launch &L) {
   HornerTable ht{};
   cudaError_t e = set_smem_ner(k_ner<8, true>, L.smem);
   if (e != cudaSuccess) return e;
-  k_ner<8, true><<<L.nblocks, kThreadsNer, L.smem, L.stream>>>(L.descs, L.work, ht);
+  k_ner<8, true><<<L.nblocks, L.threads, L.smem, L.stream>>>(L.descs, L.work, ht);
   return cudaGetLastError();
 }
 

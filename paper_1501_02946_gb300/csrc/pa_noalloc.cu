@@ -98,8 +98,9 @@ extern "C" int pa_position_grad_noalloc(pa_plan *plan, const float *g_dev, const
   L.nblocks = pa::blocks_imgx(h);
   L.smem = pa::smem_imgx(h);
   if ((rc = launched(pa::launch_imgx(L, true), "imgx_adj")) != PA_OK) return rc;
+  L.threads = h.ner_threads;
   L.nblocks = pa::blocks_ner_adj(h);
-  L.smem = pa::smem_ner_adj(h);
+  L.smem = pa::smem_ner(h);
   if ((rc = launched(pa::launch_ner_stage(L, v.width, *v.ht, 1), "ner_adj")) != PA_OK) return rc;
 
   L.nblocks = pa::blocks_colfft(h);

@@ -216,6 +216,7 @@ struct pa_batch {
     size_t smem = 0;
   } st_spread, st_rowfft, st_col, st_ner, st_imgx, st_imgy;
   int spread_spl = 4;
+  int ner_threads = 0;
   HornerTable ht{};
   int width = 8;
   cudaGraphExec_t exec = nullptr;
@@ -439,6 +440,7 @@ int run_forward(pa_plan *P, const IoPtrs &io, cudaStream_t s, bool cubic) {
   L.nblocks = pa::blocks_colfft(h);
   L.smem = pa::smem_colfft(h);
   if ((rc = timed(P, 1, s, [&] { return pa::launch_colfft(L, false); }, "colfft")) != PA_OK) return rc;
+  L.threads = h.ner_threads;
   L.nblocks = pa::blocks_ner(h);
   L.smem = pa::smem_ner(h);
   if (cubic) {
@@ -466,8 +468,9 @@ int run_adjoint(pa_plan *P, const IoPtrs &io, cudaStream_t s, bool grad) {
   L.nblocks = pa::blocks_imgx(h);
   L.smem = pa::smem_imgx(h);
   if ((rc = timed(P, 6, s, [&] { return pa::launch_imgx(L, true); }, "imgx_adj")) != PA_OK) return rc;
+  L.threads = h.ner_threads;
   L.nblocks = pa::blocks_ner_adj(h);
-  L.smem = pa::smem_ner_adj(h);
+  L.smem = pa::smem_ner(h);
   if ((rc = timed(P, 7, s, [&] { return pa::launch_ner_stage(L, P->w, P->ht, 1); }, "ner_adj")) != PA_OK) return rc;
 
   L.nblocks = pa::blocks_colfft(h);
@@ -581,6 +584,21 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
   h.nchunk_adj = int((Nt + pa::kInterpNC - 1) / pa::kInterpNC);
   h.sigma = sigma;
 
+  // NER block size: the smallest for which the column transforms have an
+  // in-place schedule
+  h.ner_threads = 0;
+  for (int nt : {128, 256}) {
+    FftPlan a, b, c;
+    if (make_fft_plan(int(Mt), nt, a) && make_fft_plan(int(Nz), nt, b) && make_fft_plan(int(Nt), nt, c)) {
+      h.ner_threads = nt;
+      break;
+    }
+  }
+  if (h.ner_threads == 0) {
+    delete P;
+    return fail(PA_ERR_UNSUPPORTED_SIZE, "time or depth transform too long for one block");
+  }
+
   // FFT schedules and twiddles
   struct Len {
     FftPlan *fp;
@@ -588,11 +606,11 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
     int nthr;
   } lens[] = {{&h.fMy, int(My), 256},
               {&h.fMx, int(Mx), 256},
-              {&h.fMt, int(Mt), 256},
-              {&h.fNz, int(Nz), 256},
+              {&h.fMt, int(Mt), h.ner_threads},
+              {&h.fNz, int(Nz), h.ner_threads},
               {&h.fNx, int(Nx), 256},
               {&h.fNy, int(Ny), 256},
-              {&h.fNt, int(Nt), 256}};
+              {&h.fNt, int(Nt), h.ner_threads}};
   std::vector<float2> tw;
   for (auto &ln : lens) {
     if (!make_fft_plan(ln.L, ln.nthr, *ln.fp)) {
@@ -605,23 +623,10 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
       tw.push_back(make_float2(float(std::cos(a)), float(std::sin(a))));
     }
   }
-  // threads per column of the NER kernels: smallest group that runs every
-  // stage of the column transforms in one round
-  h.ner_group = 0;
-  for (int G : {128, 256}) {
-    bool ok = true;
-    for (const FftPlan *fp : {&h.fMt, &h.fNz, &h.fNt})
-      for (int st = 0; st < fp->nst; ++st)
-        if (fp->L / fp->radix[st] > G * ipt_of(fp->radix[st])) ok = false;
-    if (ok) {
-      h.ner_group = G;
-      break;
-    }
-  }
-  if (h.ner_group == 0) {
-    delete P;
-    return fail(PA_ERR_UNSUPPORTED_SIZE, "time transforms too long for one block");
-  }
+  // NER blocks: ner_cb (column, source) transforms side by side, at least
+  // two (the two transforms of a Nyquist column share a block); four when
+  // their buffers stay within 48 KB
+  h.ner_cb = (size_t(Mt) + size_t(Nz)) * 4 * sizeof(float2) <= 48 * 1024 ? 4 : 2;
 
   // deconvolution tables and time-frequency constants
   const Kb kb(width, sigma);
@@ -641,7 +646,7 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
   fit_horner(kb, horner_degree(width), P->ht);
 
   // shared-memory limits
-  const size_t smems[] = {pa::smem_rowfft(h), pa::smem_colfft(h),  pa::smem_ner(h),  pa::smem_ner_adj(h),
+  const size_t smems[] = {pa::smem_rowfft(h), pa::smem_colfft(h), pa::smem_ner(h),
                           pa::smem_rowifft(h), pa::smem_imgx(h), pa::smem_imgy(h), pa::smem_interp(h)};
   for (size_t sm : smems)
     if (sm > P->smem_limit) {
@@ -902,6 +907,8 @@ int pa_batch_create(pa_batch **out, int n, pa_plan *const *plans, void *stream) 
   B->st_spread.nblocks = int(work.size() - B->st_spread.off);
   add_stage(B->st_rowfft, pa::blocks_rowfft, pa::smem_rowfft);
   add_stage(B->st_col, pa::blocks_colfft, pa::smem_colfft);
+  // one NER block size for the whole batch (the largest any instance needs)
+  for (int i = 0; i < n; ++i) B->ner_threads = std::max(B->ner_threads, descs[i].ner_threads);
   add_stage(B->st_ner, pa::blocks_ner, pa::smem_ner);
   add_stage(B->st_imgx, pa::blocks_imgx, pa::smem_imgx);
   add_stage(B->st_imgy, pa::blocks_imgy, pa::smem_imgy);
@@ -946,6 +953,7 @@ static int batch_launches(pa_batch *B, cudaStream_t s) {
   L.work = B->d_work + B->st_ner.off;
   L.nblocks = B->st_ner.nblocks;
   L.smem = B->st_ner.smem;
+  L.threads = B->ner_threads;
   if ((rc = check_launch(pa::launch_ner(L, B->width, B->ht, false), "batch ner")) != PA_OK) return rc;
   L.work = B->d_work + B->st_imgx.off;
   L.nblocks = B->st_imgx.nblocks;
