@@ -231,7 +231,19 @@ __device__ __forceinline__ void group_sync(int bar_id, int nthr) {
   }
 }
 
-template <int R, int DIR>
+// Element row e of a transform buffer, with one pad row after every 2^PADSH
+// rows when PADSH > 0 (spreads strided accesses of narrow batches over the
+// shared-memory banks).
+template <int PADSH>
+__host__ __device__ __forceinline__ int pad_row(int e) {
+  return PADSH > 0 ? e + (e >> PADSH) : e;
+}
+template <int PADSH>
+__host__ __device__ __forceinline__ int padded_rows(int L) {
+  return PADSH > 0 ? L + (L >> PADSH) + 1 : L;
+}
+
+template <int R, int DIR, int PADSH>
 __device__ __forceinline__ void fft_stage(float2 *buf, int estride, int nb, int L, int Ns,
                                           const float2 *__restrict__ tw, int tid, int nthr, int bar_id = 0) {
   constexpr int IPT = Ipt<R>::v;
@@ -252,7 +264,7 @@ __device__ __forceinline__ void fft_stage(float2 *buf, int estride, int nb, int 
         const int k = j % Ns;
 #pragma unroll
         for (int t = 0; t < R; ++t) {
-          float2 x = buf[(j + t * nj) * estride + b];
+          float2 x = buf[pad_row<PADSH>(j + t * nj) * estride + b];
           if (t > 0 && k > 0) {
             float2 w = __ldg(tw + t * k * twstep);
             if (DIR > 0) w.y = -w.y;
@@ -273,27 +285,102 @@ __device__ __forceinline__ void fft_stage(float2 *buf, int estride, int nb, int 
         Dft<R, DIR>::run(v[it]);
         const int o = (j / Ns) * Ns * R + k;
 #pragma unroll
-        for (int t = 0; t < R; ++t) buf[(o + t * Ns) * estride + b] = v[it][t];
+        for (int t = 0; t < R; ++t) buf[pad_row<PADSH>(o + t * Ns) * estride + b] = v[it][t];
       }
     }
     group_sync(bar_id, nthr);
   }
 }
 
+// The same stage when the length, the sequence count and the thread count are
+// powers of two: every index split is a shift or a mask, and a thread keeps
+// one sequence (b) for all its items of a round.
+__device__ __forceinline__ int ilog2_pow2(int x) { return __ffs(x) - 1; }
+
+template <int R, int DIR, int PADSH>
+__device__ __forceinline__ void fft_stage_p2(float2 *buf, int estride, int lgnb, int lgL, int lgNs,
+                                             const float2 *__restrict__ tw, int tid, int lgT, int bar_id) {
+  constexpr int IPT = Ipt<R>::v;
+  constexpr int LGR = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
+  constexpr int LGIPT = IPT == 1 ? 0 : (IPT == 2 ? 1 : 2);
+  const int lgnj = lgL - LGR;
+  const int nj = 1 << lgnj;
+  int lgnbr = lgT + LGIPT - lgnj;  // sequences per round (the plan keeps it >= 0)
+  if (lgnbr > lgnb) lgnbr = lgnb;
+  if (lgnbr > lgT) lgnbr = lgT;
+  if (lgnbr < 0) lgnbr = 0;
+  const int nbr = 1 << lgnbr;
+  const int j0 = tid >> lgnbr, jstep = 1 << (lgT - lgnbr);
+  const int kmask = (1 << lgNs) - 1;
+  const int lgtw = lgL - lgNs - LGR;
+  for (int b0 = 0; b0 < (1 << lgnb); b0 += nbr) {
+    const int b = b0 + (tid & (nbr - 1));
+    float2 v[IPT][R];
+#pragma unroll
+    for (int it = 0; it < IPT; ++it) {
+      const int j = j0 + it * jstep;
+      if (j < nj) {
+        const int k = j & kmask;
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+          float2 x = buf[pad_row<PADSH>(j + (t << lgnj)) * estride + b];
+          if (t > 0) {  // tw[0] = 1 leaves x unchanged
+            float2 w = __ldg(tw + ((t * k) << lgtw));
+            if (DIR > 0) w.y = -w.y;
+            x = cmul(x, w);
+          }
+          v[it][t] = x;
+        }
+      }
+    }
+    group_sync(bar_id, 1 << lgT);
+#pragma unroll
+    for (int it = 0; it < IPT; ++it) {
+      const int j = j0 + it * jstep;
+      if (j < nj) {
+        const int k = j & kmask;
+        Dft<R, DIR>::run(v[it]);
+        const int o = ((j >> lgNs) << (lgNs + LGR)) + k;
+#pragma unroll
+        for (int t = 0; t < R; ++t) buf[pad_row<PADSH>(o + (t << lgNs)) * estride + b] = v[it][t];
+      }
+    }
+    group_sync(bar_id, 1 << lgT);
+  }
+}
+
 // Whole transform y[k] = sum_i x[i] exp(DIR 2 pi i i k / L), unnormalised,
-// in place in shared memory.  All threads of the block must call it.
-template <int DIR>
+// in place in shared memory (element i of sequence b at
+// buf[pad_row<PADSH>(i) * estride + b]).  All threads of the block must call it.
+template <int DIR, int PADSH = 0>
 __device__ void fft_smem(float2 *buf, int estride, int nb, const FftPlan &fp, const float2 *__restrict__ twbase,
                          int tid, int nthr, int bar_id = 0) {
   const float2 *tw = twbase + fp.tw;
   const int L = fp.L;
   const int nst = fp.nst;
   int Ns = 1, s = 0;
+  if (((L & (L - 1)) | (nb & (nb - 1)) | (nthr & (nthr - 1))) == 0) {
+    // power-of-two schedule: radices 16, 8, 4, 2 in that order
+    const int lgL = ilog2_pow2(L), lgnb = ilog2_pow2(nb), lgT = ilog2_pow2(nthr);
+    int lgNs = 0;
+#define PA_FFT_RUN_P2(R, LGR)                                                    \
+  while (s < nst && fp.radix[s] == R) {                                          \
+    fft_stage_p2<R, DIR, PADSH>(buf, estride, lgnb, lgL, lgNs, tw, tid, lgT, bar_id);  \
+    lgNs += LGR;                                                                 \
+    ++s;                                                                         \
+  }
+    PA_FFT_RUN_P2(16, 4)
+    PA_FFT_RUN_P2(8, 3)
+    PA_FFT_RUN_P2(4, 2)
+    PA_FFT_RUN_P2(2, 1)
+#undef PA_FFT_RUN_P2
+    return;
+  }
   // The schedule lists radices in the order 16, 8, 4, 2, 3, 5, 7; one loop per
   // radix keeps the register allocation of each radix separate.
 #define PA_FFT_RUN(R)                                                   \
   while (s < nst && fp.radix[s] == R) {                                 \
-    fft_stage<R, DIR>(buf, estride, nb, L, Ns, tw, tid, nthr, bar_id);  \
+    fft_stage<R, DIR, PADSH>(buf, estride, nb, L, Ns, tw, tid, nthr, bar_id);  \
     Ns *= R;                                                            \
     ++s;                                                                \
   }
@@ -307,69 +394,6 @@ __device__ void fft_smem(float2 *buf, int estride, int nb, const FftPlan &fp, co
 #undef PA_FFT_RUN
 }
 
-// Out-of-place variant for single sequences stored with pad32 indexing: each
-// stage reads `src` and writes `dst` one butterfly at a time, so a thread
-// holds only R values at once; the buffers swap after every stage.  Returns
-// the buffer that holds the result (src or dst).
-// Shared-memory index with one pad element after every 32, which spreads the
-// strided Stockham writes over the banks.
-__host__ __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
-__host__ __device__ __forceinline__ int padded_len(int L) { return L + (L >> 5) + 1; }
-
-template <int R, int DIR>
-__device__ __forceinline__ void fft_stage_oop(const float2 *src, float2 *dst, int L, int Ns,
-                                              const float2 *__restrict__ tw, int tid, int nthr) {
-  const int nj = L / R;
-  const int twstep = L / (Ns * R);
-#pragma unroll 1
-  for (int j = tid; j < nj; j += nthr) {
-    const int k = j % Ns;
-    float2 v[R];
-#pragma unroll
-    for (int t = 0; t < R; ++t) {
-      float2 x = src[pad32(j + t * nj)];
-      if (t > 0 && k > 0) {
-        float2 w = __ldg(tw + t * k * twstep);
-        if (DIR > 0) w.y = -w.y;
-        x = cmul(x, w);
-      }
-      v[t] = x;
-    }
-    Dft<R, DIR>::run(v);
-    const int o = (j / Ns) * Ns * R + k;
-#pragma unroll
-    for (int t = 0; t < R; ++t) dst[pad32(o + t * Ns)] = v[t];
-  }
-}
-
-template <int DIR>
-__device__ float2 *fft_pingpong(float2 *a, float2 *b, const FftPlan &fp, const float2 *__restrict__ twbase, int tid,
-                                int nthr, int bar_id) {
-  const float2 *tw = twbase + fp.tw;
-  const int L = fp.L;
-  const int nst = fp.nst;
-  int Ns = 1, s = 0;
-  float2 *src = a, *dst = b;
-#define PA_FFT_OOP(R)                                                \
-  while (s < nst && fp.radix[s] == R) {                              \
-    fft_stage_oop<R, DIR>(src, dst, L, Ns, tw, tid, nthr);           \
-    group_sync(bar_id, nthr);                                        \
-    float2 *x = src;                                                 \
-    src = dst;                                                       \
-    dst = x;                                                         \
-    Ns *= R;                                                         \
-    ++s;                                                             \
-  }
-  PA_FFT_OOP(16)
-  PA_FFT_OOP(8)
-  PA_FFT_OOP(4)
-  PA_FFT_OOP(2)
-  PA_FFT_OOP(3)
-  PA_FFT_OOP(5)
-  PA_FFT_OOP(7)
-#undef PA_FFT_OOP
-  return src;
-}
 
 // n items moved by the block with U loads in flight per thread: every thread
 // first issues up to U independent loads ld(i), then stores them st(i, v).

@@ -4,7 +4,7 @@
 //
 // A block owns CB columns j = (jx, jy) of the half spectrum and transforms
 // them together (batched in-place FFTs in shared memory, element n of slot b
-// at [n*CB + b]).  Forward, per column:
+// at [prow(n)*CB + b], prow adding a pad row per 16).  Forward, per column:
 //   load G1(j, n) / phihat((n - nc)/Mt) at n' = n - nc (the paper's centred
 //   theta = 2 pi n / N - pi), zero-pad to Mt = sigma Nt, FFT, evaluate at the
 //   nz non-integer frequencies tau(j, l) = omega Nt dt / (2 pi) with w window
@@ -25,6 +25,8 @@ namespace pa {
 namespace {
 
 constexpr int kNerMaxCB = 4;  // most columns per block
+constexpr int kNerPad = 4;    // one pad row per 16 rows of the [n][CB] buffers
+__device__ __forceinline__ int prow(int e) { return pad_row<kNerPad>(e); }
 
 
 template <int W>
@@ -87,7 +89,7 @@ __device__ __forceinline__ void window_taps(float fr, const HornerTable &ht, flo
   }
 }
 
-// H: element k of the transformed column at H[k * CB] (slot-offset pointer).
+// H: element k of the transformed column at H[prow(k) * CB] (slot-offset pointer).
 template <int W>
 __device__ __forceinline__ float2 ner_interp(const float2 *H, int CB, ff tau, const InstDesc &d,
                                              const HornerTable &ht) {
@@ -101,7 +103,7 @@ __device__ __forceinline__ float2 ner_interp(const float2 *H, int CB, ff tau, co
   const int Mt = d.Mt;
 #pragma unroll
   for (int t = 0; t < W; ++t) {
-    const float2 h = H[idx * CB];
+    const float2 h = H[prow(idx) * CB];
     acc.x = fmaf(wt[t], h.x, acc.x);
     acc.y = fmaf(wt[t], h.y, acc.y);
     idx = (idx + 1 == Mt) ? 0 : idx + 1;
@@ -123,8 +125,8 @@ __device__ __forceinline__ void ner_spread(float2 *H, int CB, ff tau, float2 v, 
   const int Mt = d.Mt;
 #pragma unroll
   for (int t = 0; t < W; ++t) {
-    atomicAdd(&H[idx * CB].x, wt[t] * vv.x);
-    atomicAdd(&H[idx * CB].y, wt[t] * vv.y);
+    atomicAdd(&H[prow(idx) * CB].x, wt[t] * vv.x);
+    atomicAdd(&H[prow(idx) * CB].y, wt[t] * vv.y);
     idx = (idx + 1 == Mt) ? 0 : idx + 1;
   }
 }
@@ -145,7 +147,7 @@ __device__ __forceinline__ float2 cubic_interp(const float2 *H, int CB, ff tau, 
   int idx = p0;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
-    const float2 h = H[idx * CB];
+    const float2 h = H[prow(idx) * CB];
     acc.x = fmaf(wt[t], h.x, acc.x);
     acc.y = fmaf(wt[t], h.y, acc.y);
     idx = (idx + 1 == Nt) ? 0 : idx + 1;
@@ -302,8 +304,8 @@ __global__ void __launch_bounds__(256, 2) k_ner(const InstDesc *__restrict__ des
   if (tile * CB >= nslots) return;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int L = CUBIC ? Nt : Mt;
-  float2 *H = reinterpret_cast<float2 *>(smem_f4);  // [L][CB]
-  float2 *Fs = H + (size_t)L * CB;                  // [Nz][CB]
+  float2 *H = reinterpret_cast<float2 *>(smem_f4);     // [prow(L)][CB]
+  float2 *Fs = H + (size_t)padded_rows<kNerPad>(Mt) * CB;  // [prow(Nz)][CB]
   if (tid < CB) {
     const int v = tile * CB + tid;
     slots[tid] = v < nslots ? fwd_slot(d, v) : NerSlot{};
@@ -323,15 +325,16 @@ __global__ void __launch_bounds__(256, 2) k_ner(const InstDesc *__restrict__ des
       },
       [&](int idx, float2 a) {
         const int b = idx / Nt, n = idx - b * Nt;
-        H[(CUBIC ? n : wrap(n - nc, Mt)) * CB + b] = a;
+        H[prow(CUBIC ? n : wrap(n - nc, Mt)) * CB + b] = a;
       });
   if (!CUBIC)
-    for (int idx = tid; idx < (Mt - Nt) * CB; idx += nthr) H[(Nt - nc) * CB + idx] = make_float2(0.f, 0.f);
+    for (int idx = tid; idx < (Mt - Nt) * CB; idx += nthr)
+      H[prow(Nt - nc + idx / CB) * CB + idx % CB] = make_float2(0.f, 0.f);
   __syncthreads();
   if (CUBIC) {
-    fft_smem<-1>(H, CB, CB, d.fNt, d.tw, tid, nthr);
+    fft_smem<-1, kNerPad>(H, CB, CB, d.fNt, d.tw, tid, nthr);
   } else {
-    fft_smem<-1>(H, CB, CB, d.fMt, d.tw, tid, nthr);
+    fft_smem<-1, kNerPad>(H, CB, CB, d.fMt, d.tw, tid, nthr);
   }
 #pragma unroll 1
   for (int idx = tid; idx < Nz * CB; idx += nthr) {
@@ -359,21 +362,22 @@ __global__ void __launch_bounds__(256, 2) k_ner(const InstDesc *__restrict__ des
       }
       F = cscale(v, (nyq || two) ? 0.5f * wgt : wgt);
     }
-    Fs[wrap(l, Nz) * CB + b] = F;
+    Fs[prow(wrap(l, Nz)) * CB + b] = F;
   }
   __syncthreads();
   // a two-source column: the leading slot takes the sum
   for (int idx = tid; idx < Nz * CB; idx += nthr) {
-    const int b = idx % CB;
-    if (slots[b].kind == 2) Fs[idx] = cadd(Fs[idx], Fs[idx + 1]);
+    const int z = idx / CB, b = idx - z * CB;
+    if (slots[b].kind == 2) Fs[prow(z) * CB + b] = cadd(Fs[prow(z) * CB + b], Fs[prow(z) * CB + b + 1]);
   }
   __syncthreads();
   // slots without an output hold stale values: transformed, never stored
-  fft_smem<+1>(Fs, CB, CB, d.fNz, d.tw, tid, nthr);
+  fft_smem<+1, kNerPad>(Fs, CB, CB, d.fNz, d.tw, tid, nthr);
   for (int idx = tid; idx < Nz * CB; idx += nthr) {
     const int b = idx / Nz, z = idx - b * Nz;
     const NerSlot sl = slots[b];
-    if (sl.kind == 1 || sl.kind == 2) d.Fz[((size_t)(sl.jx + hx) * nY1 + sl.iy) * Nz + z] = Fs[z * CB + b];
+    if (sl.kind == 1 || sl.kind == 2)
+      d.Fz[((size_t)(sl.jx + hx) * nY1 + sl.iy) * Nz + z] = Fs[prow(z) * CB + b];
   }
 }
 
@@ -394,8 +398,8 @@ __global__ void __launch_bounds__(256, 2) k_ner_adj(const InstDesc *__restrict__
   const int nslots = ner_adj_slots(d);
   if (tile * CB >= nslots) return;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  float2 *H = reinterpret_cast<float2 *>(smem_f4);  // [Mt][CB]
-  float2 *Fs = H + (size_t)Mt * CB;                 // [Nz][CB]
+  float2 *H = reinterpret_cast<float2 *>(smem_f4);     // [prow(Mt)][CB]
+  float2 *Fs = H + (size_t)padded_rows<kNerPad>(Mt) * CB;  // [prow(Nz)][CB]
   if (tid < CB) {
     const int v = tile * CB + tid;
     slots[tid] = v < nslots ? adj_slot(d, v) : NerSlot{};
@@ -411,11 +415,11 @@ __global__ void __launch_bounds__(256, 2) k_ner_adj(const InstDesc *__restrict__
       },
       [&](int idx, float2 v) {
         const int b = idx / Nz, z = idx - b * Nz;
-        Fs[z * CB + b] = v;
+        Fs[prow(z) * CB + b] = v;
       });
-  for (int idx = tid; idx < Mt * CB; idx += nthr) H[idx] = make_float2(0.f, 0.f);
+  for (int idx = tid; idx < padded_rows<kNerPad>(Mt) * CB; idx += nthr) H[idx] = make_float2(0.f, 0.f);
   __syncthreads();
-  fft_smem<-1>(Fs, CB, CB, d.fNz, d.tw, tid, nthr);
+  fft_smem<-1, kNerPad>(Fs, CB, CB, d.fNz, d.tw, tid, nthr);
 #pragma unroll 1
   for (int idx = tid; idx < Nz * CB; idx += nthr) {
     const int il = idx / CB, b = idx - il * CB;
@@ -428,7 +432,7 @@ __global__ void __launch_bounds__(256, 2) k_ner_adj(const InstDesc *__restrict__
     const ff tau = tau_of(d, ci.jx, ci.jy, l);
     const float wgt = weight_of(d, tau, l) * d.scale;
     const bool lnyq = ((Nz & 1) == 0) && (l == -hz);
-    const float2 v = cscale(Fs[wrap(l, Nz) * CB + b], wgt);
+    const float2 v = cscale(Fs[prow(wrap(l, Nz)) * CB + b], wgt);
     float2 *Hb = H + b;
     if (!nyq) {
       if (!lnyq) {
@@ -443,12 +447,12 @@ __global__ void __launch_bounds__(256, 2) k_ner_adj(const InstDesc *__restrict__
     }
   }
   __syncthreads();
-  fft_smem<+1>(H, CB, CB, d.fMt, d.tw, tid, nthr);
+  fft_smem<+1, kNerPad>(H, CB, CB, d.fMt, d.tw, tid, nthr);
   for (int idx = tid; idx < Nt * CB; idx += nthr) {
     const int b = idx / Nt, n = idx - b * Nt;
     const NerSlot sl = slots[b];
     if (sl.kind != 1 && sl.kind != 2) continue;
-    const int p = wrap(n - nc, Mt);
+    const int p = prow(wrap(n - nc, Mt));
     const float sc = __ldg(d.invpht + n);
     // the A source of a y-Nyquist column is the conjugate of its G1 row
     const ColInfo ci = col_info(d, sl.jx, sl.iy);
@@ -471,7 +475,9 @@ __global__ void __launch_bounds__(256, 2) k_ner_adj(const InstDesc *__restrict__
 
 int blocks_ner(const InstDesc &d) { return (ner_fwd_slots(d) + d.ner_cb - 1) / d.ner_cb; }
 int blocks_ner_adj(const InstDesc &d) { return (ner_adj_slots(d) + d.ner_cb - 1) / d.ner_cb; }
-size_t smem_ner(const InstDesc &d) { return (size_t)(d.Mt + d.Nz) * d.ner_cb * sizeof(float2); }
+size_t smem_ner(const InstDesc &d) {
+  return (size_t)(padded_rows<kNerPad>(d.Mt) + padded_rows<kNerPad>(d.Nz)) * d.ner_cb * sizeof(float2);
+}
 
 template <typename K>
 static cudaError_t set_smem_ner(K kernel, size_t smem) {

@@ -626,7 +626,8 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
   // NER blocks: ner_cb (column, source) transforms side by side, at least
   // two (the two transforms of a Nyquist column share a block); four when
   // their buffers stay within 48 KB
-  h.ner_cb = (size_t(Mt) + size_t(Nz)) * 4 * sizeof(float2) <= 48 * 1024 ? 4 : 2;
+  h.ner_cb = 4;
+  if (pa::smem_ner(h) > 48 * 1024) h.ner_cb = 2;
 
   // deconvolution tables and time-frequency constants
   const Kb kb(width, sigma);
