@@ -44,6 +44,7 @@ struct InstDesc {
   int nchunk_adj;       // n-chunks of the adjoint NED kernel (gradient partials)
   int ner_cb;           // columns per block of the NER kernels (1, 2 or 4)
   int ner_threads;      // block size of the NER kernels (128 or 256)
+  int ner_lperm;        // adjoint NER depth order il = (i * ner_lperm) mod Nz
 
   FftPlan fMy, fMx, fMt, fNz, fNx, fNy, fNt;
   const float2 *tw;

@@ -311,34 +311,35 @@ __global__ void __launch_bounds__(256, 2) k_ner(const InstDesc *__restrict__ des
     slots[tid] = v < nslots ? fwd_slot(d, v) : NerSlot{};
   }
   __syncthreads();
-  copy_unrolled<4, float2>(
-      Nt * CB, tid, nthr,
-      [&](int idx) {
-        const int b = idx / Nt, n = idx - b * Nt;
-        const NerSlot sl = slots[b];
-        if (sl.kind == 0) return make_float2(0.f, 0.f);
-        const ColInfo ci = col_info(d, sl.jx, sl.iy);
-        const float2 *src = d.G1 + ((size_t)(sl.src == 0 ? ci.rowA : ci.rowB) * nY1 + sl.iy) * Nt;
-        float2 a = src[n];
-        if (sl.src == 0 && ci.ynyq) a.y = -a.y;
-        return CUBIC ? a : cscale(a, __ldg(d.invpht + n));
-      },
-      [&](int idx, float2 a) {
-        const int b = idx / Nt, n = idx - b * Nt;
-        H[prow(CUBIC ? n : wrap(n - nc, Mt)) * CB + b] = a;
-      });
-  if (!CUBIC)
-    for (int idx = tid; idx < (Mt - Nt) * CB; idx += nthr)
-      H[prow(Nt - nc + idx / CB) * CB + idx % CB] = make_float2(0.f, 0.f);
+  // slot b's source row, at n' = n - nc (mod Mt) after 1/phihat; an empty
+  // slot keeps stale values (transformed, never stored)
+  for (int b = 0; b < CB; ++b) {
+    const NerSlot sl = slots[b];
+    if (sl.kind == 0) continue;
+    const ColInfo ci = col_info(d, sl.jx, sl.iy);
+    const float2 *src = d.G1 + ((size_t)(sl.src == 0 ? ci.rowA : ci.rowB) * nY1 + sl.iy) * Nt;
+    const bool cj = sl.src == 0 && ci.ynyq;
+    copy_unrolled<4, float2>(
+        Nt, tid, nthr,
+        [&](int n) {
+          float2 a = src[n];
+          if (cj) a.y = -a.y;
+          return CUBIC ? a : cscale(a, __ldg(d.invpht + n));
+        },
+        [&](int n, float2 a) { H[prow(CUBIC ? n : (n < nc ? n - nc + Mt : n - nc)) * CB + b] = a; });
+    if (!CUBIC)
+      for (int u = tid; u < Mt - Nt; u += nthr) H[prow(Nt - nc + u) * CB + b] = make_float2(0.f, 0.f);
+  }
   __syncthreads();
   if (CUBIC) {
     fft_smem<-1, kNerPad>(H, CB, CB, d.fNt, d.tw, tid, nthr);
   } else {
     fft_smem<-1, kNerPad>(H, CB, CB, d.fMt, d.tw, tid, nthr);
   }
+  const int lgcb = ilog2_pow2(CB);
 #pragma unroll 1
   for (int idx = tid; idx < Nz * CB; idx += nthr) {
-    const int il = idx / CB, b = idx - il * CB;
+    const int il = idx >> lgcb, b = idx & (CB - 1);
     const NerSlot sl = slots[b];
     if (sl.kind == 0) continue;
     const ColInfo ci = col_info(d, sl.jx, sl.iy);
@@ -362,22 +363,21 @@ __global__ void __launch_bounds__(256, 2) k_ner(const InstDesc *__restrict__ des
       }
       F = cscale(v, (nyq || two) ? 0.5f * wgt : wgt);
     }
-    Fs[prow(wrap(l, Nz)) * CB + b] = F;
+    Fs[prow(l < 0 ? l + Nz : l) * CB + b] = F;
   }
   __syncthreads();
   // a two-source column: the leading slot takes the sum
-  for (int idx = tid; idx < Nz * CB; idx += nthr) {
-    const int z = idx / CB, b = idx - z * CB;
-    if (slots[b].kind == 2) Fs[prow(z) * CB + b] = cadd(Fs[prow(z) * CB + b], Fs[prow(z) * CB + b + 1]);
+  for (int b = 0; b < CB; b += 2) {
+    if (slots[b].kind != 2) continue;
+    for (int z = tid; z < Nz; z += nthr) Fs[prow(z) * CB + b] = cadd(Fs[prow(z) * CB + b], Fs[prow(z) * CB + b + 1]);
   }
   __syncthreads();
-  // slots without an output hold stale values: transformed, never stored
   fft_smem<+1, kNerPad>(Fs, CB, CB, d.fNz, d.tw, tid, nthr);
-  for (int idx = tid; idx < Nz * CB; idx += nthr) {
-    const int b = idx / Nz, z = idx - b * Nz;
+  for (int b = 0; b < CB; ++b) {
     const NerSlot sl = slots[b];
-    if (sl.kind == 1 || sl.kind == 2)
-      d.Fz[((size_t)(sl.jx + hx) * nY1 + sl.iy) * Nz + z] = Fs[prow(z) * CB + b];
+    if (sl.kind != 1 && sl.kind != 2) continue;
+    float2 *dst = d.Fz + ((size_t)(sl.jx + hx) * nY1 + sl.iy) * Nz;
+    for (int z = tid; z < Nz; z += nthr) dst[z] = Fs[prow(z) * CB + b];
   }
 }
 
@@ -405,24 +405,24 @@ __global__ void __launch_bounds__(256, 2) k_ner_adj(const InstDesc *__restrict__
     slots[tid] = v < nslots ? adj_slot(d, v) : NerSlot{};
   }
   __syncthreads();
-  copy_unrolled<4, float2>(
-      Nz * CB, tid, nthr,
-      [&](int idx) {
-        const int b = idx / Nz, z = idx - b * Nz;
-        const NerSlot sl = slots[b];
-        if (sl.kind == 0) return make_float2(0.f, 0.f);
-        return d.Fz[((size_t)(sl.jx + hx) * nY1 + sl.iy) * Nz + z];
-      },
-      [&](int idx, float2 v) {
-        const int b = idx / Nz, z = idx - b * Nz;
-        Fs[prow(z) * CB + b] = v;
-      });
+  for (int b = 0; b < CB; ++b) {
+    const NerSlot sl = slots[b];
+    if (sl.kind == 0) continue;  // stale values: transformed, never stored
+    const float2 *src = d.Fz + ((size_t)(sl.jx + hx) * nY1 + sl.iy) * Nz;
+    copy_unrolled<4, float2>(
+        Nz, tid, nthr, [&](int z) { return src[z]; }, [&](int z, float2 v) { Fs[prow(z) * CB + b] = v; });
+  }
   for (int idx = tid; idx < padded_rows<kNerPad>(Mt) * CB; idx += nthr) H[idx] = make_float2(0.f, 0.f);
   __syncthreads();
   fft_smem<-1, kNerPad>(Fs, CB, CB, d.fNz, d.tw, tid, nthr);
+  // depth samples in the order il = (i * K) mod Nz (K prime to Nz, about
+  // Nz / (samples per warp)): the lanes of a warp spread to distant grid
+  // points, so their shared-memory atomics do not collide
+  const int lgcb = ilog2_pow2(CB);
+  const int K = d.ner_lperm;
 #pragma unroll 1
   for (int idx = tid; idx < Nz * CB; idx += nthr) {
-    const int il = idx / CB, b = idx - il * CB;
+    const int il = int(((long long)(idx >> lgcb) * K) % Nz), b = idx & (CB - 1);
     const NerSlot sl = slots[b];
     if (sl.kind == 0) continue;
     const ColInfo ci = col_info(d, sl.jx, sl.iy);
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(256, 2) k_ner_adj(const InstDesc *__restrict__
     const ff tau = tau_of(d, ci.jx, ci.jy, l);
     const float wgt = weight_of(d, tau, l) * d.scale;
     const bool lnyq = ((Nz & 1) == 0) && (l == -hz);
-    const float2 v = cscale(Fs[prow(wrap(l, Nz)) * CB + b], wgt);
+    const float2 v = cscale(Fs[prow(l < 0 ? l + Nz : l) * CB + b], wgt);
     float2 *Hb = H + b;
     if (!nyq) {
       if (!lnyq) {
@@ -448,26 +448,33 @@ __global__ void __launch_bounds__(256, 2) k_ner_adj(const InstDesc *__restrict__
   }
   __syncthreads();
   fft_smem<+1, kNerPad>(H, CB, CB, d.fMt, d.tw, tid, nthr);
-  for (int idx = tid; idx < Nt * CB; idx += nthr) {
-    const int b = idx / Nt, n = idx - b * Nt;
+  for (int b = 0; b < CB; ++b) {
     const NerSlot sl = slots[b];
     if (sl.kind != 1 && sl.kind != 2) continue;
-    const int p = prow(wrap(n - nc, Mt));
-    const float sc = __ldg(d.invpht + n);
     // the A source of a y-Nyquist column is the conjugate of its G1 row
     const ColInfo ci = col_info(d, sl.jx, sl.iy);
-    float2 v = cscale(H[p * CB + b], sc);
-    if (sl.src == 0 && ci.ynyq) v.y = -v.y;
+    const bool cj = sl.src == 0 && ci.ynyq;
+    bool cj2 = false;
     if (sl.kind == 2) {
       const NerSlot s2 = slots[b + 1];
-      const ColInfo c2 = col_info(d, s2.jx, s2.iy);
-      float2 v2 = cscale(H[p * CB + b + 1], sc);
-      if (s2.src == 0 && c2.ynyq) v2.y = -v2.y;
-      v = cadd(v, v2);
+      cj2 = s2.src == 0 && col_info(d, s2.jx, s2.iy).ynyq;
     }
     const int row = sl.src == 0 ? ci.rowA : ci.rowB;
-    d.G1[((size_t)row * nY1 + sl.iy) * Nt + n] = v;
-    if (sl.zero_row0) d.G1[((size_t)0 * nY1 + sl.iy) * Nt + n] = make_float2(0.f, 0.f);
+    float2 *dst = d.G1 + ((size_t)row * nY1 + sl.iy) * Nt;
+    float2 *dst0 = sl.zero_row0 ? d.G1 + ((size_t)0 * nY1 + sl.iy) * Nt : nullptr;
+    for (int n = tid; n < Nt; n += nthr) {
+      const int p = prow(n < nc ? n - nc + Mt : n - nc);
+      const float sc = __ldg(d.invpht + n);
+      float2 v = cscale(H[p * CB + b], sc);
+      if (cj) v.y = -v.y;
+      if (sl.kind == 2) {
+        float2 v2 = cscale(H[p * CB + b + 1], sc);
+        if (cj2) v2.y = -v2.y;
+        v = cadd(v, v2);
+      }
+      dst[n] = v;
+      if (dst0) dst0[n] = make_float2(0.f, 0.f);
+    }
   }
 }
 

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <limits>
 #include <string>
+#include <numeric>
 #include <vector>
 
 #include "pa_internal.h"
@@ -628,6 +629,12 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
   // their buffers stay within 48 KB
   h.ner_cb = 4;
   if (pa::smem_ner(h) > 48 * 1024) h.ner_cb = 2;
+  {
+    // a stride near Nz / (samples per warp) that is prime to Nz
+    int K = std::max(1, int(Nz) / (32 / h.ner_cb) + 1);
+    while (std::gcd(K, int(Nz)) != 1) ++K;
+    h.ner_lperm = K % int(Nz) == 0 ? 1 : K;
+  }
 
   // deconvolution tables and time-frequency constants
   const Kb kb(width, sigma);
