@@ -310,6 +310,29 @@ def run_ours(args):
     pipeline = {"min_bytes_per_step": pipe, "achieved_gbs": pipe / (ms_per_step / 1e3) / 1e9,
                 "frac": pipe / (ms_per_step / 1e3) / 1e9 / hbm}
 
+    # forward alone, adjoint alone and the cubic-in-omega baseline forward
+    # (same plan, same L2 flush, CUDA events around each call)
+    def timed_calls(fn, k):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for _ in range(2):
+            fn()
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        return statistics.median(a.elapsed_time(b) for a, b in evs)
+    k_parts = max(3, min(args.steps, 10))
+    fwd_ms = timed_calls(lambda: plan.reconstruct(g, out=f), k_parts)
+    adj_ms = timed_calls(lambda: plan.adjoint(f, out=g2), k_parts)
+    cub_ms = timed_calls(lambda: plan.reconstruct_cubic(g, out=f), k_parts)
+    plan.reconstruct(g, out=f)
+    parts = {"forward": {"ms": fwd_ms, "voxels_per_s": voxels / (fwd_ms / 1e3)},
+             "adjoint": {"ms": adj_ms, "voxels_per_s": voxels / (adj_ms / 1e3)},
+             "cubic_baseline_forward": {"ms": cub_ms, "voxels_per_s": voxels / (cub_ms / 1e3)},
+             "median_of": k_parts}
+
     # end to end through the public API with host buffers
     g_h = torch.tensor(P.g, dtype=torch.float32).pin_memory()
     f_h = torch.empty(P.grid.shape, dtype=torch.float32).pin_memory()
@@ -351,7 +374,8 @@ def run_ours(args):
            "config": {"workload": WORKLOAD, "step": "forward + adjoint (A g, then A^T of the result)",
                       "l2": "flushed between timed steps (256 MiB write outside the timed events)",
                       "parallelism": f"replicas x{world}", "wall_s": t_wall},
-           "roofline": roofline, "pipeline_roofline": pipeline, "stages": stages, "cpu_baseline": cpu,
+           "roofline": roofline, "pipeline_roofline": pipeline, "stages": stages, "parts": parts,
+           "cpu_baseline": cpu,
            "e2e": e2e, "gpu_launches": sum(v[1] for v in prof.values()), "clocks": clocks}
     if rank == 0:
         print(json.dumps(out))

@@ -427,8 +427,18 @@ __device__ __forceinline__ void block_work(const int2 *__restrict__ work, int &i
 }
 
 __device__ __forceinline__ int wrap(int i, int n) {
-  i %= n;
-  return i < 0 ? i + n : i;
+  // one conditional add or subtract in the usual case -n <= i < 2n
+  if (i >= n) {
+    i -= n;
+    if (i >= n) i %= n;
+  } else if (i < 0) {
+    i += n;
+    if (i < 0) {
+      i %= n;
+      if (i < 0) i += n;
+    }
+  }
+  return i;
 }
 
 }  // namespace pa
