@@ -3,6 +3,8 @@
 // batched mixed-radix Stockham FFT that runs in shared memory.
 #pragma once
 
+#include <cstdint>
+
 #include "pa_internal.h"
 
 namespace pa {
@@ -349,6 +351,21 @@ __device__ __forceinline__ void fft_stage_p2(float2 *buf, int estride, int lgnb,
   }
 }
 
+// Transform of compile-time length 2^LGL (radix-16 stages, then one radix-8,
+// -4 or -2 stage): every index split folds to constants, so the transform can
+// sit inside a loop without its address arithmetic being kept live across
+// iterations.  Sequences and threads as in fft_stage_p2.
+template <int LGL, int DIR, int PADSH = 0>
+__device__ __forceinline__ void fft_fixed(float2 *buf, int estride, int lgnb, int lgT, const float2 *__restrict__ tw,
+                                          int tid, int bar_id = 0) {
+  constexpr int n16 = LGL / 4, rem = LGL % 4;
+#pragma unroll
+  for (int st = 0; st < n16; ++st) fft_stage_p2<16, DIR, PADSH>(buf, estride, lgnb, LGL, 4 * st, tw, tid, lgT, bar_id);
+  if (rem == 3) fft_stage_p2<8, DIR, PADSH>(buf, estride, lgnb, LGL, 4 * n16, tw, tid, lgT, bar_id);
+  if (rem == 2) fft_stage_p2<4, DIR, PADSH>(buf, estride, lgnb, LGL, 4 * n16, tw, tid, lgT, bar_id);
+  if (rem == 1) fft_stage_p2<2, DIR, PADSH>(buf, estride, lgnb, LGL, 4 * n16, tw, tid, lgT, bar_id);
+}
+
 // Whole transform y[k] = sum_i x[i] exp(DIR 2 pi i i k / L), unnormalised,
 // in place in shared memory (element i of sequence b at
 // buf[pad_row<PADSH>(i) * estride + b]).  All threads of the block must call it.
@@ -415,6 +432,95 @@ __device__ __forceinline__ void copy_unrolled(int n, int tid, int nthr, LoadF ld
 }
 
 // Instance and tile of this block.
+// ------------------------------------------------ asynchronous tile copies
+// Bulk copies global -> shared through the TMA engine (cp.async.bulk), each
+// completing on an mbarrier of the block with a byte count (complete_tx).
+// Every wait is bounded: after kMbarPolls unsuccessful polls it gives up and
+// reports failure, which the kernel records in the plan's status word.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+// dst, src 16-byte aligned; bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+// Orders this thread's (and, after a block barrier, the block's) earlier
+// shared-memory accesses before later bulk copies into the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+constexpr int kMbarPolls = 1 << 20;  // each poll suspends for a hardware-defined interval
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (int i = 0; i < kMbarPolls; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// Status-word bit recorded by a kernel whose bounded wait ran out.
+constexpr int kStatusWaitTimeout = 1;
+
+// Persistent loop over the work items w = blockIdx.x, blockIdx.x + gridDim.x,
+// ... with two tile buffers: while item i is computed in one buffer, the bulk
+// copies of item i+1 fill the other.  issue(w, buf, bar) starts the copies of
+// item w (all threads call it; one thread posts the expected byte count);
+// compute(w, buf) runs on a landed tile and must leave `buf` free for reuse
+// after the block barrier that follows it.  Returns false if a wait ran out
+// (the status word then holds kStatusWaitTimeout).
+template <typename Issue, typename Compute>
+__device__ __forceinline__ bool tile_pipeline(int nwork, float2 *buf0, float2 *buf1, uint64_t *bars, int *status,
+                                              Issue issue, Compute compute) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  uint32_t parity = 0;  // bit s: parity of the next phase of barrier s
+  int w = blockIdx.x;
+  if (w < nwork) issue(w, buf0, &bars[0]);
+  for (int i = 0; w < nwork; ++i, w += gridDim.x) {
+    const int s = i & 1;
+    float2 *cur = s ? buf1 : buf0;
+    float2 *nxt = s ? buf0 : buf1;
+    const int wn = w + gridDim.x;
+    if (wn < nwork) {
+      fence_proxy_async_smem();  // the other buffer's last reads precede its refill
+      issue(wn, nxt, &bars[s ^ 1]);
+    }
+    const uint32_t par = (parity >> s) & 1u;
+    const bool ok = mbar_wait(&bars[s], par);
+    parity ^= 1u << s;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(status, kStatusWaitTimeout);
+      // give the copies still in flight one more bounded wait before leaving
+      mbar_wait(&bars[s], par);
+      if (wn < nwork) mbar_wait(&bars[s ^ 1], (parity >> (s ^ 1)) & 1u);
+      return false;
+    }
+    compute(w, cur);
+    __syncthreads();
+  }
+  return true;
+}
+
 __device__ __forceinline__ void block_work(const int2 *__restrict__ work, int &inst, int &tile) {
   if (work) {
     int2 w = work[blockIdx.x];

@@ -116,6 +116,7 @@ struct Launch {
   size_t smem;
   cudaStream_t stream;
   int threads;            // block size, for kernels that take it from the host
+  const InstDesc *host;   // host copy of the descriptor of a single-plan launch (else null)
 };
 
 // Block counts and shared-memory sizes per stage for one instance.

@@ -270,6 +270,103 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft(const InstDesc *__restri
   }
 }
 
+// Persistent, double-buffered column FFT for Mx = 2^LGL and even Nt (one
+// plan): the rows of the next tile arrive by bulk copies (TMA engine) while
+// the current tile is transformed.  Same arithmetic as k_colfft.
+template <bool ADJ, int LGL>
+__global__ void __launch_bounds__(kThreadsCol) k_colfft_pipe(const InstDesc *__restrict__ descs, int nwork) {
+  extern __shared__ float4 smem_f4[];
+  __shared__ __align__(8) uint64_t bars[2];
+  constexpr int L = 1 << LGL, NC = kColNC, LGNC = 4;
+  static_assert(NC == 1 << LGNC, "tile width");
+  float2 *buf0 = reinterpret_cast<float2 *>(smem_f4);
+  float2 *buf1 = buf0 + L * NC;
+  const InstDesc &d = descs[0];
+  const int Nt = d.Nt, nY1 = d.nY1, nX1 = d.nX1, hx = d.hx;
+  const int nchunks = (Nt + NC - 1) / NC;
+  const int tid = threadIdx.x, nthr = blockDim.x, lgT = ilog2_pow2(nthr);
+  const float2 *tw = d.tw + d.fMx.tw;
+  auto issue = [&](int w, float2 *buf, uint64_t *bar) {
+    const int jy = w / nchunks, n0 = (w - jy * nchunks) * NC;
+    const uint32_t rb = uint32_t(min(NC, Nt - n0)) * sizeof(float2);
+    if (!ADJ) {
+      if (tid == 0) mbar_arrive_expect_tx(bar, rb * L);
+      for (int p = tid; p < L; p += nthr) bulk_g2s(buf + p * NC, d.T + ((size_t)p * nY1 + jy) * Nt + n0, rb, bar);
+    } else {
+      if (tid == 0) mbar_arrive_expect_tx(bar, rb * nX1);
+      for (int ix = tid; ix < nX1; ix += nthr)
+        bulk_g2s(buf + ((ix - hx) & (L - 1)) * NC, d.G1 + ((size_t)ix * nY1 + jy) * Nt + n0, rb, bar);
+    }
+  };
+  auto compute = [&](int w, float2 *buf) {
+    const int jy = w / nchunks, n0 = (w - jy * nchunks) * NC;
+    if (!ADJ) {
+      fft_fixed<LGL, -1>(buf, NC, LGNC, lgT, tw, tid);
+      for (int idx = tid; idx < nX1 * NC; idx += nthr) {
+        const int kk = idx & (NC - 1), ix = idx >> LGNC;
+        const int n = n0 + kk;
+        if (n < Nt)
+          d.G1[((size_t)ix * nY1 + jy) * Nt + n] = cscale(buf[((ix - hx) & (L - 1)) * NC + kk], __ldg(d.invphx + ix));
+      }
+    } else {
+      // bins jx mod Mx hold G1 row jx + hx; scale them, clear the others
+      for (int idx = tid; idx < L * NC; idx += nthr) {
+        const int r = idx >> LGNC;
+        const int ix = (r + hx) & (L - 1);
+        buf[idx] = ix < nX1 ? cscale(buf[idx], __ldg(d.invphx + ix)) : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      fft_fixed<LGL, +1>(buf, NC, LGNC, lgT, tw, tid);
+      for (int idx = tid; idx < L * NC; idx += nthr) {
+        const int kk = idx & (NC - 1), p = idx >> LGNC;
+        const int n = n0 + kk;
+        if (n < Nt) d.T[((size_t)p * nY1 + jy) * Nt + n] = buf[idx];
+      }
+    }
+  };
+  tile_pipeline(nwork, buf0, buf1, bars, d.status, issue, compute);
+}
+
+// Persistent, double-buffered row FFT (k_rowfft) for My = 2^LGL and
+// Nt % 4 == 0 (one plan).
+template <int LGL>
+__global__ void __launch_bounds__(kThreadsCol) k_rowfft_pipe(const InstDesc *__restrict__ descs, int nwork) {
+  extern __shared__ float4 smem_f4[];
+  __shared__ __align__(8) uint64_t bars[2];
+  constexpr int L = 1 << LGL, NCP = 16, LGNCP = 4;
+  float2 *buf0 = reinterpret_cast<float2 *>(smem_f4);  // [My][NCP] sample pairs
+  float2 *buf1 = buf0 + L * NCP;
+  const InstDesc &d = descs[0];
+  const int Nt = d.Nt, nY1 = d.nY1;
+  const int nchunks = (Nt + 2 * NCP - 1) / (2 * NCP);
+  const int tid = threadIdx.x, nthr = blockDim.x, lgT = ilog2_pow2(nthr);
+  const float2 *tw = d.tw + d.fMy.tw;
+  auto issue = [&](int w, float2 *buf, uint64_t *bar) {
+    const int p = w / nchunks, n0 = (w - p * nchunks) * 2 * NCP;
+    const uint32_t rb = uint32_t(min(2 * NCP, Nt - n0)) * sizeof(float);
+    if (tid == 0) mbar_arrive_expect_tx(bar, rb * L);
+    const float *G0 = d.G0 + (size_t)p * L * Nt + n0;
+    for (int q = tid; q < L; q += nthr) bulk_g2s(buf + q * NCP, G0 + (size_t)q * Nt, rb, bar);
+  };
+  auto compute = [&](int w, float2 *buf) {
+    const int p = w / nchunks, n0 = (w - p * nchunks) * 2 * NCP;
+    fft_fixed<LGL, -1>(buf, NCP, LGNCP, lgT, tw, tid);
+    float2 *Trow = d.T + (size_t)p * nY1 * Nt;
+    for (int idx = tid; idx < nY1 * NCP; idx += nthr) {
+      const int k = idx & (NCP - 1), jy = idx >> LGNCP;
+      const int n = n0 + 2 * k;
+      if (n >= Nt) continue;
+      const float2 Z = buf[jy * NCP + k];
+      const float2 Zm = buf[((L - jy) & (L - 1)) * NCP + k];
+      const float sc = 0.5f * __ldg(d.invphy + jy);
+      const float2 a = make_float2(sc * (Z.x + Zm.x), sc * (Z.y - Zm.y));
+      const float2 b = make_float2(sc * (Z.y + Zm.y), -sc * (Z.x - Zm.x));
+      *reinterpret_cast<float4 *>(Trow + (size_t)jy * Nt + n) = make_float4(a.x, a.y, b.x, b.y);
+    }
+  };
+  tile_pipeline(nwork, buf0, buf1, bars, d.status, issue, compute);
+}
+
 // ------------------------------------------------------- adjoint row FFT
 // Transpose of (spread-strip row FFT, unpack, deconvolution in y): for one
 // grid row p and the sample pairs [n0, n0 + 2 NCP):
@@ -515,7 +612,51 @@ cudaError_t launch_spread(const Launch &L, int spl) {
   return cudaGetLastError();
 }
 
+// Blocks of a persistent launch: as many as fit on the device at once, at
+// most one per work item.
+template <typename K>
+static int persistent_grid(K kernel, int threads, size_t smem, int nwork) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+  const long long g = (long long)(per < 1 ? 1 : per) * (nsm < 1 ? 1 : nsm);
+  return int(g < nwork ? g : nwork);
+}
+
+template <typename K>
+static cudaError_t launch_persistent(K kernel, const Launch &L, size_t smem, int nwork) {
+  cudaError_t e = set_smem(kernel, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = persistent_grid(kernel, kThreadsCol, smem, nwork);
+  kernel<<<grid, kThreadsCol, smem, L.stream>>>(L.descs, nwork);
+  return cudaGetLastError();
+}
+
+static int pow2_log(int n) {
+  if (n <= 0 || (n & (n - 1))) return -1;
+  int lg = 0;
+  while ((1 << lg) < n) ++lg;
+  return lg;
+}
+
+// The persistent kernels are instantiated for lengths 2^5 .. 2^9 (two tile
+// buffers of at most 128 KB).
+
 cudaError_t launch_rowfft(const Launch &L) {
+  if (L.host && !L.work && (L.host->Nt % 4) == 0) {
+    const InstDesc &h = *L.host;
+    const int lg = pow2_log(h.My);
+    const int nwork = h.Mx * ((h.Nt + 31) / 32);
+    const size_t smem = 2 * size_t(h.My) * 16 * sizeof(float2);
+    switch (lg) {
+#define PA_ROWFFT_CASE(G) \
+  case G: return launch_persistent(k_rowfft_pipe<G>, L, smem, nwork);
+      PA_ROWFFT_CASE(5) PA_ROWFFT_CASE(6) PA_ROWFFT_CASE(7) PA_ROWFFT_CASE(8) PA_ROWFFT_CASE(9)
+#undef PA_ROWFFT_CASE
+      default: break;
+    }
+  }
   auto kern = k_rowfft<kRowFftNCP>;
   cudaError_t e = set_smem(kern, L.smem);
   if (e != cudaSuccess) return e;
@@ -524,6 +665,21 @@ cudaError_t launch_rowfft(const Launch &L) {
 }
 
 cudaError_t launch_colfft(const Launch &L, bool adjoint) {
+  if (L.host && !L.work && (L.host->Nt % 2) == 0) {
+    const InstDesc &h = *L.host;
+    const int lg = pow2_log(h.Mx);
+    const int nwork = h.nY1 * ((h.Nt + kColNC - 1) / kColNC);
+    const size_t smem = 2 * size_t(h.Mx) * kColNC * sizeof(float2);
+    switch (lg) {
+#define PA_COLFFT_CASE(G)                                                                   \
+  case G:                                                                                   \
+    return adjoint ? launch_persistent(k_colfft_pipe<true, G>, L, smem, nwork)              \
+                   : launch_persistent(k_colfft_pipe<false, G>, L, smem, nwork);
+      PA_COLFFT_CASE(5) PA_COLFFT_CASE(6) PA_COLFFT_CASE(7) PA_COLFFT_CASE(8) PA_COLFFT_CASE(9)
+#undef PA_COLFFT_CASE
+      default: break;
+    }
+  }
   cudaError_t e;
   if (adjoint) {
     e = set_smem(k_colfft<true>, L.smem);

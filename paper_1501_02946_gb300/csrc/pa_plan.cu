@@ -386,6 +386,7 @@ pa::Launch make_launch(const pa_plan *P, cudaStream_t s) {
   L.work = nullptr;
   L.io_table = nullptr;
   L.stream = s;
+  L.host = &P->h;
   return L;
 }
 
