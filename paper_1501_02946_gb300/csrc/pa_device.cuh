@@ -547,4 +547,35 @@ __device__ __forceinline__ int wrap(int i, int n) {
   return i;
 }
 
+// ------------------------------------------------------------ host side
+// Blocks of a persistent launch: as many as fit on the device at once, at
+// most one per work item.
+template <typename K>
+static int persistent_grid(K kernel, int threads, size_t smem, int nwork) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+  const long long g = (long long)(per < 1 ? 1 : per) * (nsm < 1 ? 1 : nsm);
+  return int(g < nwork ? g : nwork);
+}
+
+template <typename K>
+static cudaError_t launch_persistent(K kernel, const Launch &L, int threads, size_t smem, int nwork) {
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = persistent_grid(kernel, threads, smem, nwork);
+  kernel<<<grid, threads, smem, L.stream>>>(L.descs, nwork);
+  return cudaGetLastError();
+}
+
+static inline int pow2_log(int n) {
+  if (n <= 0 || (n & (n - 1))) return -1;
+  int lg = 0;
+  while ((1 << lg) < n) ++lg;
+  return lg;
+}
+
 }  // namespace pa

@@ -149,6 +149,126 @@ __global__ void __launch_bounds__(kThreadsImg) k_imgy(const InstDesc *__restrict
   }
 }
 
+// Persistent, double-buffered k_imgx for Nx = 2^LGL and even Nz (one plan):
+// the rows of the next tile arrive by bulk copies (TMA engine) while the
+// current tile is transformed.
+template <bool ADJ, int LGL>
+__global__ void __launch_bounds__(kThreadsImg) k_imgx_pipe(const InstDesc *__restrict__ descs, int nwork) {
+  extern __shared__ float4 smem_f4[];
+  __shared__ __align__(8) uint64_t bars[2];
+  constexpr int L = 1 << LGL, ZC = kImgZC, LGZC = 4;
+  static_assert(ZC == 1 << LGZC, "tile width");
+  float2 *buf0 = reinterpret_cast<float2 *>(smem_f4);
+  float2 *buf1 = buf0 + L * ZC;
+  const InstDesc &d = descs[0];
+  const int Nz = d.Nz, nY1 = d.nY1, hx = d.hx;
+  const int nzc = (Nz + ZC - 1) / ZC;
+  const int tid = threadIdx.x, nthr = blockDim.x, lgT = ilog2_pow2(nthr);
+  const float2 *tw = d.tw + d.fNx.tw;
+  const float2 *src = ADJ ? d.U : d.Fz;
+  float2 *dst = ADJ ? d.Fz : d.U;
+  auto issue = [&](int w, float2 *buf, uint64_t *bar) {
+    const int iy = w / nzc, z0 = (w - iy * nzc) * ZC;
+    const uint32_t rb = uint32_t(min(ZC, Nz - z0)) * sizeof(float2);
+    if (tid == 0) mbar_arrive_expect_tx(bar, rb * L);
+    for (int a = tid; a < L; a += nthr)
+      bulk_g2s(buf + ((a - hx) & (L - 1)) * ZC, src + ((size_t)a * nY1 + iy) * Nz + z0, rb, bar);
+  };
+  auto compute = [&](int w, float2 *buf) {
+    const int iy = w / nzc, z0 = (w - iy * nzc) * ZC;
+    fft_fixed<LGL, ADJ ? -1 : +1>(buf, ZC, LGZC, lgT, tw, tid);
+    for (int idx = tid; idx < L * ZC; idx += nthr) {
+      const int zz = idx & (ZC - 1), a = idx >> LGZC;
+      const int z = z0 + zz;
+      if (z < Nz) dst[((size_t)a * nY1 + iy) * Nz + z] = buf[((a - hx) & (L - 1)) * ZC + zz];
+    }
+  };
+  tile_pipeline(nwork, buf0, buf1, bars, d.status, issue, compute);
+}
+
+// Persistent, double-buffered k_imgy for Ny = 2^LGL and Nz % 4 == 0 (one
+// plan).  Forward: the half-spectrum rows U[x][jy] land in a staging buffer;
+// adjoint: the image rows f[x][y] land directly as depth pairs.
+template <bool ADJ, int LGL>
+__global__ void __launch_bounds__(kThreadsImg) k_imgy_pipe(const InstDesc *__restrict__ descs, int nwork, IoPtrs io) {
+  extern __shared__ float4 smem_f4[];
+  __shared__ __align__(8) uint64_t bars[2];
+  constexpr int L = 1 << LGL, ZP = kImgZP, LGZP = 4;
+  static_assert(ZP == 1 << LGZP, "tile width");
+  const InstDesc &d = descs[0];
+  const int Nz = d.Nz, nY1 = d.nY1, hy = d.hy;
+  const bool ny_even = (L & 1) == 0;
+  const int nzc = (Nz + 2 * ZP - 1) / (2 * ZP);
+  const int tid = threadIdx.x, nthr = blockDim.x, lgT = ilog2_pow2(nthr);
+  const float2 *tw = d.tw + d.fNy.tw;
+  float2 *B = reinterpret_cast<float2 *>(smem_f4);  // [Ny][ZP] depth pairs
+  // forward: two staging buffers [nY1][2 ZP]; adjoint: two tile buffers [Ny][ZP]
+  float2 *b0 = ADJ ? B : B + L * ZP;
+  float2 *b1 = ADJ ? B + L * ZP : b0 + nY1 * 2 * ZP;
+  auto issue = [&](int w, float2 *buf, uint64_t *bar) {
+    const int x = w / nzc, z0 = (w - x * nzc) * 2 * ZP;
+    const int nz = min(2 * ZP, Nz - z0);
+    if (!ADJ) {
+      const uint32_t rb = uint32_t(nz) * sizeof(float2);
+      if (tid == 0) mbar_arrive_expect_tx(bar, rb * nY1);
+      const float2 *Ur = d.U + (size_t)x * nY1 * Nz + z0;
+      for (int jy = tid; jy < nY1; jy += nthr) bulk_g2s(buf + jy * 2 * ZP, Ur + (size_t)jy * Nz, rb, bar);
+    } else {
+      const uint32_t rb = uint32_t(nz) * sizeof(float);
+      if (tid == 0) mbar_arrive_expect_tx(bar, rb * L);
+      const float *fr = io.f_in + (size_t)x * L * Nz + z0;
+      for (int y = tid; y < L; y += nthr) bulk_g2s(buf + ((y - hy) & (L - 1)) * ZP, fr + (size_t)y * Nz, rb, bar);
+    }
+  };
+  auto compute = [&](int w, float2 *buf) {
+    const int x = w / nzc, z0 = (w - x * nzc) * 2 * ZP;
+    const int nz = min(2 * ZP, Nz - z0);
+    if (!ADJ) {
+      // interior bins jy and Ny - jy from (U[z], U[z+1]); jy = 0 and the
+      // even-length Nyquist bin through their real parts
+      for (int idx = tid; idx < L * ZP; idx += nthr) {
+        const int q = idx >> LGZP, zp = idx & (ZP - 1);
+        const int jy = q <= L / 2 ? q : L - q;
+        const bool in = 2 * zp < nz;
+        const float2 Ya = in ? buf[jy * 2 * ZP + 2 * zp] : make_float2(0.f, 0.f);
+        const float2 Yb = in ? buf[jy * 2 * ZP + 2 * zp + 1] : make_float2(0.f, 0.f);
+        float2 v;
+        if (jy == 0 || (ny_even && jy == hy)) {
+          v = make_float2(Ya.x, Yb.x);
+        } else if (q == jy) {
+          v = make_float2(Ya.x - Yb.y, Ya.y + Yb.x);
+        } else {
+          v = make_float2(Ya.x + Yb.y, Yb.x - Ya.y);
+        }
+        B[idx] = v;
+      }
+      __syncthreads();
+      fft_fixed<LGL, +1>(B, ZP, LGZP, lgT, tw, tid);
+      float *fo = io.f_out + (size_t)x * L * Nz + z0;
+      const int nv4 = nz >> 2;
+      for (int idx = tid; idx < L * nv4; idx += nthr) {
+        const int y = idx / nv4, k2 = idx - y * nv4;
+        *reinterpret_cast<float4 *>(fo + (size_t)y * Nz + 4 * k2) =
+            reinterpret_cast<const float4 *>(B + ((y - hy) & (L - 1)) * ZP)[k2];
+      }
+    } else {
+      fft_fixed<LGL, -1>(buf, ZP, LGZP, lgT, tw, tid);
+      float2 *Ur = d.U + (size_t)x * nY1 * Nz + z0;
+      for (int idx = tid; idx < nY1 * ZP; idx += nthr) {
+        const int jy = idx >> LGZP, zp = idx & (ZP - 1);
+        if (2 * zp >= nz) continue;
+        const float2 Z = buf[jy * ZP + zp];
+        const float2 Zm = buf[(jy == 0 ? 0 : L - jy) * ZP + zp];
+        const float cj = (jy == 0 || (ny_even && jy == hy)) ? 0.5f : 1.f;
+        const float2 va = make_float2(cj * (Z.x + Zm.x), cj * (Z.y - Zm.y));
+        const float2 vb = make_float2(cj * (Z.y + Zm.y), -cj * (Z.x - Zm.x));
+        *reinterpret_cast<float4 *>(Ur + (size_t)jy * Nz + 2 * zp) = make_float4(va.x, va.y, vb.x, vb.y);
+      }
+    }
+  };
+  tile_pipeline(nwork, b0, b1, bars, d.status, issue, compute);
+}
+
 }  // namespace
 
 int blocks_imgx(const InstDesc &d) { return d.nY1 * ((d.Nz + kImgZC - 1) / kImgZC); }
@@ -163,6 +283,20 @@ static cudaError_t set_smem_img(K kernel, size_t smem) {
 }
 
 cudaError_t launch_imgx(const Launch &L, bool adjoint) {
+  if (L.host && !L.work && (L.host->Nz % 2) == 0) {
+    const InstDesc &h = *L.host;
+    const int nwork = h.nY1 * ((h.Nz + kImgZC - 1) / kImgZC);
+    const size_t smem = 2 * size_t(h.Nx) * kImgZC * sizeof(float2);
+    switch (pow2_log(h.Nx)) {
+#define PA_IMGX_CASE(G)                                                                        \
+  case G:                                                                                      \
+    return adjoint ? launch_persistent(k_imgx_pipe<true, G>, L, kThreadsImg, smem, nwork)      \
+                   : launch_persistent(k_imgx_pipe<false, G>, L, kThreadsImg, smem, nwork);
+      PA_IMGX_CASE(5) PA_IMGX_CASE(6) PA_IMGX_CASE(7) PA_IMGX_CASE(8) PA_IMGX_CASE(9)
+#undef PA_IMGX_CASE
+      default: break;
+    }
+  }
   cudaError_t e;
   if (adjoint) {
     e = set_smem_img(k_imgx<true>, L.smem);
@@ -176,7 +310,33 @@ cudaError_t launch_imgx(const Launch &L, bool adjoint) {
   return cudaGetLastError();
 }
 
+template <typename K>
+static cudaError_t launch_persistent_io(K kernel, const Launch &L, size_t smem, int nwork) {
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = persistent_grid(kernel, kThreadsImg, smem, nwork);
+  kernel<<<grid, kThreadsImg, smem, L.stream>>>(L.descs, nwork, L.io);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_imgy(const Launch &L, bool adjoint) {
+  if (L.host && !L.work && (L.host->Nz % 4) == 0) {
+    const InstDesc &h = *L.host;
+    const int nwork = h.Nx * ((h.Nz + 2 * kImgZP - 1) / (2 * kImgZP));
+    const size_t smem = adjoint ? 2 * size_t(h.Ny) * kImgZP * sizeof(float2)
+                                : (size_t(h.Ny) * kImgZP + 2 * size_t(h.nY1) * 2 * kImgZP) * sizeof(float2);
+    switch (pow2_log(h.Ny)) {
+#define PA_IMGY_CASE(G)                                                                  \
+  case G:                                                                                \
+    return adjoint ? launch_persistent_io(k_imgy_pipe<true, G>, L, smem, nwork)         \
+                   : launch_persistent_io(k_imgy_pipe<false, G>, L, smem, nwork);
+      PA_IMGY_CASE(5) PA_IMGY_CASE(6) PA_IMGY_CASE(7) PA_IMGY_CASE(8) PA_IMGY_CASE(9)
+#undef PA_IMGY_CASE
+      default: break;
+    }
+  }
   cudaError_t e;
   if (adjoint) {
     e = set_smem_img(k_imgy<true>, L.smem);

@@ -426,6 +426,63 @@ __global__ void __launch_bounds__(kThreadsCol) k_rowifft(const InstDesc *__restr
   }
 }
 
+// Persistent, double-buffered k_rowifft for My = 2^LGL and Nt % 4 == 0 (one
+// plan): the T rows of the next tile land in a staging buffer by bulk copies
+// while the current spectrum is built, transformed and written.
+template <int LGL>
+__global__ void __launch_bounds__(kThreadsCol) k_rowifft_pipe(const InstDesc *__restrict__ descs, int nwork) {
+  extern __shared__ float4 smem_f4[];
+  __shared__ __align__(8) uint64_t bars[2];
+  constexpr int L = 1 << LGL, NCP = 16, LGNCP = 4;
+  const InstDesc &d = descs[0];
+  const int Nt = d.Nt, nY1 = d.nY1;
+  float2 *S = reinterpret_cast<float2 *>(smem_f4);  // [My][NCP] packed spectrum
+  float2 *st0 = S + L * NCP;                        // [nY1][2 NCP] staged T rows
+  float2 *st1 = st0 + nY1 * 2 * NCP;
+  const int nchunks = (Nt + 2 * NCP - 1) / (2 * NCP);
+  const int tid = threadIdx.x, nthr = blockDim.x, lgT = ilog2_pow2(nthr);
+  const float2 *tw = d.tw + d.fMy.tw;
+  auto issue = [&](int w, float2 *stg, uint64_t *bar) {
+    const int p = w / nchunks, n0 = (w - p * nchunks) * 2 * NCP;
+    const uint32_t rb = uint32_t(min(2 * NCP, Nt - n0)) * sizeof(float2);
+    if (tid == 0) mbar_arrive_expect_tx(bar, rb * nY1);
+    const float2 *Trow = d.T + (size_t)p * nY1 * Nt + n0;
+    for (int jy = tid; jy < nY1; jy += nthr) bulk_g2s(stg + jy * 2 * NCP, Trow + (size_t)jy * Nt, rb, bar);
+  };
+  auto compute = [&](int w, float2 *stg) {
+    const int p = w / nchunks, n0 = (w - p * nchunks) * 2 * NCP;
+    // bins jy and My - jy from the staged rows; the rest of S is zero
+    for (int idx = tid; idx < L * NCP; idx += nthr) {
+      const int q = idx >> LGNCP, kk = idx & (NCP - 1);
+      const int jy = q <= L / 2 ? q : L - q;
+      float2 v = make_float2(0.f, 0.f);
+      if (jy < nY1) {
+        const int n = n0 + 2 * kk;
+        const float sc = __ldg(d.invphy + jy);
+        const float2 a = n < Nt ? cscale(stg[jy * 2 * NCP + 2 * kk], sc) : make_float2(0.f, 0.f);
+        const float2 b = n + 1 < Nt ? cscale(stg[jy * 2 * NCP + 2 * kk + 1], sc) : make_float2(0.f, 0.f);
+        if (q == 0) {
+          v = make_float2(a.x, b.x);
+        } else if (q == jy) {
+          v = make_float2(0.5f * (a.x - b.y), 0.5f * (a.y + b.x));
+        } else {
+          v = make_float2(0.5f * (a.x + b.y), 0.5f * (b.x - a.y));
+        }
+      }
+      S[idx] = v;
+    }
+    __syncthreads();
+    fft_fixed<LGL, +1>(S, NCP, LGNCP, lgT, tw, tid);
+    float *G0 = d.G0 + (size_t)p * L * Nt + n0;
+    const int nv4 = (min(2 * NCP, Nt - n0)) >> 2;
+    for (int idx = tid; idx < L * nv4; idx += nthr) {
+      const int q = idx / nv4, k2 = idx - q * nv4;
+      *reinterpret_cast<float4 *>(G0 + (size_t)q * Nt + 4 * k2) = reinterpret_cast<const float4 *>(S + q * NCP)[k2];
+    }
+  };
+  tile_pipeline(nwork, st0, st1, bars, d.status, issue, compute);
+}
+
 // ---------------------------------------------------- adjoint interpolation
 // g'[m][n] = sum_{r,t} wx[r] wy[t] G0b[bx - w/2 + 1 + r][by - w/2 + 1 + t][n]
 // (wy carries a_m), the transpose of the spread.  One tile: the sensors whose
@@ -612,34 +669,6 @@ cudaError_t launch_spread(const Launch &L, int spl) {
   return cudaGetLastError();
 }
 
-// Blocks of a persistent launch: as many as fit on the device at once, at
-// most one per work item.
-template <typename K>
-static int persistent_grid(K kernel, int threads, size_t smem, int nwork) {
-  int dev = 0, nsm = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
-  const long long g = (long long)(per < 1 ? 1 : per) * (nsm < 1 ? 1 : nsm);
-  return int(g < nwork ? g : nwork);
-}
-
-template <typename K>
-static cudaError_t launch_persistent(K kernel, const Launch &L, size_t smem, int nwork) {
-  cudaError_t e = set_smem(kernel, smem);
-  if (e != cudaSuccess) return e;
-  const int grid = persistent_grid(kernel, kThreadsCol, smem, nwork);
-  kernel<<<grid, kThreadsCol, smem, L.stream>>>(L.descs, nwork);
-  return cudaGetLastError();
-}
-
-static int pow2_log(int n) {
-  if (n <= 0 || (n & (n - 1))) return -1;
-  int lg = 0;
-  while ((1 << lg) < n) ++lg;
-  return lg;
-}
-
 // The persistent kernels are instantiated for lengths 2^5 .. 2^9 (two tile
 // buffers of at most 128 KB).
 
@@ -651,7 +680,7 @@ cudaError_t launch_rowfft(const Launch &L) {
     const size_t smem = 2 * size_t(h.My) * 16 * sizeof(float2);
     switch (lg) {
 #define PA_ROWFFT_CASE(G) \
-  case G: return launch_persistent(k_rowfft_pipe<G>, L, smem, nwork);
+  case G: return launch_persistent(k_rowfft_pipe<G>, L, kThreadsCol, smem, nwork);
       PA_ROWFFT_CASE(5) PA_ROWFFT_CASE(6) PA_ROWFFT_CASE(7) PA_ROWFFT_CASE(8) PA_ROWFFT_CASE(9)
 #undef PA_ROWFFT_CASE
       default: break;
@@ -673,8 +702,8 @@ cudaError_t launch_colfft(const Launch &L, bool adjoint) {
     switch (lg) {
 #define PA_COLFFT_CASE(G)                                                                   \
   case G:                                                                                   \
-    return adjoint ? launch_persistent(k_colfft_pipe<true, G>, L, smem, nwork)              \
-                   : launch_persistent(k_colfft_pipe<false, G>, L, smem, nwork);
+    return adjoint ? launch_persistent(k_colfft_pipe<true, G>, L, kThreadsCol, smem, nwork)  \
+                   : launch_persistent(k_colfft_pipe<false, G>, L, kThreadsCol, smem, nwork);
       PA_COLFFT_CASE(5) PA_COLFFT_CASE(6) PA_COLFFT_CASE(7) PA_COLFFT_CASE(8) PA_COLFFT_CASE(9)
 #undef PA_COLFFT_CASE
       default: break;
@@ -713,6 +742,19 @@ cudaError_t launch_interp_width(const Launch &L, int width, bool grad) {
 }
 
 cudaError_t launch_rowifft(const Launch &L) {
+  if (L.host && !L.work && (L.host->Nt % 4) == 0) {
+    const InstDesc &h = *L.host;
+    const int lg = pow2_log(h.My);
+    const int nwork = h.Mx * ((h.Nt + 31) / 32);
+    const size_t smem = (size_t(h.My) * 16 + 2 * size_t(h.nY1) * 32) * sizeof(float2);
+    switch (lg) {
+#define PA_ROWIFFT_CASE(G) \
+  case G: return launch_persistent(k_rowifft_pipe<G>, L, kThreadsCol, smem, nwork);
+      PA_ROWIFFT_CASE(5) PA_ROWIFFT_CASE(6) PA_ROWIFFT_CASE(7) PA_ROWIFFT_CASE(8) PA_ROWIFFT_CASE(9)
+#undef PA_ROWIFFT_CASE
+      default: break;
+    }
+  }
   auto kern = k_rowifft<kRowIfftNCP>;
   cudaError_t e = set_smem(kern, L.smem);
   if (e != cudaSuccess) return e;
