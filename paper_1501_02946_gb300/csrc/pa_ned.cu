@@ -530,9 +530,30 @@ __global__ void __launch_bounds__(kThreadsInterp) k_interp(const InstDesc *__res
     }
     row_pref[TX] = acc;
   }
-  // G0b tile with halo, 128-byte rows of 32 samples
+  // G0b tile with halo, 128-byte rows of 32 samples: one bulk copy (TMA
+  // engine) per cell when rows are 16-byte aligned, else plain loads
   const float *G0 = d.G0;
   const bool vec4 = (Nt & 3) == 0;
+  __shared__ __align__(8) uint64_t bar;
+  if (vec4) {
+    if (tid == 0) {
+      mbar_init(&bar, 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    const uint32_t rb = uint32_t(min(NC, Nt - n0)) * sizeof(float);
+    if (tid == 0) mbar_arrive_expect_tx(&bar, rb * HX * HY);
+    for (int cell = tid; cell < HX * HY; cell += nthr) {
+      const int hr = cell / HY, hc = cell - hr * HY;
+      const int p = wrap(p0 - W / 2 + 1 + hr, Mx), q = wrap(q0 - W / 2 + 1 + hc, My);
+      bulk_g2s(Gs + cell * NC, G0 + ((size_t)p * My + q) * Nt + n0, rb, &bar);
+    }
+    if (__syncthreads_or(!mbar_wait(&bar, 0))) {
+      if (tid == 0) atomicOr(d.status, kStatusWaitTimeout);
+      mbar_wait(&bar, 0);  // one more bounded wait for the copies in flight
+      return;
+    }
+  } else {
   copy_unrolled<8, float4>(
       HX * HY * (NC / 4), tid, nthr,
       [&](int idx) {
@@ -553,6 +574,7 @@ __global__ void __launch_bounds__(kThreadsInterp) k_interp(const InstDesc *__res
         return v;
       },
       [&](int idx, float4 v) { reinterpret_cast<float4 *>(Gs)[idx] = v; });
+  }
   __syncthreads();
   const int ns = row_pref[TX];
   const int n = n0 + lane;
@@ -592,8 +614,9 @@ __global__ void __launch_bounds__(kThreadsInterp) k_interp(const InstDesc *__res
     const int m = __ldg(d.perm + i);
     if (io.g_out && n < Nt) io.g_out[(size_t)m * Nt + n] = a0;
     if (GRAD) {
+      // samples past Nt hold stale tile values: keep them out of the sums
       const float gv = n < Nt ? __ldg(io.g_in + (size_t)m * Nt + n) : 0.f;
-      float px = ax * gv, py = ay * gv;
+      float px = n < Nt ? ax * gv : 0.f, py = n < Nt ? ay * gv : 0.f;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
         px += __shfl_xor_sync(0xffffffffu, px, off);
