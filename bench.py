@@ -200,6 +200,10 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    # the oracle runs on one host thread (numpy's FFT is single-threaded;
+    # pin BLAS pools before numpy loads so that `cores` is exact)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
     import synth
     # sample per step: a central sub-aperture crop sized so that the whole
     # (steps + warmup) run stays within about three minutes
@@ -223,7 +227,7 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "sample": sample, "oracle": "FP64 NUFFT (numpy), width 16"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -385,6 +389,67 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """The uneven batch (64 instances, N uniform over the 7-smooth integers in
+    [64, 256], T in {256, 512, 1024}, output N x N x 2T): one pa_batch_run
+    (one launch per stage over all instances, replayed as a CUDA graph)
+    against 64 sequential single-plan reconstructions.  Seeded random data
+    (timing only)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1501_02946_gb300 as pa
+    import synth
+
+    dev = torch.device("cuda", 0)
+    shapes = synth.batch_shapes()
+    rng = np.random.default_rng(1505)
+    plans, gs, fs = [], [], []
+    voxels = 0
+    for k, (n_side, n_t) in enumerate(shapes):
+        xy = synth.jittered_lattice(rng, n_side, n_side, 1e-4, 1e-4)
+        grid = (n_side, n_side, 2 * n_t, 1e-4, 1e-4, 1e-4)
+        plans.append(pa.Plan(xy, n_t, 20e-9, synth.C_WATER, grid))
+        gs.append(torch.randn(n_side * n_side, n_t, device=dev, dtype=torch.float32))
+        fs.append(torch.empty(n_side, n_side, 2 * n_t, device=dev, dtype=torch.float32))
+        voxels += n_side * n_side * 2 * n_t
+    batch = pa.Batch(plans)
+    stream = torch.cuda.current_stream(dev)
+
+    def seq():
+        for p, g, f in zip(plans, gs, fs):
+            p.reconstruct(g, out=f)
+
+    def bat():
+        batch.run(gs, fs)
+
+    res = {}
+    for name, fn in (("batch_graph", bat), ("sequential_64", seq)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for a, b in evs:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = statistics.median(a.elapsed_time(b) for a, b in evs)
+        res[name] = {"ms": ms, "voxels_per_s": voxels / (ms / 1e3)}
+    out = {"metric": "voxels/s (uneven batch of 64 forward reconstructions)", "value": res["batch_graph"]["voxels_per_s"],
+           "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": res["batch_graph"]["ms"], "higher_is_better": True, "dtype": "f32", "data": "synthetic (seeded random)",
+           "config": {"workload": "64 instances, N in 7-smooth [64, 256], T in {256, 512, 1024}, output N x N x 2T",
+                      "total_voxels": voxels, "shapes": shapes},
+           "comparison": res, "speedup_vs_sequential": res["sequential_64"]["ms"] / res["batch_graph"]["ms"]}
+    print(json.dumps(out))
+    batch.close()
+    for p in plans:
+        p.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -392,11 +457,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", action="store_true", help="time the uneven 64-instance batch instead")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch:
+        return run_batch(args)
     return run_ours(args)
 
 

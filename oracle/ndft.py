@@ -40,15 +40,26 @@ def wavenumbers(grid):
     return kx, ky, kz
 
 
+def wrap_index(j, N):
+    """Integer frequency j moved into the index set freqs(N) (period N)."""
+    lo = -(N // 2)
+    return (np.asarray(j) - lo) % N + lo
+
+
+def omega_weight_at(kx, ky, kz, c):
+    """omega = c s(kz) |K| and W = 2 c |kz| / |K| (W = 2c at K = 0), elementwise."""
+    K = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+    s = np.where(kz >= 0, 1.0, -1.0)
+    omega = c * s * K
+    W = np.where(K > 0, 2.0 * c * np.abs(kz) / np.where(K > 0, K, 1.0), 2.0 * c)
+    return omega, W
+
+
 def omega_and_weight(grid, c):
     """omega(j, l) and W(j, l) on the full (jx, jy, l) grid, shape (nx, ny, nz)."""
     kx, ky, kz = wavenumbers(grid)
     KX, KY, KZ = np.meshgrid(kx, ky, kz, indexing="ij")
-    K = np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2)
-    s = np.where(KZ >= 0, 1.0, -1.0)
-    omega = c * s * K
-    W = np.where(K > 0, 2.0 * c * np.abs(KZ) / np.where(K > 0, K, 1.0), 2.0 * c)
-    return omega, W
+    return omega_weight_at(KX, KY, KZ, c)
 
 
 def spatial_factors(xy, grid, jx=None, jy=None):
@@ -184,3 +195,70 @@ def position_grad(xy, h, g, fbar, dt, c, grid):
     gx = a * np.sum(g * Dx.real, axis=1)
     gy = a * np.sum(g * Dy.real, axis=1)
     return np.stack([gx, gy], axis=1)
+
+
+# ---------------------------------------------------------------------------
+# Single columns and single voxels, for checks at sizes where the full dense
+# sums are out of reach.
+
+def column_spectrum(xy, h, g, dt, c, grid, jx, jy):
+    """F(j, l) = (dt/dz) W(j, l) sum_n G1(j, n) exp(-i omega(j, l) n dt) for one
+    column of integer frequencies j = (jx, jy) and every l in freqs(nz)."""
+    nt = g.shape[1]
+    a = h / (grid.dx * grid.dy)
+    Ex, Ey = spatial_factors(xy, grid, [jx], [jy])
+    E = Ex[0] * Ey[0]                                             # (M,)
+    ag = a[:, None] * g                                           # real (M, nt)
+    G = E.real @ ag + 1j * (E.imag @ ag)                          # G1(j, n)
+    l = freqs(grid.nz)
+    kx = 2 * np.pi * jx / (grid.nx * grid.dx)
+    ky = 2 * np.pi * jy / (grid.ny * grid.dy)
+    kz = 2 * np.pi * l / (grid.nz * grid.dz)
+    omega, W = omega_weight_at(kx, ky, kz, c)
+    t = np.arange(nt) * dt
+    Ghat = np.exp(-1j * np.outer(omega, t)) @ G
+    return (dt / grid.dz) * W * Ghat
+
+
+def column_depth_profile(xy, h, g, dt, c, grid, jx, jy):
+    """(1/(nx ny nz)) sum_l Fsym(j, l) exp(i kz z_k), k = 0..nz-1, for one column
+    j of the index sets, where Fsym(k) = (F(k) + conj F(-k mod N)) / 2 is the
+    Hermitian part of F (its inverse DFT is the real part of F's)."""
+    nx, ny, nz = grid.nx, grid.ny, grid.nz
+    F = column_spectrum(xy, h, g, dt, c, grid, jx, jy)
+    Fm = column_spectrum(xy, h, g, dt, c, grid, int(wrap_index(-jx, nx)), int(wrap_index(-jy, ny)))
+    l = freqs(nz)
+    Fsym = 0.5 * (F + np.conj(Fm[wrap_index(-l, nz) - l[0]]))
+    z = np.arange(nz) * grid.dz
+    kz = 2 * np.pi * l / (nz * grid.dz)
+    return (np.exp(1j * np.outer(z, kz)) @ Fsym) / (nx * ny * nz)
+
+
+def half_spectrum_voxels(half, grid, pts):
+    """f[p, q, k] at the voxels pts (P x 3 integers) from a Hermitian half
+    spectrum half[ix][iy][k] over jx = ix - floor(nx/2) (all nx) and jy = iy
+    (iy = 0..floor(ny/2); for even ny the last entry is the unpaired
+    jy = -ny/2): f = sum over the whole (jx, jy) plane of S(j, k)
+    exp(i (kx x_p + ky y_q)), with S(jx, -jy) = conj S(-jx, jy) off the stored
+    half."""
+    nx, ny = grid.nx, grid.ny
+    hx, hy = nx // 2, ny // 2
+    jxs, jys = freqs(nx), freqs(ny)
+    S = np.empty((nx, ny, half.shape[2]), dtype=np.complex128)
+    for a, jx in enumerate(jxs):
+        for b, jy in enumerate(jys):
+            if jy >= 0:
+                S[a, b] = half[jx + hx, jy]
+            elif ny % 2 == 0 and jy == -hy:
+                S[a, b] = half[jx + hx, hy]
+            else:
+                S[a, b] = np.conj(half[int(wrap_index(-jx, nx)) + hx, -jy])
+    kx = 2 * np.pi * jxs / (nx * grid.dx)
+    ky = 2 * np.pi * jys / (ny * grid.dy)
+    out = np.empty(len(pts))
+    for i, (p, q, k) in enumerate(pts):
+        x = (p - hx) * grid.dx
+        y = (q - hy) * grid.dy
+        E = np.exp(1j * np.add.outer(kx * x, ky * y))
+        out[i] = np.sum(E * S[:, :, k]).real
+    return out

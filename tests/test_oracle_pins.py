@@ -145,3 +145,53 @@ def test_ball_c1_geometry():
     assert fv[am] > 0
     assert np.abs(f[:, :, 32:]).max() < 0.1 * f.max()
     assert f[fv > 0].mean() > 0.2
+
+
+# --- single-column and single-voxel helpers (used for sampled checks at full size)
+@pytest.mark.parametrize("shape", [(8, 8, 16), (7, 9, 11), (6, 5, 8)])
+def test_column_depth_profile_matches_full_o1(shape):
+    """Each column's depth profile equals the corresponding slice of the full
+    O1 chain (Hermitian part of F, inverse DFT over depth), odd and even N."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(11)
+    grid = synth.Grid(nx, ny, nz, 1e-4, 1.2e-4, 0.9e-4)
+    X, Y = nx * grid.dx, ny * grid.dy
+    xy = np.stack([rng.uniform(-X / 2, X / 2, 30), rng.uniform(-Y / 2, Y / 2, 30)], axis=1)
+    h = np.full(30, X * Y / 30)
+    g = rng.normal(size=(30, 24))
+    dt, c = 40e-9, 1500.0
+    _, aux = ndft.reconstruct(xy, h, g, dt, c, grid, full=True)
+    F = aux["F"]
+    hx, hy, hz = nx // 2, ny // 2, nz // 2
+    ia = (2 * hx - np.arange(nx)) % nx
+    ib = (2 * hy - np.arange(ny)) % ny
+    ic = (2 * hz - np.arange(nz)) % nz
+    Fsym = 0.5 * (F + np.conj(F[np.ix_(ia, ib, ic)]))
+    E = np.exp(1j * np.outer(np.arange(nz) * grid.dz, 2 * np.pi * ndft.freqs(nz) / (nz * grid.dz)))
+    full = np.einsum("zl,abl->abz", E, Fsym) / (nx * ny * nz)
+    scale = np.abs(full).max()
+    for jx in ndft.freqs(nx):
+        for jy in ndft.freqs(ny):
+            col = ndft.column_depth_profile(xy, h, g, dt, c, grid, int(jx), int(jy))
+            assert np.abs(col - full[jx + hx, jy + hy]).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("shape", [(8, 6, 5), (7, 9, 4)])
+def test_half_spectrum_voxels_round_trip(shape):
+    """A real image is rebuilt from its Hermitian half spectrum (taken with
+    numpy.fft.fft2 over x and y), at every voxel, odd and even N."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(12)
+    grid = synth.Grid(nx, ny, nz, 1e-4, 1e-4, 1e-4)
+    f = rng.normal(size=shape)
+    hx, hy = nx // 2, ny // 2
+    # S(jx, jy, k) = 1/(nx ny) sum_{p,q} f exp(-i (kx x_p + ky y_q)), x_p = (p - hx) dx
+    D = np.fft.fft2(f, axes=(0, 1)) / (nx * ny)
+    jx, jy = ndft.freqs(nx), ndft.freqs(ny)
+    ph = np.exp(2j * np.pi * (np.outer(jx, np.ones(ny)) * hx / nx + np.outer(np.ones(nx), jy) * hy / ny))
+    S = D[np.ix_(jx % nx, jy % ny)] * ph[:, :, None]            # [jx + hx][jy + hy][k]
+    half = S[:, hy:, :] if ny % 2 else np.concatenate([S[:, hy:, :], S[:, :1, :]], axis=1)
+    pts = [(p, q, k) for p in range(nx) for q in range(ny) for k in range(nz)]
+    got = ndft.half_spectrum_voxels(half, grid, pts)
+    ref = np.array([f[p, q, k] for p, q, k in pts])
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
