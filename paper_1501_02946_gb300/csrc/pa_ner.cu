@@ -312,23 +312,43 @@ __global__ void __launch_bounds__(256, 2) k_ner(const InstDesc *__restrict__ des
   }
   __syncthreads();
   // slot b's source row, at n' = n - nc (mod Mt) after 1/phihat; an empty
-  // slot keeps stale values (transformed, never stored)
-  for (int b = 0; b < CB; ++b) {
-    const NerSlot sl = slots[b];
-    if (sl.kind == 0) continue;
-    const ColInfo ci = col_info(d, sl.jx, sl.iy);
-    const float2 *src = d.G1 + ((size_t)(sl.src == 0 ? ci.rowA : ci.rowB) * nY1 + sl.iy) * Nt;
-    const bool cj = sl.src == 0 && ci.ynyq;
-    copy_unrolled<4, float2>(
-        Nt, tid, nthr,
-        [&](int n) {
-          float2 a = src[n];
-          if (cj) a.y = -a.y;
-          return CUBIC ? a : cscale(a, __ldg(d.invpht + n));
-        },
-        [&](int n, float2 a) { H[prow(CUBIC ? n : (n < nc ? n - nc + Mt : n - nc)) * CB + b] = a; });
+  // slot keeps stale values (transformed, never stored).  All slots' rows
+  // are read in one loop, so their loads are in flight together.
+  {
+    const float2 *src[kNerMaxCB];
+    bool cj[kNerMaxCB];
+#pragma unroll
+    for (int b = 0; b < kNerMaxCB; ++b) {
+      src[b] = nullptr;
+      cj[b] = false;
+      if (b < CB && slots[b].kind != 0) {
+        const NerSlot sl = slots[b];
+        const ColInfo ci = col_info(d, sl.jx, sl.iy);
+        src[b] = d.G1 + ((size_t)(sl.src == 0 ? ci.rowA : ci.rowB) * nY1 + sl.iy) * Nt;
+        cj[b] = sl.src == 0 && ci.ynyq;
+      }
+    }
+#pragma unroll 2
+    for (int n = tid; n < Nt; n += nthr) {
+      float2 a[kNerMaxCB];
+#pragma unroll
+      for (int b = 0; b < kNerMaxCB; ++b)
+        if (src[b]) a[b] = src[b][n];
+      const float sc = CUBIC ? 1.f : __ldg(d.invpht + n);
+      const int r = prow(CUBIC ? n : (n < nc ? n - nc + Mt : n - nc));
+#pragma unroll
+      for (int b = 0; b < kNerMaxCB; ++b)
+        if (src[b]) {
+          float2 v = a[b];
+          if (cj[b]) v.y = -v.y;
+          H[r * CB + b] = cscale(v, sc);
+        }
+    }
     if (!CUBIC)
-      for (int u = tid; u < Mt - Nt; u += nthr) H[prow(Nt - nc + u) * CB + b] = make_float2(0.f, 0.f);
+      for (int u = tid; u < Mt - Nt; u += nthr)
+#pragma unroll
+        for (int b = 0; b < kNerMaxCB; ++b)
+          if (b < CB) H[prow(Nt - nc + u) * CB + b] = make_float2(0.f, 0.f);
   }
   __syncthreads();
   if (CUBIC) {
@@ -405,12 +425,25 @@ __global__ void __launch_bounds__(256, 2) k_ner_adj(const InstDesc *__restrict__
     slots[tid] = v < nslots ? adj_slot(d, v) : NerSlot{};
   }
   __syncthreads();
-  for (int b = 0; b < CB; ++b) {
-    const NerSlot sl = slots[b];
-    if (sl.kind == 0) continue;  // stale values: transformed, never stored
-    const float2 *src = d.Fz + ((size_t)(sl.jx + hx) * nY1 + sl.iy) * Nz;
-    copy_unrolled<4, float2>(
-        Nz, tid, nthr, [&](int z) { return src[z]; }, [&](int z, float2 v) { Fs[prow(z) * CB + b] = v; });
+  {
+    // all slots' columns in one loop (empty slots keep stale values:
+    // transformed, never stored)
+    const float2 *src[kNerMaxCB];
+#pragma unroll
+    for (int b = 0; b < kNerMaxCB; ++b) {
+      src[b] = nullptr;
+      if (b < CB && slots[b].kind != 0) src[b] = d.Fz + ((size_t)(slots[b].jx + hx) * nY1 + slots[b].iy) * Nz;
+    }
+#pragma unroll 2
+    for (int z = tid; z < Nz; z += nthr) {
+      float2 v[kNerMaxCB];
+#pragma unroll
+      for (int b = 0; b < kNerMaxCB; ++b)
+        if (src[b]) v[b] = src[b][z];
+#pragma unroll
+      for (int b = 0; b < kNerMaxCB; ++b)
+        if (src[b]) Fs[prow(z) * CB + b] = v[b];
+    }
   }
   for (int idx = tid; idx < padded_rows<kNerPad>(Mt) * CB; idx += nthr) H[idx] = make_float2(0.f, 0.f);
   __syncthreads();
