@@ -562,7 +562,7 @@ static int persistent_grid(K kernel, int threads, size_t smem, int nwork) {
 
 template <typename K>
 static cudaError_t launch_persistent(K kernel, const Launch &L, int threads, size_t smem, int nwork) {
-  if (smem > 48 * 1024) {
+  if (smem > 40 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
   }

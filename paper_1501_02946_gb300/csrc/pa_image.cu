@@ -278,7 +278,7 @@ size_t smem_imgy(const InstDesc &d) { return (size_t)d.Ny * kImgZP * sizeof(floa
 
 template <typename K>
 static cudaError_t set_smem_img(K kernel, size_t smem) {
-  if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 40 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return cudaSuccess;
 }
 
@@ -312,7 +312,7 @@ cudaError_t launch_imgx(const Launch &L, bool adjoint) {
 
 template <typename K>
 static cudaError_t launch_persistent_io(K kernel, const Launch &L, size_t smem, int nwork) {
-  if (smem > 48 * 1024) {
+  if (smem > 40 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
   }
