@@ -332,9 +332,23 @@ def run_ours(args):
     adj_ms = timed_calls(lambda: plan.adjoint(f, out=g2), k_parts)
     cub_ms = timed_calls(lambda: plan.reconstruct_cubic(g, out=f), k_parts)
     plan.reconstruct(g, out=f)
+    # library comparison (bench only): cuFFT (through torch.fft) doing the
+    # row and column transforms of the same oversampled grid, without the
+    # deconvolution, truncation and pair packing that the kernels fuse
+    Mx, My = 2 * Nx, 2 * Ny
+    g0 = torch.randn(Mx, My, P.n_t, device=dev, dtype=torch.float32)
+    def cufft_rows_cols():
+        t = torch.fft.rfft(g0, dim=1)[:, : Ny // 2 + 1, :]
+        return torch.fft.fft(t, dim=0)
+    cufft_ms = timed_calls(cufft_rows_cols, k_parts)
+    del g0
     parts = {"forward": {"ms": fwd_ms, "voxels_per_s": voxels / (fwd_ms / 1e3)},
              "adjoint": {"ms": adj_ms, "voxels_per_s": voxels / (adj_ms / 1e3)},
              "cubic_baseline_forward": {"ms": cub_ms, "voxels_per_s": voxels / (cub_ms / 1e3)},
+             "cufft_row_col_transforms_ms": cufft_ms,
+             "own_row_col_transforms_ms": (prof["ned_rowfft"][0] / prof["ned_rowfft"][1]
+                                           + prof["ned_colfft"][0] / prof["ned_colfft"][1])
+             if "ned_rowfft" in prof and "ned_colfft" in prof else None,
              "median_of": k_parts}
 
     # end to end through the public API with host buffers

@@ -153,6 +153,19 @@ int pa_position_grad_noalloc(pa_plan *plan, const float *g_dev, const float *gra
 int pa_plan_update_positions(pa_plan *plan, const double *sensor_xy, void *stream);
 
 /*
+ * The same with the new positions in device memory (float32 [M][2], metres):
+ * the reduction modulo (X, Y) and the split into base cell and fraction (in
+ * FP64), the sort of the sensors by cell, the window taps and the spread
+ * entry lists are rebuilt on the device, in the order the host builds them.
+ * Synchronises `stream` once (to size the entry lists).  Returns
+ * PA_ERR_INVALID_ARG for a non-finite position (the plan then holds the
+ * finite remainder with the bad positions at 0).  The first call allocates
+ * the plan's re-binning scratch (about 32 bytes per sensor plus 4 bytes per
+ * oversampled cell); later calls allocate only when the entry lists grow.
+ */
+int pa_plan_update_positions_device(pa_plan *plan, const float *xy_dev, void *stream);
+
+/*
  * Same-GPU baseline of Sec. 2's polynomial interpolation: identical NED and
  * inverse FFT, but the time transform is a plain n_t-point FFT per column
  * followed by 4-tap cubic Lagrange interpolation at the non-integer

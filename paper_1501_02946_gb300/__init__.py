@@ -161,6 +161,17 @@ class Plan:
         return grad_g, grad_xy
 
     def update_positions(self, xy):
+        """New sensor positions (M, 2) in metres: a host array (re-binned on
+        the host in FP64) or a CUDA tensor (float32, re-binned on the device)."""
+        torch = _torch()
+        if isinstance(xy, torch.Tensor) and xy.is_cuda:
+            t = xy.detach().to(torch.float32).contiguous().reshape(-1, 2)
+            if t.shape[0] != self.M:
+                raise ValueError("update_positions needs one position per sensor")
+            check(_lib.load().pa_plan_update_positions_device(self.handle, c_void_p(t.data_ptr()),
+                                                              _stream_ptr(self.device)))
+            self._xy = t.cpu().numpy().astype(np.float64)
+            return
         xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(-1, 2))
         if xy.shape[0] != self.M:
             raise ValueError("update_positions needs one position per sensor")

@@ -151,6 +151,33 @@ cudaError_t launch_interp_width(const Launch &L, int width, bool grad);
 cudaError_t launch_rowifft(const Launch &L);
 cudaError_t launch_grad_reduce(const Launch &L, int M);
 
+// Device re-binning of new sensor positions (pa_rebin.cu): inputs, the plan
+// tables it rewrites and its scratch.
+struct RebinArgs {
+  int M, Mx, My, w, nstrips;
+  double X, Y, ax;         // period lengths and 1/(dx dy)
+  double beta, phi0;       // Kaiser-Bessel window of the plan
+  const float *xy;         // [M][2] new positions (caller's device buffer)
+  const double *weights;   // [M] detector areas h_m
+  int *status;             // plan status word (non-finite positions)
+  // plan tables (outputs)
+  int *perm, *sbx, *sby, *cell_start;
+  float *wx, *wy, *dwx, *dwy;
+  // scratch
+  int *bx, *by;
+  double *frx, *fry;
+  int *fill;               // max(cells, entry lists) counters
+  int *sp_cnt;             // [nstrips*My + 1] entry counts, then offsets
+  int *sp_m;               // entry lists (outputs, sized by the count)
+  float4 *sp_w;
+  long long *sp_key;       // order keys of the entries
+};
+cudaError_t rebin_sensors(const RebinArgs &a, cudaStream_t s);
+cudaError_t rebin_count_entries(const RebinArgs &a, cudaStream_t s);
+cudaError_t rebin_fill_entries(const RebinArgs &a, cudaStream_t s);
+// Status-word bit: non-finite sensor positions met by the device re-binning.
+constexpr int kStatusBadPositions = 2;
+
 // Read-only view of a plan for the other translation units of the library.
 struct PlanView {
   const InstDesc *h;        // host copy of the descriptor (device pointers inside)

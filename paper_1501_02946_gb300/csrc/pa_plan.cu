@@ -200,6 +200,9 @@ struct pa_plan {
   // forward-spread entry lists (device), reallocated when they outgrow it
   char *d_entries = nullptr;
   size_t entries_bytes = 0;
+  // device re-binning scratch (first pa_plan_update_positions_device call)
+  char *d_rebin = nullptr;
+  size_t rebin_bytes = 0;
   // optional per-stage event timing
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -345,6 +348,7 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
     if (P->d_entries) {
       PA_CUDA(cudaStreamSynchronize(stream));
       cudaFree(P->d_entries);
+  cudaFree(P->d_rebin);
       P->d_entries = nullptr;
       P->entries_bytes = 0;
     }
@@ -752,6 +756,103 @@ int pa_plan_update_positions(pa_plan *plan, const double *sensor_xy, void *strea
   if (rc != PA_OK) return rc;
   // the spread entry lists may have moved: refresh the device descriptor
   PA_CUDA(cudaMemcpyAsync(plan->d_desc, &plan->h, sizeof(InstDesc), cudaMemcpyHostToDevice, s));
+  return PA_OK;
+}
+
+int pa_plan_update_positions_device(pa_plan *plan, const float *xy_dev, void *stream) {
+  g_err.clear();
+  if (!plan || !xy_dev) return fail(PA_ERR_INVALID_ARG, "plan or xy_dev is NULL");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  pa_plan *P = plan;
+  InstDesc &h = P->h;
+  const int M = int(P->M), Mx = h.Mx, My = h.My, w = P->w;
+  const int nstrips = (Mx + pa::kSpreadP - 1) / pa::kSpreadP;
+  const size_t ncell = size_t(Mx) * My, nkeys = size_t(nstrips) * My;
+  // scratch: weights, bx, by, frx, fry, counters, entry counts
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + std::max<size_t>(bytes, 16));
+    return o;
+  };
+  const size_t o_w = take(sizeof(double) * M), o_bx = take(sizeof(int) * M), o_by = take(sizeof(int) * M);
+  const size_t o_fx = take(sizeof(double) * M), o_fy = take(sizeof(double) * M);
+  const size_t o_fill = take(sizeof(int) * std::max(ncell, nkeys)), o_cnt = take(sizeof(int) * (nkeys + 1));
+  if (!P->d_rebin) {
+    PA_CUDA(cudaMalloc(&P->d_rebin, off));
+    P->rebin_bytes = off;
+    PA_CUDA(cudaMemcpyAsync(P->d_rebin + o_w, P->weights.data(), sizeof(double) * M, cudaMemcpyHostToDevice, s));
+  }
+  char *R = P->d_rebin;
+  const Kb kb(w, P->sigma);
+  pa::RebinArgs a{};
+  a.M = M;
+  a.Mx = Mx;
+  a.My = My;
+  a.w = w;
+  a.nstrips = nstrips;
+  a.X = P->grid.nx * P->grid.dx;
+  a.Y = P->grid.ny * P->grid.dy;
+  a.ax = 1.0 / (P->grid.dx * P->grid.dy);
+  a.beta = kb.beta;
+  a.phi0 = kb.phi0;
+  a.xy = xy_dev;
+  a.weights = reinterpret_cast<const double *>(R + o_w);
+  a.status = h.status;
+  a.perm = const_cast<int *>(h.perm);
+  a.sbx = const_cast<int *>(h.sbx);
+  a.sby = const_cast<int *>(h.sby);
+  a.cell_start = const_cast<int *>(h.cell_start);
+  a.wx = const_cast<float *>(h.wx);
+  a.wy = const_cast<float *>(h.wy);
+  a.dwx = const_cast<float *>(h.dwx);
+  a.dwy = const_cast<float *>(h.dwy);
+  a.bx = reinterpret_cast<int *>(R + o_bx);
+  a.by = reinterpret_cast<int *>(R + o_by);
+  a.frx = reinterpret_cast<double *>(R + o_fx);
+  a.fry = reinterpret_cast<double *>(R + o_fy);
+  a.fill = reinterpret_cast<int *>(R + o_fill);
+  a.sp_cnt = reinterpret_cast<int *>(R + o_cnt);
+  int st0 = 0;
+  PA_CUDA(cudaMemcpyAsync(&st0, h.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PA_CUDA(pa::rebin_sensors(a, s));
+  PA_CUDA(pa::rebin_count_entries(a, s));
+  int nent = 0, st1 = 0;
+  PA_CUDA(cudaMemcpyAsync(&nent, a.sp_cnt + nkeys, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PA_CUDA(cudaMemcpyAsync(&st1, h.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PA_CUDA(cudaStreamSynchronize(s));
+  if ((st1 & pa::kStatusBadPositions) && !(st0 & pa::kStatusBadPositions)) {
+    int clear = st0;
+    PA_CUDA(cudaMemcpy(h.status, &clear, sizeof(int), cudaMemcpyHostToDevice));
+    return fail(PA_ERR_INVALID_ARG, "non-finite sensor position");
+  }
+  // entry lists: [sp_start | sp_m | sp_w | order keys]
+  size_t eo = 0;
+  auto place = [&](size_t bytes) {
+    const size_t o = eo;
+    eo = align_up(eo + std::max<size_t>(bytes, 16));
+    return o;
+  };
+  const size_t o_ss = place(sizeof(int) * (nkeys + 1)), o_sm = place(sizeof(int) * size_t(nent));
+  const size_t o_sw = place(sizeof(float4) * size_t(nent)), o_sk = place(sizeof(long long) * size_t(nent));
+  if (eo > P->entries_bytes) {
+    cudaFree(P->d_entries);
+    P->d_entries = nullptr;
+    P->entries_bytes = 0;
+    PA_CUDA(cudaMalloc(&P->d_entries, eo));
+    P->entries_bytes = eo;
+  }
+  char *V = P->d_entries;
+  a.sp_m = reinterpret_cast<int *>(V + o_sm);
+  a.sp_w = reinterpret_cast<float4 *>(V + o_sw);
+  a.sp_key = reinterpret_cast<long long *>(V + o_sk);
+  PA_CUDA(pa::rebin_fill_entries(a, s));
+  PA_CUDA(cudaMemcpyAsync(V + o_ss, a.sp_cnt, sizeof(int) * (nkeys + 1), cudaMemcpyDeviceToDevice, s));
+  h.sp_start = reinterpret_cast<const int *>(V + o_ss);
+  h.sp_m = a.sp_m;
+  h.sp_w = a.sp_w;
+  // pageable source: the copy has consumed the descriptor when it returns
+  PA_CUDA(cudaMemcpyAsync(P->d_desc, &h, sizeof(InstDesc), cudaMemcpyHostToDevice, s));
   return PA_OK;
 }
 

@@ -227,6 +227,45 @@ def test_update_positions_matches_new_plan():
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("name", ["c1", "tiny"])
+def test_update_positions_on_device_matches_host(name):
+    """Re-binning on the device (float32 positions, FP64 cell coordinates)
+    gives the tables of a host re-binning of the same positions: identical
+    sensor order and entry lists, taps to float rounding, the same image to
+    1e-6 and the same adjoint and position gradient."""
+    P = getattr(synth, name)()
+    rng = np.random.default_rng(22)
+    xy2 = (P.xy + rng.normal(scale=3e-5, size=P.xy.shape)).astype(np.float32)
+    # a few positions outside the period, reduced on the device
+    X = P.grid.nx * P.grid.dx
+    xy2[:3, 0] += np.float32(2 * X)
+    plan_d = plan_of(P)
+    plan_d.update_positions(torch.tensor(xy2, device="cuda"))
+    plan_h = plan_of(P)
+    plan_h.update_positions(xy2.astype(np.float64))
+    g = dev(P.g)
+    a, b = host(plan_d.reconstruct(g)), host(plan_h.reconstruct(g))
+    err = rel(a, b)
+    print(f"{name}: device vs host re-binning rel L2 = {err:.3e}")
+    assert err <= 1e-6
+    fb = dev(np.random.default_rng(23).normal(size=P.grid.shape))
+    assert rel(host(plan_d.adjoint(fb)), host(plan_h.adjoint(fb))) <= 1e-6
+    gd = host(plan_d.position_grad(g, fb)[1])
+    gh = host(plan_h.position_grad(g, fb)[1])
+    assert rel(gd, gh) <= 1e-5
+
+
+def test_update_positions_on_device_rejects_nonfinite():
+    P = synth.c1()
+    plan = plan_of(P)
+    xy = torch.tensor(P.xy.astype(np.float32), device="cuda")
+    xy[5, 1] = float("nan")
+    with pytest.raises(Exception):
+        plan.update_positions(xy)
+    # the status word is left as it was
+    assert plan.status() == 0
+
+
 # ---------------------------------------------------------- edge cases
 def test_positions_wrap_by_period():
     P = synth.c1()
