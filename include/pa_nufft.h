@@ -194,6 +194,21 @@ int pa_batch_destroy(pa_batch *batch);
  */
 int pa_status(pa_plan *plan, int *device_status, void *stream);
 
+/*
+ * Measure the alternative launch shapes of the plan's three heaviest stages
+ * on the device and keep the fastest of each: samples per lane of the spread
+ * (4 or 8), columns per block and block size of the NER kernels (2 or 4
+ * columns, 128 or 256 threads, as the shared memory and the transform plans
+ * allow) and the tile height of the interpolation (16 or 32 columns).  The
+ * forward results do not change (every shape sums in the same order); the
+ * adjoint's shared-memory accumulation order follows the NER block shape, so
+ * the adjoint and the gradient may change in the last bits.  Allocates a
+ * test input of the plan's sizes for the duration of the call and
+ * synchronises `stream`.  choice (NULL or int[4]) receives the shapes kept,
+ * in that order (samples per lane, columns, threads, tile height).
+ */
+int pa_plan_autotune(pa_plan *plan, void *stream, int *choice);
+
 /* Plan properties: sizes of the workspace in bytes and of the problem. */
 int pa_plan_info(const pa_plan *plan, int64_t *n_sensors, int64_t *n_t,
                  int64_t *workspace_bytes);

@@ -216,6 +216,14 @@ class Plan:
         check(lib.pa_profile_read(self.handle, ms, cnt))
         return {lib.pa_profile_stage_name(k).decode(): (ms[k], cnt[k]) for k in range(n) if cnt[k]}
 
+    def autotune(self):
+        """Time the alternative launch shapes of the spread, NER and
+        interpolation kernels and keep the fastest (pa_plan_autotune)."""
+        arr = (c_int * 4)()
+        check(_lib.load().pa_plan_autotune(self.handle, _stream_ptr(self.device), arr))
+        return {"spread_samples_per_lane": arr[0], "ner_columns_per_block": arr[1],
+                "ner_threads": arr[2], "interp_tile_columns": arr[3]}
+
     def status(self):
         v = c_int()
         rc = _lib.load().pa_status(self.handle, byref(v), _stream_ptr(self.device))

@@ -37,6 +37,7 @@ SIGNATURES = {
     "pa_position_grad_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pa_plan_update_positions": (c_int, [c_void_p, c_void_p, c_void_p]),
     "pa_plan_update_positions_device": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "pa_plan_autotune": (c_int, [c_void_p, c_void_p, POINTER(c_int)]),
     "pa_reconstruct_cubic": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pa_plan_destroy": (c_int, [c_void_p]),
     "pa_batch_create": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p), c_void_p]),

@@ -45,6 +45,8 @@ struct InstDesc {
   int ner_cb;           // columns per block of the NER kernels (1, 2 or 4)
   int ner_threads;      // block size of the NER kernels (128 or 256)
   int ner_lperm;        // adjoint NER depth order il = (i * ner_lperm) mod Nz
+  int spread_spl;       // samples per lane of the spread (4 or 8)
+  int interp_ty;        // grid columns per interpolation tile (16 or 32)
 
   FftPlan fMy, fMx, fMt, fNz, fNx, fNy, fNt;
   const float2 *tw;
@@ -147,7 +149,7 @@ cudaError_t launch_ner_stage(const Launch &L, int width, const HornerTable &ht, 
 cudaError_t launch_cubic(const Launch &L);
 cudaError_t launch_imgx(const Launch &L, bool adjoint);
 cudaError_t launch_imgy(const Launch &L, bool adjoint);
-cudaError_t launch_interp_width(const Launch &L, int width, bool grad);
+cudaError_t launch_interp_width(const Launch &L, int width, bool grad, int ty);
 cudaError_t launch_rowifft(const Launch &L);
 cudaError_t launch_grad_reduce(const Launch &L, int M);
 

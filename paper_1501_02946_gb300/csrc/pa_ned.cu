@@ -651,7 +651,7 @@ __global__ void k_grad_reduce(const InstDesc *__restrict__ descs, IoPtrs io0, co
 }  // namespace
 
 // ------------------------------------------------------------------ host side
-int spread_spl(const InstDesc &d) { return d.Nt > 128 ? 8 : 4; }
+int spread_spl(const InstDesc &d) { return d.spread_spl; }
 int blocks_spread(const InstDesc &d, int spl) {
   constexpr int QC = kThreadsSpread / 32;
   const int ch = 32 * spl;
@@ -664,7 +664,7 @@ int blocks_colfft(const InstDesc &d) { return d.nY1 * ((d.Nt + kColNC - 1) / kCo
 size_t smem_colfft(const InstDesc &d) { return (size_t)d.Mx * kColNC * sizeof(float2); }
 constexpr int kRowIfftNCP = 16;
 constexpr int kInterpTX = 8, kInterpTY = 32;
-int interp_ty(const InstDesc &d) { return d.w <= 8 ? kInterpTY : 16; }
+int interp_ty(const InstDesc &d) { return d.interp_ty; }
 int blocks_rowifft(const InstDesc &d) { return d.Mx * ((d.Nt + 2 * kRowIfftNCP - 1) / (2 * kRowIfftNCP)); }
 size_t smem_rowifft(const InstDesc &d) { return (size_t)d.My * kRowIfftNCP * sizeof(float2); }
 int blocks_interp(const InstDesc &d) {
@@ -754,14 +754,20 @@ static cudaError_t launch_interp_w(const Launch &L) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_interp_width(const Launch &L, int width, bool grad) {
+cudaError_t launch_interp_width(const Launch &L, int width, bool grad, int ty) {
+#define PA_INTERP_W(W)                                                                                  \
+  case W:                                                                                               \
+    if (ty == 32) return grad ? launch_interp_w<W, 32, true>(L) : launch_interp_w<W, 32, false>(L);     \
+    if (ty == 16) return grad ? launch_interp_w<W, 16, true>(L) : launch_interp_w<W, 16, false>(L);     \
+    return cudaErrorInvalidValue;
   switch (width) {
-    case 6: return grad ? launch_interp_w<6, kInterpTY, true>(L) : launch_interp_w<6, kInterpTY, false>(L);
-    case 8: return grad ? launch_interp_w<8, kInterpTY, true>(L) : launch_interp_w<8, kInterpTY, false>(L);
-    case 12: return grad ? launch_interp_w<12, 16, true>(L) : launch_interp_w<12, 16, false>(L);
-    case 16: return grad ? launch_interp_w<16, 16, true>(L) : launch_interp_w<16, 16, false>(L);
+    PA_INTERP_W(6)
+    PA_INTERP_W(8)
+    PA_INTERP_W(12)
+    PA_INTERP_W(16)
     default: return cudaErrorInvalidValue;
   }
+#undef PA_INTERP_W
 }
 
 cudaError_t launch_rowifft(const Launch &L) {

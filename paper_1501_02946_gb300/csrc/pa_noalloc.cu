@@ -111,7 +111,7 @@ extern "C" int pa_position_grad_noalloc(pa_plan *plan, const float *g_dev, const
   if ((rc = launched(pa::launch_rowifft(L), "rowifft")) != PA_OK) return rc;
   L.nblocks = pa::blocks_interp(h);
   L.smem = pa::smem_interp(h);
-  if ((rc = launched(pa::launch_interp_width(L, v.width, true), "interp")) != PA_OK) return rc;
+  if ((rc = launched(pa::launch_interp_width(L, v.width, true, h.interp_ty), "interp")) != PA_OK) return rc;
   L.nblocks = int((h.M + 255) / 256) < 1024 ? int((h.M + 255) / 256) : 1024;
   if ((rc = launched(pa::launch_grad_reduce(L, 1), "grad_reduce")) != PA_OK) return rc;
   return PA_OK;

@@ -97,6 +97,14 @@ struct Kb {
   }
 };
 
+// Depth-order stride of the adjoint NER spread: near Nz / (samples per
+// warp) and prime to Nz.
+int ner_lperm_for(int Nz, int cb) {
+  int K = std::max(1, Nz / (32 / cb) + 1);
+  while (std::gcd(K, Nz) != 1) ++K;
+  return K % Nz == 0 ? 1 : K;
+}
+
 bool smooth7(long n) {
   if (n < 1) return false;
   for (int p : {2, 3, 5, 7})
@@ -487,7 +495,8 @@ int run_adjoint(pa_plan *P, const IoPtrs &io, cudaStream_t s, bool grad) {
   if ((rc = timed(P, 12, s, [&] { return pa::launch_rowifft(L); }, "rowifft")) != PA_OK) return rc;
   L.nblocks = pa::blocks_interp(h);
   L.smem = pa::smem_interp(h);
-  if ((rc = timed(P, 9, s, [&] { return pa::launch_interp_width(L, P->w, grad); }, "interp")) != PA_OK) return rc;
+  if ((rc = timed(P, 9, s, [&] { return pa::launch_interp_width(L, P->w, grad, h.interp_ty); }, "interp")) != PA_OK)
+    return rc;
   if (grad) {
     L.nblocks = std::min(1024, int((P->M + 255) / 256));
     if ((rc = timed(P, 10, s, [&] { return pa::launch_grad_reduce(L, 1); }, "grad_reduce")) != PA_OK) return rc;
@@ -509,6 +518,45 @@ int plan_view(const pa_plan *P, PlanView *v) {
 }
 int set_error(int code, const char *msg) { return fail(code, msg ? msg : ""); }
 }  // namespace pa
+
+namespace {
+// Deterministic values in [-1, 1) for the autotuner's input.
+__global__ void k_fill_pattern(float *x, size_t n, uint32_t seed) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    uint32_t v = uint32_t(i) * 2654435761u ^ seed;
+    v ^= v >> 16;
+    v *= 2246822519u;
+    v ^= v >> 13;
+    x[i] = float(v & 0xffffffu) * (2.0f / 16777216.0f) - 1.0f;
+  }
+}
+
+// Median device time of `reps` calls of fn (after two untimed calls).
+template <typename Fn>
+int median_ms(cudaStream_t s, int reps, Fn fn, float *ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PA_CUDA(cudaEventCreate(&e0));
+  PA_CUDA(cudaEventCreate(&e1));
+  std::vector<float> t;
+  int rc = PA_OK;
+  for (int k = 0; k < reps + 2 && rc == PA_OK; ++k) {
+    cudaEventRecord(e0, s);
+    rc = fn();
+    cudaEventRecord(e1, s);
+    if (rc == PA_OK && cudaEventSynchronize(e1) == cudaSuccess && k >= 2) {
+      float v = 0.f;
+      cudaEventElapsedTime(&v, e0, e1);
+      t.push_back(v);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != PA_OK) return rc;
+  std::sort(t.begin(), t.end());
+  *ms = t.empty() ? 0.f : t[t.size() / 2];
+  return PA_OK;
+}
+}  // namespace
 
 extern "C" {
 
@@ -634,12 +682,10 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
   // their buffers stay within 48 KB
   h.ner_cb = 4;
   if (pa::smem_ner(h) > 48 * 1024) h.ner_cb = 2;
-  {
-    // a stride near Nz / (samples per warp) that is prime to Nz
-    int K = std::max(1, int(Nz) / (32 / h.ner_cb) + 1);
-    while (std::gcd(K, int(Nz)) != 1) ++K;
-    h.ner_lperm = K % int(Nz) == 0 ? 1 : K;
-  }
+  // launch shapes before any tuning (pa_plan_autotune measures the others)
+  h.spread_spl = Nt > 128 ? 8 : 4;
+  h.interp_ty = width <= 8 ? 32 : 16;
+  h.ner_lperm = ner_lperm_for(h.Nz, h.ner_cb);
 
   // deconvolution tables and time-frequency constants
   const Kb kb(width, sigma);
@@ -854,6 +900,128 @@ int pa_plan_update_positions_device(pa_plan *plan, const float *xy_dev, void *st
   // pageable source: the copy has consumed the descriptor when it returns
   PA_CUDA(cudaMemcpyAsync(P->d_desc, &h, sizeof(InstDesc), cudaMemcpyHostToDevice, s));
   return PA_OK;
+}
+
+int pa_plan_autotune(pa_plan *plan, void *stream, int *choice) {
+  g_err.clear();
+  if (!plan) return fail(PA_ERR_INVALID_ARG, "plan is NULL");
+  pa_plan *P = plan;
+  InstDesc &h = P->h;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t ng = size_t(P->M) * size_t(P->Nt), nf = size_t(h.Nx) * h.Ny * h.Nz;
+  float *g = nullptr, *f = nullptr;
+  if (cudaMalloc(&g, sizeof(float) * ng) != cudaSuccess || cudaMalloc(&f, sizeof(float) * nf) != cudaSuccess) {
+    cudaFree(g);
+    return fail(PA_ERR_OOM, "autotune: no room for the test input");
+  }
+  int rc = PA_OK;
+  const int ner_threads_min = h.ner_threads;
+  auto upload = [&]() { return check_launch(cudaMemcpyAsync(P->d_desc, &h, sizeof(InstDesc), cudaMemcpyHostToDevice, s), "descriptor"); };
+  IoPtrs io{};
+  io.g_in = g;
+  io.f_out = f;
+  io.f_in = f;
+  io.g_out = g;
+  do {
+    k_fill_pattern<<<1024, 256, 0, s>>>(g, ng, 1501u);
+    k_fill_pattern<<<1024, 256, 0, s>>>(f, nf, 2u);
+    if ((rc = check_launch(cudaGetLastError(), "autotune fill")) != PA_OK) break;
+    // one forward + adjoint so that every intermediate holds realistic values
+    IoPtrs fw{};
+    fw.g_in = g;
+    fw.f_out = f;
+    if ((rc = run_forward(P, fw, s, false)) != PA_OK) break;
+    if ((rc = run_adjoint(P, io, s, false)) != PA_OK) break;
+
+    pa::Launch L = make_launch(P, s);
+    L.io = io;
+    // spread: samples per lane
+    {
+      float best = 1e30f;
+      int pick = h.spread_spl;
+      for (int spl : {4, 8}) {
+        float ms = 0.f;
+        L.nblocks = pa::blocks_spread(h, spl);
+        L.smem = 0;
+        if ((rc = median_ms(s, 5, [&] { return check_launch(pa::launch_spread(L, spl), "spread"); }, &ms)) != PA_OK) break;
+        if (ms < best) {
+          best = ms;
+          pick = spl;
+        }
+      }
+      if (rc != PA_OK) break;
+      h.spread_spl = pick;
+    }
+    // NER: columns per block and block size (forward + adjoint)
+    {
+      float best = 1e30f;
+      int pick_cb = h.ner_cb, pick_t = h.ner_threads;
+      for (int cb : {2, 4})
+        for (int thr : {128, 256}) {
+          if (thr < ner_threads_min) continue;
+          h.ner_cb = cb;
+          h.ner_threads = thr;
+          h.ner_lperm = ner_lperm_for(h.Nz, cb);
+          if (pa::smem_ner(h) > P->smem_limit) continue;
+          if ((rc = upload()) != PA_OK) break;
+          // forward repetitions first (G1 fixed), then adjoint ones (Fz fixed)
+          float ms_f = 0.f, ms_a = 0.f;
+          L.threads = thr;
+          L.smem = pa::smem_ner(h);
+          L.nblocks = pa::blocks_ner(h);
+          rc = median_ms(s, 5, [&] { return check_launch(pa::launch_ner_stage(L, P->w, P->ht, 0), "ner"); }, &ms_f);
+          if (rc != PA_OK) break;
+          L.nblocks = pa::blocks_ner_adj(h);
+          rc = median_ms(s, 5, [&] { return check_launch(pa::launch_ner_stage(L, P->w, P->ht, 1), "ner_adj"); },
+                         &ms_a);
+          if (rc != PA_OK) break;
+          const float ms = ms_f + ms_a;
+          if (ms < best) {
+            best = ms;
+            pick_cb = cb;
+            pick_t = thr;
+          }
+        }
+      if (rc != PA_OK) break;
+      h.ner_cb = pick_cb;
+      h.ner_threads = pick_t;
+      h.ner_lperm = ner_lperm_for(h.Nz, pick_cb);
+      if ((rc = upload()) != PA_OK) break;
+    }
+    // interpolation: tile height
+    {
+      float best = 1e30f;
+      int pick = h.interp_ty;
+      for (int ty : {16, 32}) {
+        h.interp_ty = ty;
+        if (pa::smem_interp(h) > P->smem_limit) continue;
+        if ((rc = upload()) != PA_OK) break;
+        float ms = 0.f;
+        L.nblocks = pa::blocks_interp(h);
+        L.smem = pa::smem_interp(h);
+        if ((rc = median_ms(s, 5, [&] { return check_launch(pa::launch_interp_width(L, P->w, false, ty), "interp"); },
+                            &ms)) != PA_OK)
+          break;
+        if (ms < best) {
+          best = ms;
+          pick = ty;
+        }
+      }
+      if (rc != PA_OK) break;
+      h.interp_ty = pick;
+    }
+    rc = upload();
+  } while (false);
+  cudaStreamSynchronize(s);
+  cudaFree(g);
+  cudaFree(f);
+  if (rc == PA_OK && choice) {
+    choice[0] = h.spread_spl;
+    choice[1] = h.ner_cb;
+    choice[2] = h.ner_threads;
+    choice[3] = h.interp_ty;
+  }
+  return rc;
 }
 
 int pa_reconstruct(pa_plan *plan, const float *g_dev, float *f_dev, void *stream) {

@@ -266,6 +266,28 @@ def test_update_positions_on_device_rejects_nonfinite():
     assert plan.status() == 0
 
 
+@pytest.mark.parametrize("name", ["c1", "tiny"])
+def test_autotune_keeps_results(name):
+    """Every launch shape the autotuner may pick sums the forward in the same
+    order (bit-identical image); the adjoint's shared-memory accumulation
+    follows the NER block shape (equal to float rounding)."""
+    P = getattr(synth, name)()
+    plan = plan_of(P)
+    g = dev(P.g)
+    fb = dev(np.random.default_rng(24).normal(size=P.grid.shape))
+    before = (host(plan.reconstruct(g)), host(plan.adjoint(fb)), host(plan.position_grad(g, fb)[1]))
+    choice = plan.autotune()
+    print(name, choice)
+    assert choice["spread_samples_per_lane"] in (4, 8)
+    assert choice["ner_columns_per_block"] in (2, 4)
+    assert choice["ner_threads"] in (128, 256)
+    assert choice["interp_tile_columns"] in (16, 32)
+    after = (host(plan.reconstruct(g)), host(plan.adjoint(fb)), host(plan.position_grad(g, fb)[1]))
+    assert np.array_equal(before[0], after[0])
+    assert rel(after[1], before[1]) <= 1e-6
+    assert rel(after[2], before[2]) <= 1e-5
+
+
 # ---------------------------------------------------------- edge cases
 def test_positions_wrap_by_period():
     P = synth.c1()
