@@ -54,6 +54,9 @@ extern "C" {
 #define PA_ERR_DEVICE 6           /* a kernel recorded an error in the plan's status word */
 
 #define PA_FLAG_DEFAULT 0
+/* Keep the general (windowed) spatial step even for sensors on the output
+ * lattice; by default such plans take the lattice path (pa_plan_is_lattice). */
+#define PA_FLAG_NO_LATTICE 1
 
 typedef struct pa_plan pa_plan;
 typedef struct pa_batch pa_batch;
@@ -78,7 +81,7 @@ typedef struct {
  *   grid       output grid (sizes >= 2, spacings > 0).
  *   sigma      oversampling factor c of Sec. 3, integer in [2, 4].
  *   width      window taps 2K of Sec. 3, even, in {6, 8, 12, 16}.
- *   flags      PA_FLAG_DEFAULT.
+ *   flags      PA_FLAG_DEFAULT or PA_FLAG_NO_LATTICE.
  *   stream     stream used for the initial uploads (a cudaStream_t or NULL).
  * Supported sizes: nx, ny, nz, n_t and sigma*nx, sigma*ny, sigma*n_t must be
  * products of 2, 3, 5, 7, with sigma*nx, sigma*ny, nz, nx, ny <= 4096,
@@ -209,6 +212,20 @@ int pa_status(pa_plan *plan, int *device_status, void *stream);
  */
 int pa_plan_autotune(pa_plan *plan, void *stream, int *choice);
 
+/*
+ * *is_lattice = 1 when the plan's sensors sit exactly on the output lattice,
+ * x_m = (i - floor(nx/2)) dx and y_m = (k - floor(ny/2)) dy (modulo X, Y),
+ * one per node (M = nx ny), and PA_FLAG_NO_LATTICE was not given.  Such a
+ * plan computes the spatial step as a plain DFT over the lattice (the
+ * equispaced case of Sec. 2, which the NER-only reconstruction uses: no
+ * window, no oversampling in x and y) in pa_reconstruct and
+ * pa_reconstruct_adjoint; pa_position_grad keeps the windowed path, whose
+ * window derivative the gradient needs.  Positions set later with
+ * pa_plan_update_positions are tested again; pa_plan_update_positions_device
+ * switches the lattice path off.
+ */
+int pa_plan_is_lattice(const pa_plan *plan, int *is_lattice);
+
 /* Plan properties: sizes of the workspace in bytes and of the problem. */
 int pa_plan_info(const pa_plan *plan, int64_t *n_sensors, int64_t *n_t,
                  int64_t *workspace_bytes);
@@ -234,7 +251,7 @@ int pa_plan_buffer(const pa_plan *plan, int which, void *dst_dev, int64_t capaci
  * and the number of launches since the last read, and clears them.
  * Stages: see pa_profile_stage_name (0 .. PA_PROFILE_STAGES-1).
  */
-#define PA_PROFILE_STAGES 14
+#define PA_PROFILE_STAGES 17
 int pa_profile_enable(pa_plan *plan, int enable);
 int pa_profile_read(pa_plan *plan, double *ms_total, int64_t *launches);
 const char *pa_profile_stage_name(int stage);

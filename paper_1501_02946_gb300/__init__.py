@@ -53,7 +53,7 @@ class Plan:
     xy: (M, 2) sensor positions in metres; weights: (M,) detector areas in m^2
     or None (X*Y/M each); grid: (nx, ny, nz, dx, dy, dz)."""
 
-    def __init__(self, xy, n_t, dt, c, grid, weights=None, sigma=2, width=8, device=None):
+    def __init__(self, xy, n_t, dt, c, grid, weights=None, sigma=2, width=8, device=None, lattice=True):
         torch = _torch()
         lib = _lib.load()
         xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(-1, 2))
@@ -77,7 +77,8 @@ class Plan:
         with torch.cuda.device(self.device):
             rc = lib.pa_plan_create(byref(ptr), self.M, xy.ctypes.data_as(c_void_p),
                                     None if w is None else w.ctypes.data_as(c_void_p),
-                                    self.n_t, self.dt, self.c, byref(g), self.sigma, self.width, 0,
+                                    self.n_t, self.dt, self.c, byref(g), self.sigma, self.width,
+                                    0 if lattice else 1,  # PA_FLAG_NO_LATTICE
                                     _stream_ptr(self.device))
         check(rc)
         self._ptr = ptr
@@ -97,6 +98,14 @@ class Plan:
         if self._ptr is None or not self._ptr.value:
             raise RuntimeError("plan was destroyed")
         return self._ptr
+
+    @property
+    def is_lattice(self):
+        """True when the sensors sit on the output lattice and the plan takes
+        the lattice spatial step (pa_plan_is_lattice)."""
+        v = c_int()
+        check(_lib.load().pa_plan_is_lattice(self.handle, byref(v)))
+        return bool(v.value)
 
     def info(self):
         M, nt, ws = c_int64(), c_int64(), c_int64()

@@ -180,6 +180,13 @@ cudaError_t rebin_fill_entries(const RebinArgs &a, cudaStream_t s);
 // Status-word bit: non-finite sensor positions met by the device re-binning.
 constexpr int kStatusBadPositions = 2;
 
+// Lattice spatial step (pa_lattice.cu).
+cudaError_t launch_lattice_scatter(float *G0, const int *pq, const float *a, const float *g, int M, int Nt,
+                                   cudaStream_t s);
+cudaError_t launch_lattice_gather(float *g, const float *G0, const int *pq, const float *a, int M, int Nt,
+                                  cudaStream_t s);
+cudaError_t launch_lattice_alias(float2 *G1, int nY1, int Nt, int hx, int dir, cudaStream_t s);
+
 // Read-only view of a plan for the other translation units of the library.
 struct PlanView {
   const InstDesc *h;        // host copy of the descriptor (device pointers inside)

@@ -406,8 +406,8 @@ __global__ void __launch_bounds__(kThreadsCol) k_rowifft(const InstDesc *__restr
       },
       [&](int idx, float4 ab) {
         const int kk = idx % NCP, jy = idx / NCP;
-        if (jy == 0) {
-          S[kk] = make_float2(ab.x, ab.z);
+        if (jy == 0 || 2 * jy == My) {  // bins that are their own mirror
+          S[jy * NCP + kk] = make_float2(ab.x, ab.z);
         } else {
           S[jy * NCP + kk] = make_float2(0.5f * (ab.x - ab.w), 0.5f * (ab.y + ab.z));
           S[(My - jy) * NCP + kk] = make_float2(0.5f * (ab.x + ab.w), 0.5f * (ab.z - ab.y));
@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(kThreadsCol) k_rowifft_pipe(const InstDesc *__
         const float sc = __ldg(d.invphy + jy);
         const float2 a = n < Nt ? cscale(stg[jy * 2 * NCP + 2 * kk], sc) : make_float2(0.f, 0.f);
         const float2 b = n + 1 < Nt ? cscale(stg[jy * 2 * NCP + 2 * kk + 1], sc) : make_float2(0.f, 0.f);
-        if (q == 0) {
+        if (q == 0 || 2 * q == L) {  // bins that are their own mirror
           v = make_float2(a.x, b.x);
         } else if (q == jy) {
           v = make_float2(0.5f * (a.x - b.y), 0.5f * (a.y + b.x));

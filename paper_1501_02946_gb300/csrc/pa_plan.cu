@@ -211,6 +211,14 @@ struct pa_plan {
   // device re-binning scratch (first pa_plan_update_positions_device call)
   char *d_rebin = nullptr;
   size_t rebin_bytes = 0;
+  // lattice path: sensors on the output lattice (see pa_plan_is_lattice)
+  bool lattice_allowed = true;
+  bool lattice = false;
+  InstDesc hl{};                  // spatial-step descriptor at sigma = 1
+  InstDesc *d_desc_lat = nullptr;
+  char *d_lattice = nullptr;      // node of each sensor | h_m/(dx dy) | ones
+  const int *lat_pq = nullptr;
+  const float *lat_amp = nullptr;
   // optional per-stage event timing
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -357,6 +365,8 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
       PA_CUDA(cudaStreamSynchronize(stream));
       cudaFree(P->d_entries);
   cudaFree(P->d_rebin);
+  cudaFree(P->d_lattice);
+  cudaFree(P->d_desc_lat);
       P->d_entries = nullptr;
       P->entries_bytes = 0;
     }
@@ -410,7 +420,7 @@ int check_launch(cudaError_t e, const char *what) {
 const char *const kStageNames[PA_PROFILE_STAGES] = {
     "ned_spread", "ned_colfft", "ner_fused", "image_x", "image_y_c2r", "image_y_adj",
     "image_x_adj", "ner_adj", "ned_colfft_adj", "ned_interp", "grad_reduce", "cubic_baseline", "ned_rowifft",
-    "ned_rowfft"};
+    "ned_rowfft", "lattice_scatter", "lattice_gather", "lattice_alias"};
 
 cudaEvent_t take_event(pa_plan *P) {
   if (!P->ev_pool.empty()) {
@@ -445,15 +455,37 @@ int run_forward(pa_plan *P, const IoPtrs &io, cudaStream_t s, bool cubic) {
   L.io = io;
   const InstDesc &h = P->h;
   int rc;
-  L.nblocks = pa::blocks_spread(h, pa::spread_spl(h));
-  L.smem = 0;
-  if ((rc = timed(P, 0, s, [&] { return pa::launch_spread(L, pa::spread_spl(h)); }, "spread")) != PA_OK) return rc;
-  L.nblocks = pa::blocks_rowfft(h);
-  L.smem = pa::smem_rowfft(h);
-  if ((rc = timed(P, 13, s, [&] { return pa::launch_rowfft(L); }, "rowfft")) != PA_OK) return rc;
-  L.nblocks = pa::blocks_colfft(h);
-  L.smem = pa::smem_colfft(h);
-  if ((rc = timed(P, 1, s, [&] { return pa::launch_colfft(L, false); }, "colfft")) != PA_OK) return rc;
+  if (P->lattice) {
+    // sensors on the lattice: place, then DFT over the lattice (sigma = 1)
+    const InstDesc &hl = P->hl;
+    if ((rc = timed(P, 14, s, [&] {
+           return pa::launch_lattice_scatter(h.G0, P->lat_pq, P->lat_amp, io.g_in, int(P->M), h.Nt, s);
+         }, "lattice_scatter")) != PA_OK)
+      return rc;
+    pa::Launch Ll = L;
+    Ll.descs = P->d_desc_lat;
+    Ll.host = &hl;
+    Ll.nblocks = pa::blocks_rowfft(hl);
+    Ll.smem = pa::smem_rowfft(hl);
+    if ((rc = timed(P, 13, s, [&] { return pa::launch_rowfft(Ll); }, "rowfft")) != PA_OK) return rc;
+    Ll.nblocks = pa::blocks_colfft(hl);
+    Ll.smem = pa::smem_colfft(hl);
+    if ((rc = timed(P, 1, s, [&] { return pa::launch_colfft(Ll, false); }, "colfft")) != PA_OK) return rc;
+    if ((h.Nx & 1) == 0 &&
+        (rc = timed(P, 16, s, [&] { return pa::launch_lattice_alias(h.G1, h.nY1, h.Nt, h.hx, 0, s); },
+                    "lattice_alias")) != PA_OK)
+      return rc;
+  } else {
+    L.nblocks = pa::blocks_spread(h, pa::spread_spl(h));
+    L.smem = 0;
+    if ((rc = timed(P, 0, s, [&] { return pa::launch_spread(L, pa::spread_spl(h)); }, "spread")) != PA_OK) return rc;
+    L.nblocks = pa::blocks_rowfft(h);
+    L.smem = pa::smem_rowfft(h);
+    if ((rc = timed(P, 13, s, [&] { return pa::launch_rowfft(L); }, "rowfft")) != PA_OK) return rc;
+    L.nblocks = pa::blocks_colfft(h);
+    L.smem = pa::smem_colfft(h);
+    if ((rc = timed(P, 1, s, [&] { return pa::launch_colfft(L, false); }, "colfft")) != PA_OK) return rc;
+  }
   L.threads = h.ner_threads;
   L.nblocks = pa::blocks_ner(h);
   L.smem = pa::smem_ner(h);
@@ -486,6 +518,26 @@ int run_adjoint(pa_plan *P, const IoPtrs &io, cudaStream_t s, bool grad) {
   L.nblocks = pa::blocks_ner_adj(h);
   L.smem = pa::smem_ner(h);
   if ((rc = timed(P, 7, s, [&] { return pa::launch_ner_stage(L, P->w, P->ht, 1); }, "ner_adj")) != PA_OK) return rc;
+
+  if (P->lattice && !grad) {
+    const InstDesc &hl = P->hl;
+    if ((h.Nx & 1) == 0 &&
+        (rc = timed(P, 16, s, [&] { return pa::launch_lattice_alias(h.G1, h.nY1, h.Nt, h.hx, 1, s); },
+                    "lattice_alias")) != PA_OK)
+      return rc;
+    pa::Launch Ll = L;
+    Ll.descs = P->d_desc_lat;
+    Ll.host = &hl;
+    Ll.nblocks = pa::blocks_colfft(hl);
+    Ll.smem = pa::smem_colfft(hl);
+    if ((rc = timed(P, 8, s, [&] { return pa::launch_colfft(Ll, true); }, "colfft_adj")) != PA_OK) return rc;
+    Ll.nblocks = pa::blocks_rowifft(hl);
+    Ll.smem = pa::smem_rowifft(hl);
+    if ((rc = timed(P, 12, s, [&] { return pa::launch_rowifft(Ll); }, "rowifft")) != PA_OK) return rc;
+    return timed(P, 15, s, [&] {
+      return pa::launch_lattice_gather(io.g_out, h.G0, P->lat_pq, P->lat_amp, int(P->M), h.Nt, s);
+    }, "lattice_gather");
+  }
 
   L.nblocks = pa::blocks_colfft(h);
   L.smem = pa::smem_colfft(h);
@@ -558,6 +610,67 @@ int median_ms(cudaStream_t s, int reps, Fn fn, float *ms) {
 }
 }  // namespace
 
+namespace {
+// Sensors exactly on the output lattice, one per node: node index p*ny + q
+// of each sensor on the sigma = 1 grid (p = i - floor(nx/2) mod nx for
+// x = (i - floor(nx/2)) dx after the reduction modulo X; q likewise).
+bool lattice_nodes(const pa_plan *P, const double *xy, std::vector<int> &pq) {
+  const int nx = P->grid.nx, ny = P->grid.ny;
+  if (P->M != int64_t(nx) * ny) return false;
+  const double X = nx * P->grid.dx, Y = ny * P->grid.dy;
+  std::vector<char> seen(size_t(P->M), 0);
+  pq.assign(size_t(P->M), 0);
+  for (int64_t m = 0; m < P->M; ++m) {
+    double ux = xy[2 * m] / X, uy = xy[2 * m + 1] / Y;
+    ux -= std::floor(ux + 0.5);
+    uy -= std::floor(uy + 0.5);
+    const double fi = ux * nx, fk = uy * ny;
+    const double ri = std::nearbyint(fi), rk = std::nearbyint(fk);
+    if (std::fabs(fi - ri) > 1e-9 || std::fabs(fk - rk) > 1e-9) return false;
+    const int p = ((int(ri) % nx) + nx) % nx, q = ((int(rk) % ny) + ny) % ny;
+    const size_t k = size_t(p) * ny + q;
+    if (seen[k]) return false;
+    seen[k] = 1;
+    pq[size_t(m)] = int(k);
+  }
+  return true;
+}
+
+// Decide and set up the lattice path for host positions xy.
+int setup_lattice(pa_plan *P, const double *xy, cudaStream_t s) {
+  std::vector<int> pq;
+  P->lattice = P->lattice_allowed && lattice_nodes(P, xy, pq);
+  if (!P->lattice) return PA_OK;
+  const InstDesc &h = P->h;
+  const size_t M = size_t(P->M), nones = size_t(std::max(h.nX1, h.nY1));
+  const size_t o_pq = 0, o_amp = align_up(sizeof(int) * M), o_one = o_amp + align_up(sizeof(float) * M);
+  if (!P->d_lattice) PA_CUDA(cudaMalloc(&P->d_lattice, o_one + sizeof(float) * nones));
+  if (!P->d_desc_lat) PA_CUDA(cudaMalloc(&P->d_desc_lat, sizeof(InstDesc)));
+  std::vector<float> amp(M), ones(nones, 1.0f);
+  const double ax = 1.0 / (P->grid.dx * P->grid.dy);
+  for (size_t m = 0; m < M; ++m) amp[m] = float(P->weights[m] * ax);
+  char *D = P->d_lattice;
+  PA_CUDA(cudaMemcpyAsync(D + o_pq, pq.data(), sizeof(int) * M, cudaMemcpyHostToDevice, s));
+  PA_CUDA(cudaMemcpyAsync(D + o_amp, amp.data(), sizeof(float) * M, cudaMemcpyHostToDevice, s));
+  PA_CUDA(cudaMemcpyAsync(D + o_one, ones.data(), sizeof(float) * nones, cudaMemcpyHostToDevice, s));
+  P->lat_pq = reinterpret_cast<const int *>(D + o_pq);
+  P->lat_amp = reinterpret_cast<const float *>(D + o_amp);
+  const float *one = reinterpret_cast<const float *>(D + o_one);
+  InstDesc &hl = P->hl;
+  hl = h;
+  hl.Mx = h.Nx;
+  hl.My = h.Ny;
+  hl.fMx = h.fNx;
+  hl.fMy = h.fNy;
+  hl.invphx = one;
+  hl.invphy = one;
+  hl.nX1 = h.Nx;  // the row of +nx/2 (even nx) is the bin of -nx/2: see launch_lattice_alias
+  // pageable source: consumed when the call returns
+  PA_CUDA(cudaMemcpyAsync(P->d_desc_lat, &hl, sizeof(InstDesc), cudaMemcpyHostToDevice, s));
+  return PA_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char *pa_last_error(void) { return g_err.c_str(); }
@@ -581,7 +694,7 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
   if (sigma < 2 || sigma > 4) return fail(PA_ERR_INVALID_ARG, "sigma must be 2, 3 or 4");
   if (!(width == 6 || width == 8 || width == 12 || width == 16))
     return fail(PA_ERR_INVALID_ARG, "width must be 6, 8, 12 or 16");
-  if (flags != PA_FLAG_DEFAULT) return fail(PA_ERR_INVALID_ARG, "unknown flags");
+  if ((flags & ~PA_FLAG_NO_LATTICE) != 0) return fail(PA_ERR_INVALID_ARG, "unknown flags");
   for (int64_t m = 0; m < 2 * n_sensors; ++m)
     if (!std::isfinite(sensor_xy[m])) return fail(PA_ERR_INVALID_ARG, "non-finite sensor position");
   const double X = grid->nx * grid->dx, Y = grid->ny * grid->dy;
@@ -772,6 +885,10 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
   h.G0 = reinterpret_cast<float *>(Wk + o_G0);
 
   int rc = upload_sensors(P, sensor_xy, s);
+  if (rc == PA_OK) {
+    P->lattice_allowed = (flags & PA_FLAG_NO_LATTICE) == 0;
+    rc = setup_lattice(P, sensor_xy, s);
+  }
   if (rc != PA_OK) {
     free_plan(P);
     return rc;
@@ -802,7 +919,7 @@ int pa_plan_update_positions(pa_plan *plan, const double *sensor_xy, void *strea
   if (rc != PA_OK) return rc;
   // the spread entry lists may have moved: refresh the device descriptor
   PA_CUDA(cudaMemcpyAsync(plan->d_desc, &plan->h, sizeof(InstDesc), cudaMemcpyHostToDevice, s));
-  return PA_OK;
+  return setup_lattice(plan, sensor_xy, s);
 }
 
 int pa_plan_update_positions_device(pa_plan *plan, const float *xy_dev, void *stream) {
@@ -810,6 +927,7 @@ int pa_plan_update_positions_device(pa_plan *plan, const float *xy_dev, void *st
   if (!plan || !xy_dev) return fail(PA_ERR_INVALID_ARG, "plan or xy_dev is NULL");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   pa_plan *P = plan;
+  P->lattice = false;  // positions on the device are not tested for the lattice
   InstDesc &h = P->h;
   const int M = int(P->M), Mx = h.Mx, My = h.My, w = P->w;
   const int nstrips = (Mx + pa::kSpreadP - 1) / pa::kSpreadP;
@@ -1113,6 +1231,13 @@ int pa_status(pa_plan *plan, int *device_status, void *stream) {
   PA_CUDA(cudaMemsetAsync(plan->h.status, 0, sizeof(int), s));
   *device_status = v;
   return v ? fail(PA_ERR_DEVICE, "a kernel recorded an error") : PA_OK;
+}
+
+int pa_plan_is_lattice(const pa_plan *plan, int *is_lattice) {
+  g_err.clear();
+  if (!plan || !is_lattice) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  *is_lattice = plan->lattice ? 1 : 0;
+  return PA_OK;
 }
 
 int pa_plan_info(const pa_plan *plan, int64_t *n_sensors, int64_t *n_t, int64_t *workspace_bytes) {
