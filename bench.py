@@ -343,10 +343,25 @@ def run_ours(args):
         return torch.fft.fft(t, dim=0)
     cufft_ms = timed_calls(cufft_rows_cols, k_parts)
     del g0
+    # the same output grid and samples with the sensors on the output lattice
+    # (the lattice spatial step: no window spreading)
+    import numpy as np
+    xy_l = synth.lattice_positions(Nx, Ny, P.grid.dx, P.grid.dy)
+    plan_l = pa.Plan(xy_l, P.n_t, P.dt, P.c, P.grid.as_tuple())
+    g_l = torch.randn(Nx * Ny, P.n_t, device=dev, dtype=torch.float32)
+    def lattice_step():
+        plan_l.reconstruct(g_l, out=f)
+        plan_l.adjoint(f, out=g_l)
+    lat_ms = timed_calls(lattice_step, k_parts) if plan_l.is_lattice else None
+    plan_l.close()
+    del g_l
     parts = {"forward": {"ms": fwd_ms, "voxels_per_s": voxels / (fwd_ms / 1e3)},
              "adjoint": {"ms": adj_ms, "voxels_per_s": voxels / (adj_ms / 1e3)},
              "cubic_baseline_forward": {"ms": cub_ms, "voxels_per_s": voxels / (cub_ms / 1e3)},
              "cufft_row_col_transforms_ms": cufft_ms,
+             "lattice_sensors_fwd_adj": None if lat_ms is None else
+             {"ms": lat_ms, "voxels_per_s": voxels / (lat_ms / 1e3),
+              "workload": f"{Nx}x{Ny} sensors on the output lattice, same samples and output"},
              "own_row_col_transforms_ms": (prof["ned_rowfft"][0] / prof["ned_rowfft"][1]
                                            + prof["ned_colfft"][0] / prof["ned_colfft"][1])
              if "ned_rowfft" in prof and "ned_colfft" in prof else None,
