@@ -57,6 +57,11 @@ extern "C" {
 /* Keep the general (windowed) spatial step even for sensors on the output
  * lattice; by default such plans take the lattice path (pa_plan_is_lattice). */
 #define PA_FLAG_NO_LATTICE 1
+/* Run the NER stage (Sec. 3) with the block kernels, which hold CB columns
+ * per block, even where the warp-per-column kernels apply (sigma = 2, width
+ * 8, n_t and nz powers of two in [256, 1024]).  Both compute the same
+ * operator; the flag exists to compare them. */
+#define PA_FLAG_BLOCK_NER 2
 
 typedef struct pa_plan pa_plan;
 typedef struct pa_batch pa_batch;
@@ -81,7 +86,8 @@ typedef struct {
  *   grid       output grid (sizes >= 2, spacings > 0).
  *   sigma      oversampling factor c of Sec. 3, integer in [2, 4].
  *   width      window taps 2K of Sec. 3, even, in {6, 8, 12, 16}.
- *   flags      PA_FLAG_DEFAULT or PA_FLAG_NO_LATTICE.
+ *   flags      PA_FLAG_DEFAULT or a bitwise or of PA_FLAG_NO_LATTICE and
+ *              PA_FLAG_BLOCK_NER.
  *   stream     stream used for the initial uploads (a cudaStream_t or NULL).
  * Supported sizes: nx, ny, nz, n_t and sigma*nx, sigma*ny, sigma*n_t must be
  * products of 2, 3, 5, 7, with sigma*nx, sigma*ny, nz, nx, ny <= 4096,
@@ -202,7 +208,8 @@ int pa_status(pa_plan *plan, int *device_status, void *stream);
  * on the device and keep the fastest of each: samples per lane of the spread
  * (4 or 8), columns per block and block size of the NER kernels (2 or 4
  * columns, 128 or 256 threads, as the shared memory and the transform plans
- * allow) and the tile height of the interpolation (16 or 32 columns).  The
+ * allow; only for plans on the block NER kernels, see PA_FLAG_BLOCK_NER)
+ * and the tile height of the interpolation (16 or 32 columns).  The
  * forward results do not change (every shape sums in the same order); the
  * adjoint's shared-memory accumulation order follows the NER block shape, so
  * the adjoint and the gradient may change in the last bits.  Allocates a
@@ -225,6 +232,14 @@ int pa_plan_autotune(pa_plan *plan, void *stream, int *choice);
  * switches the lattice path off.
  */
 int pa_plan_is_lattice(const pa_plan *plan, int *is_lattice);
+
+/*
+ * *warp = 1 when the plan's NER stage (Sec. 3) runs the warp-per-column
+ * kernels (one warp transforms, interpolates and back-transforms a whole
+ * column; sigma = 2, width 8, n_t and nz powers of two in [256, 1024], and
+ * PA_FLAG_BLOCK_NER not given), 0 when it runs the block kernels.
+ */
+int pa_plan_uses_warp_ner(const pa_plan *plan, int *warp);
 
 /* Plan properties: sizes of the workspace in bytes and of the problem. */
 int pa_plan_info(const pa_plan *plan, int64_t *n_sensors, int64_t *n_t,

@@ -53,7 +53,8 @@ class Plan:
     xy: (M, 2) sensor positions in metres; weights: (M,) detector areas in m^2
     or None (X*Y/M each); grid: (nx, ny, nz, dx, dy, dz)."""
 
-    def __init__(self, xy, n_t, dt, c, grid, weights=None, sigma=2, width=8, device=None, lattice=True):
+    def __init__(self, xy, n_t, dt, c, grid, weights=None, sigma=2, width=8, device=None, lattice=True,
+                 warp_ner=True):
         torch = _torch()
         lib = _lib.load()
         xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(-1, 2))
@@ -78,7 +79,8 @@ class Plan:
             rc = lib.pa_plan_create(byref(ptr), self.M, xy.ctypes.data_as(c_void_p),
                                     None if w is None else w.ctypes.data_as(c_void_p),
                                     self.n_t, self.dt, self.c, byref(g), self.sigma, self.width,
-                                    0 if lattice else 1,  # PA_FLAG_NO_LATTICE
+                                    (0 if lattice else 1)  # PA_FLAG_NO_LATTICE
+                                    | (0 if warp_ner else 2),  # PA_FLAG_BLOCK_NER
                                     _stream_ptr(self.device))
         check(rc)
         self._ptr = ptr
@@ -105,6 +107,14 @@ class Plan:
         the lattice spatial step (pa_plan_is_lattice)."""
         v = c_int()
         check(_lib.load().pa_plan_is_lattice(self.handle, byref(v)))
+        return bool(v.value)
+
+    @property
+    def warp_ner(self):
+        """True when the NER stage runs the warp-per-column kernels
+        (pa_plan_uses_warp_ner)."""
+        v = c_int()
+        check(_lib.load().pa_plan_uses_warp_ner(self.handle, byref(v)))
         return bool(v.value)
 
     def info(self):

@@ -39,6 +39,7 @@ SIGNATURES = {
     "pa_plan_update_positions_device": (c_int, [c_void_p, c_void_p, c_void_p]),
     "pa_plan_autotune": (c_int, [c_void_p, c_void_p, POINTER(c_int)]),
     "pa_plan_is_lattice": (c_int, [c_void_p, POINTER(c_int)]),
+    "pa_plan_uses_warp_ner": (c_int, [c_void_p, POINTER(c_int)]),
     "pa_reconstruct_cubic": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pa_plan_destroy": (c_int, [c_void_p]),
     "pa_batch_create": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p), c_void_p]),

@@ -83,6 +83,18 @@ struct Tw16 {
   }
   __device__ __forceinline__ static constexpr float s(int m) { return c((m + 12) & 15); }
 };
+// cos and sin of 2 pi m / 32 from the first octant by symmetry.
+struct Tw32 {
+  __device__ __forceinline__ static constexpr float oct(int m) {  // cos(2 pi m / 32), 0 <= m <= 8
+    return m == 0 ? 1.0f : m == 1 ? 0.98078528040323043f : m == 2 ? 0.92387953251128674f
+         : m == 3 ? 0.83146961230254524f : m == 4 ? 0.70710678118654752f : m == 5 ? 0.55557023301960218f
+         : m == 6 ? 0.38268343236508977f : m == 7 ? 0.19509032201612826f : 0.0f;
+  }
+  __device__ __forceinline__ static constexpr float c(int m) {
+    return m <= 8 ? oct(m) : m <= 16 ? -oct(16 - m) : m <= 24 ? -oct(m - 16) : oct(32 - m);
+  }
+  __device__ __forceinline__ static constexpr float s(int m) { return c((m + 24) & 31); }
+};
 struct Tw3 {
   __device__ __forceinline__ static constexpr float c(int m) { return m == 0 ? 1.0f : -0.5f; }
   __device__ __forceinline__ static constexpr float s(int m) {
@@ -167,9 +179,9 @@ struct Dft<5, DIR> : DftNaive<Tw5, 5, DIR> {};
 template <int DIR>
 struct Dft<7, DIR> : DftNaive<Tw7, 7, DIR> {};
 
-// Cooley-Tukey composition N = N1 N2 (N divides 16): n = N2 n1 + n2,
-// k = k1 + N1 k2, inner twiddle exp(DIR 2 pi i n2 k1 / N).
-template <int N1, int N2, int DIR>
+// Cooley-Tukey composition N = N1 N2 (N divides the size TWN of the table
+// TW): n = N2 n1 + n2, k = k1 + N1 k2, inner twiddle exp(DIR 2 pi i n2 k1 / N).
+template <int N1, int N2, int DIR, typename TW = Tw16, int TWN = 16>
 struct DftComp {
   __device__ __forceinline__ static void run(float2 *v) {
     constexpr int N = N1 * N2;
@@ -182,11 +194,11 @@ struct DftComp {
       Dft<N1, DIR>::run(t);
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) {
-        const int e = ((n2 * k1) * (16 / N)) % 16;
+        const int e = ((n2 * k1) * (TWN / N)) % TWN;
         if (e == 0) {
           y[n2][k1] = t[k1];
         } else {
-          const float c = Tw16::c(e), s = DIR * Tw16::s(e);
+          const float c = TW::c(e), s = DIR * TW::s(e);
           y[n2][k1] = make_float2(t[k1].x * c - t[k1].y * s, t[k1].x * s + t[k1].y * c);
         }
       }
@@ -206,6 +218,8 @@ template <int DIR>
 struct Dft<8, DIR> : DftComp<2, 4, DIR> {};
 template <int DIR>
 struct Dft<16, DIR> : DftComp<4, 4, DIR> {};
+template <int DIR>
+struct Dft<32, DIR> : DftComp<2, 16, DIR, Tw32, 32> {};
 
 // Items (butterflies) a thread holds per round, by radix.
 template <int R>

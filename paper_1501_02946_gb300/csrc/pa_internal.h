@@ -47,6 +47,8 @@ struct InstDesc {
   int ner_lperm;        // adjoint NER depth order il = (i * ner_lperm) mod Nz
   int spread_spl;       // samples per lane of the spread (4 or 8)
   int interp_ty;        // grid columns per interpolation tile (16 or 32)
+  int ner_warp;         // 1: the NER stage runs the warp-per-column kernels
+  int wtw;              // offset of the warp-transform twiddle tables in tw
 
   FftPlan fMy, fMx, fMt, fNz, fNx, fNy, fNt;
   const float2 *tw;
@@ -89,6 +91,15 @@ struct InstDesc {
   float *G0;            // [Mx][My][Nt] real oversampled grid (forward) or its cotangent (adjoint)
   int *status;
 };
+
+// Twiddle tables of the warp-per-column NER kernels, appended to the plan's
+// twiddle array at InstDesc::wtw: for N = 2^lgn, lgn = 8, 9, 10, the rows
+// [k2][n1] = exp(-2 pi i n1 k2 / N) (k2 < N/32, n1 < 32) at wtw_T(lgn), then
+// for M = 2^lgm, lgm = 9, 10, 11, the circle exp(-2 pi i j / M), j < M, at
+// wtw_F(lgm).
+__host__ __device__ constexpr int wtw_T(int lgn) { return lgn == 8 ? 0 : (lgn == 9 ? 256 : 768); }
+__host__ __device__ constexpr int wtw_F(int lgm) { return lgm == 9 ? 1792 : (lgm == 10 ? 2304 : 3328); }
+constexpr int kWtwSize = 5376;
 
 // Caller buffers of one call (device pointers).  Single-plan launches pass
 // them by value; batched launches pass a device table indexed by instance.
@@ -147,6 +158,12 @@ cudaError_t launch_ner(const Launch &L, int width, const HornerTable &ht, bool a
 // which: 0 forward, 1 adjoint
 cudaError_t launch_ner_stage(const Launch &L, int width, const HornerTable &ht, int which);
 cudaError_t launch_cubic(const Launch &L);
+// Warp-per-column NER kernels (pa_ner_warp.cu): sigma = 2, width 8, Nt and
+// Nz powers of two in [256, 1024]; single-plan launches (L.host set).
+bool ner_warp_eligible(const InstDesc &d);
+size_t smem_ner_warp(const InstDesc &d);
+int ner_warp_block_warps(const InstDesc &d);
+cudaError_t launch_ner_warp(const Launch &L, const HornerTable &ht, int which);
 cudaError_t launch_imgx(const Launch &L, bool adjoint);
 cudaError_t launch_imgy(const Launch &L, bool adjoint);
 cudaError_t launch_interp_width(const Launch &L, int width, bool grad, int ty);

@@ -18,7 +18,7 @@
 // Such columns take two passes (one per source); the work items are ordered
 // so that one-pass columns fill most blocks.
 // The adjoint kernel is the exact transpose (spread <-> interpolate).
-#include "pa_device.cuh"
+#include "pa_ner_common.cuh"
 
 namespace pa {
 
@@ -28,66 +28,6 @@ constexpr int kNerMaxCB = 4;  // most columns per block
 constexpr int kNerPad = 4;    // one pad row per 16 rows of the [n][CB] buffers
 __device__ __forceinline__ int prow(int e) { return pad_row<kNerPad>(e); }
 
-
-template <int W>
-struct HornerDeg {
-  static constexpr int v = W <= 6 ? 7 : (W <= 8 ? 8 : (W <= 12 ? 10 : 14));
-};
-
-__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
-
-// tau(j, l) = sign(l) sqrt(ax jx^2 + ay jy^2 + az l^2) in double-float.
-__device__ __forceinline__ ff tau_of(const InstDesc &d, int jx, int jy, int l) {
-  const float jx2 = float(jx * jx), jy2 = float(jy * jy), l2 = float(l * l);
-  ff t2 = ff_add(ff_add(ff_mul_f({d.ax_hi, d.ax_lo}, jx2), ff_mul_f({d.ay_hi, d.ay_lo}, jy2)),
-                 ff_mul_f({d.az_hi, d.az_lo}, l2));
-  ff t = ff_sqrt(t2);
-  return l < 0 ? ff_neg(t) : t;
-}
-
-// W(j, l) = 2 c |kz| / |K| with W(0, 0) = 2c and W(j != 0, 0) = 0.
-__device__ __forceinline__ float weight_of(const InstDesc &d, ff tau, int l) {
-  if (l == 0) return tau.hi == 0.f ? d.two_c : 0.f;
-  return d.two_c * d.sqrt_az * fabsf(float(l)) / fabsf(tau.hi);
-}
-
-// exp(-2 pi i tau nc / Nt) with the argument reduced in double-float.
-__device__ __forceinline__ float2 centring_phase(const InstDesc &d, ff tau) {
-  ff turns = ff_mul(tau, {d.ph_hi, d.ph_lo});
-  const float ti = rintf(turns.hi);
-  const float tr = (turns.hi - ti) + turns.lo;
-  float sn, cs;
-  sincospif(-2.f * tr, &sn, &cs);
-  return make_float2(cs, sn);
-}
-
-// First tap index (mod L) and fraction of the point u = scale * tau.
-__device__ __forceinline__ void footprint(ff tau, int scale, int L, int half, int &p0, float &fr) {
-  const float uh = tau.hi * float(scale), ul = tau.lo * float(scale);
-  float fb = floorf(uh);
-  fr = (uh - fb) + ul;
-  if (fr < 0.f) {
-    fr += 1.f;
-    fb -= 1.f;
-  } else if (fr >= 1.f) {
-    fr -= 1.f;
-    fb += 1.f;
-  }
-  p0 = wrap(int(fb) - half + 1, L);
-}
-
-template <int W>
-__device__ __forceinline__ void window_taps(float fr, const HornerTable &ht, float *wt) {
-  constexpr int D = HornerDeg<W>::v;
-  const float s = 2.f * fr - 1.f;
-#pragma unroll
-  for (int t = 0; t < W; ++t) {
-    float a = ht.c[t][D];
-#pragma unroll
-    for (int k = D - 1; k >= 0; --k) a = fmaf(a, s, ht.c[t][k]);
-    wt[t] = a;
-  }
-}
 
 // H: element k of the transformed column at H[prow(k) * CB] (slot-offset pointer).
 template <int W>
@@ -153,139 +93,6 @@ __device__ __forceinline__ float2 cubic_interp(const float2 *H, int CB, ff tau, 
     idx = (idx + 1 == Nt) ? 0 : idx + 1;
   }
   return acc;
-}
-
-struct ColInfo {
-  int jx, jy;
-  bool xnyq, ynyq;
-  int rowA, rowB;  // G1 rows of the two sources (B = the flipped frequency)
-};
-
-__device__ __forceinline__ ColInfo col_info(const InstDesc &d, int jx, int jy) {
-  ColInfo c;
-  c.jx = jx;
-  c.jy = jy;
-  c.xnyq = ((d.Nx & 1) == 0) && (jx == -d.hx);
-  c.ynyq = ((d.Ny & 1) == 0) && (jy == d.hy);
-  c.rowA = (c.ynyq ? -jx : jx) + d.hx;  // conj source when ynyq
-  c.rowB = (c.xnyq ? d.hx : jx) + d.hx;
-  return c;
-}
-
-// Slot of a NER block: one (column, source) transform.  A column on an
-// unpaired Nyquist index has two sources (A, B); transforms whose results add
-// into one output take two adjacent slots, the first (even) one leading.
-struct NerSlot {
-  int kind;   // 0 empty, 1 alone, 2 leads a group of two, 3 second of a group
-  int jx, iy;
-  int src;    // 0: source A, 1: source B
-  int zero_row0;  // adjoint: G1 row jx = -hx of the y-Nyquist row is read by no column
-};
-
-// Forward slots: the one-source columns, (padding to an even count), then the
-// two sources of every Nyquist column (x-Nyquist row ix = 0 for even Nx,
-// y-Nyquist row iy = hy for even Ny).
-__host__ __device__ __forceinline__ int ner_fwd_slots(const InstDesc &d) {
-  const int xe = (d.Nx & 1) == 0, ye = (d.Ny & 1) == 0;
-  const int R = (d.Nx - xe) * (d.nY1 - ye);
-  return R + (R & 1) + 2 * (xe * d.nY1 + ye * (d.Nx - xe));
-}
-__device__ __forceinline__ NerSlot fwd_slot(const InstDesc &d, int v) {
-  NerSlot sl{};
-  const int xe = (d.Nx & 1) == 0, ye = (d.Ny & 1) == 0;
-  const int ry = d.nY1 - ye;
-  const int R = (d.Nx - xe) * ry;
-  if (v < R) {
-    sl.kind = 1;
-    sl.jx = xe + v / ry - d.hx;
-    sl.iy = v % ry;
-    return sl;
-  }
-  const int O1 = R + (R & 1);
-  if (v < O1) return sl;
-  const int k = v - O1;
-  int q = k >> 1;
-  sl.src = k & 1;
-  if (xe) {
-    if (q < d.nY1) {
-      sl.kind = 2 + sl.src;
-      sl.jx = -d.hx;
-      sl.iy = q;
-      return sl;
-    }
-    q -= d.nY1;
-  }
-  if (ye && q < d.Nx - xe) {
-    sl.kind = 2 + sl.src;
-    sl.jx = xe + q - d.hx;
-    sl.iy = d.hy;
-  }
-  return sl;
-}
-
-// Adjoint slots: the one-source columns, (padding), the two sources of the
-// x-Nyquist columns (even Nx, jy < hy; they feed two different G1 rows), then
-// for even Ny the y-Nyquist row, whose G1 rows each take two transforms:
-// row hx from both sources of jx = 0, row 2hx from both sources of the corner
-// jx = -hx (even Nx), and for each g > 0 of a pair {g, -g} row hx - g from
-// (g, A) + (-g, B) and row hx + g from (g, B) + (-g, A).
-__host__ __device__ __forceinline__ int ner_adj_slots(const InstDesc &d) {
-  const int xe = (d.Nx & 1) == 0, ye = (d.Ny & 1) == 0;
-  const int ry = d.nY1 - ye;
-  const int R = (d.Nx - xe) * ry;
-  const int npairs = xe ? d.hx - 1 : d.hx;
-  return R + (R & 1) + 2 * xe * ry + ye * (2 + 2 * xe + 4 * (npairs > 0 ? npairs : 0));
-}
-__device__ __forceinline__ NerSlot adj_slot(const InstDesc &d, int v) {
-  NerSlot sl{};
-  const int xe = (d.Nx & 1) == 0, ye = (d.Ny & 1) == 0;
-  const int ry = d.nY1 - ye, hx = d.hx;
-  const int R = (d.Nx - xe) * ry;
-  if (v < R) {
-    sl.kind = 1;
-    sl.jx = xe + v / ry - hx;
-    sl.iy = v % ry;
-    return sl;
-  }
-  int k = v - (R + (R & 1));
-  if (k < 0) return sl;
-  if (xe) {
-    if (k < 2 * ry) {
-      sl.kind = 1;
-      sl.jx = -hx;
-      sl.iy = k >> 1;
-      sl.src = k & 1;
-      return sl;
-    }
-    k -= 2 * ry;
-  }
-  if (!ye) return sl;
-  sl.iy = d.hy;
-  if (k < 2) {
-    sl.kind = 2 + k;
-    sl.jx = 0;
-    sl.src = k;
-    return sl;
-  }
-  k -= 2;
-  if (xe) {
-    if (k < 2) {
-      sl.kind = 2 + k;
-      sl.jx = -hx;
-      sl.src = k;
-      sl.zero_row0 = k == 0;
-      return sl;
-    }
-    k -= 2;
-  }
-  const int npairs = xe ? hx - 1 : hx;
-  const int p = k >> 2, r = k & 3;
-  if (p >= npairs) return NerSlot{};
-  const int g = 1 + p;
-  sl.kind = 2 + (r & 1);
-  sl.jx = (r == 0 || r == 2) ? g : -g;
-  sl.src = (r == 0 || r == 3) ? 0 : 1;
-  return sl;
 }
 
 // Forward NER: slot b of the block transforms slot tile*CB + b.
@@ -545,6 +352,7 @@ cudaError_t launch_ner(const Launch &L, int width, const HornerTable &ht, bool a
 }
 
 cudaError_t launch_ner_stage(const Launch &L, int width, const HornerTable &ht, int which) {
+  if (L.host && L.host->ner_warp) return launch_ner_warp(L, ht, which);
   switch (width) {
     case 6: return launch_ner_w<6>(L, ht, which);
     case 8: return launch_ner_w<8>(L, ht, which);

@@ -87,6 +87,7 @@ extern "C" int pa_position_grad_noalloc(pa_plan *plan, const float *g_dev, const
 
   pa::Launch L{};
   L.descs = ddesc;
+  L.host = &d;
   L.stream = s;
   L.io.g_in = g_dev;
   L.io.f_in = grad_f_dev;

@@ -694,7 +694,7 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
   if (sigma < 2 || sigma > 4) return fail(PA_ERR_INVALID_ARG, "sigma must be 2, 3 or 4");
   if (!(width == 6 || width == 8 || width == 12 || width == 16))
     return fail(PA_ERR_INVALID_ARG, "width must be 6, 8, 12 or 16");
-  if ((flags & ~PA_FLAG_NO_LATTICE) != 0) return fail(PA_ERR_INVALID_ARG, "unknown flags");
+  if ((flags & ~(PA_FLAG_NO_LATTICE | PA_FLAG_BLOCK_NER)) != 0) return fail(PA_ERR_INVALID_ARG, "unknown flags");
   for (int64_t m = 0; m < 2 * n_sensors; ++m)
     if (!std::isfinite(sensor_xy[m])) return fail(PA_ERR_INVALID_ARG, "non-finite sensor position");
   const double X = grid->nx * grid->dx, Y = grid->ny * grid->dy;
@@ -790,6 +790,23 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
       tw.push_back(make_float2(float(std::cos(a)), float(std::sin(a))));
     }
   }
+  // warp-transform twiddles (FP64, rounded once)
+  h.wtw = int(tw.size());
+  for (int lgn = 8; lgn <= 10; ++lgn) {
+    const int N = 1 << lgn;
+    for (int k2 = 0; k2 < N / 32; ++k2)
+      for (int n1 = 0; n1 < 32; ++n1) {
+        const double a = -2.0 * kPi * double(n1 * k2) / N;
+        tw.push_back(make_float2(float(std::cos(a)), float(std::sin(a))));
+      }
+  }
+  for (int lgm = 9; lgm <= 11; ++lgm) {
+    const int M = 1 << lgm;
+    for (int j = 0; j < M; ++j) {
+      const double a = -2.0 * kPi * double(j) / M;
+      tw.push_back(make_float2(float(std::cos(a)), float(std::sin(a))));
+    }
+  }
   // NER blocks: ner_cb (column, source) transforms side by side, at least
   // two (the two transforms of a Nyquist column share a block); four when
   // their buffers stay within 48 KB
@@ -816,6 +833,9 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
   h.two_c = float(2.0 * c);
   h.scale = float(dt / (grid->dz * double(Nx) * double(Ny) * double(Nz)));
   fit_horner(kb, horner_degree(width), P->ht);
+
+  h.ner_warp = (flags & PA_FLAG_BLOCK_NER) == 0 && pa::ner_warp_eligible(h) &&
+               pa::smem_ner_warp(h) <= P->smem_limit ? 1 : 0;
 
   // shared-memory limits
   const size_t smems[] = {pa::smem_rowfft(h), pa::smem_colfft(h), pa::smem_ner(h),
@@ -1070,8 +1090,9 @@ int pa_plan_autotune(pa_plan *plan, void *stream, int *choice) {
       if (rc != PA_OK) break;
       h.spread_spl = pick;
     }
-    // NER: columns per block and block size (forward + adjoint)
-    {
+    // NER: columns per block and block size (forward + adjoint) of the
+    // block kernels; the warp-per-column kernels have one shape
+    if (!h.ner_warp) {
       float best = 1e30f;
       int pick_cb = h.ner_cb, pick_t = h.ner_threads;
       for (int cb : {2, 4})
@@ -1237,6 +1258,13 @@ int pa_plan_is_lattice(const pa_plan *plan, int *is_lattice) {
   g_err.clear();
   if (!plan || !is_lattice) return fail(PA_ERR_INVALID_ARG, "NULL argument");
   *is_lattice = plan->lattice ? 1 : 0;
+  return PA_OK;
+}
+
+int pa_plan_uses_warp_ner(const pa_plan *plan, int *warp) {
+  g_err.clear();
+  if (!plan || !warp) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  *warp = plan->h.ner_warp ? 1 : 0;
   return PA_OK;
 }
 

@@ -65,7 +65,7 @@ def _create(lib, **kw):
 
 @pytest.mark.parametrize("bad", [
     dict(M=0), dict(xy=None), dict(grid=None), dict(nt=1), dict(dt=0.0), dict(dt=float("nan")),
-    dict(c=-1.0), dict(sigma=1), dict(sigma=5), dict(width=7), dict(width=10), dict(flags=3),
+    dict(c=-1.0), dict(sigma=1), dict(sigma=5), dict(width=7), dict(width=10), dict(flags=4),
     dict(xy=np.array([[0.0, float("nan")]] * 4)), dict(w=np.array([1.0, 1.0, -1.0, 1.0])),
 ])
 def test_invalid_arguments_rejected(lib, bad):
