@@ -5,6 +5,7 @@
 
 #include <cstdint>
 
+#include <cuda.h>
 #include "pa_internal.h"
 
 namespace pa {
@@ -469,6 +470,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
+// Tiled bulk copy of the 3-D box at element coordinates (x, y, z) of a tensor
+// map (a __grid_constant__ kernel parameter) into shared memory, completing
+// on `bar` with the box's full byte count (elements outside the tensor are
+// filled with zeros).  dst 128-byte aligned; x * element size a multiple of 16.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
 // Orders this thread's (and, after a block barrier, the block's) earlier
 // shared-memory accesses before later bulk copies into the same memory.
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -535,6 +547,51 @@ __device__ __forceinline__ bool tile_pipeline(int nwork, float2 *buf0, float2 *b
   return true;
 }
 
+// The same loop with NS buffers: the copies of the next NS - 1 items are in
+// flight while item i is computed in buffer i mod NS (buffer b at
+// buf + b * stride floats2; barrier b at bars[b]).
+template <int NS, typename Issue, typename Compute>
+__device__ __forceinline__ bool tile_pipeline_n(int nwork, float2 *buf, size_t stride, uint64_t *bars, int *status,
+                                                Issue issue, Compute compute) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int b = 0; b < NS; ++b) mbar_init(&bars[b], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int k = 0; k < NS - 1; ++k) {
+    const int w = blockIdx.x + k * gridDim.x;
+    if (w < nwork) issue(w, buf + k * stride, &bars[k]);
+  }
+#pragma unroll 1
+  for (int i = 0;; ++i) {
+    const int w = blockIdx.x + i * gridDim.x;
+    if (w >= nwork) break;
+    const int s = i % NS;
+    const int wn = w + (NS - 1) * gridDim.x;
+    if (wn < nwork) {
+      const int sn = (i + NS - 1) % NS;
+      fence_proxy_async_smem();  // that buffer's last reads precede its refill
+      issue(wn, buf + sn * stride, &bars[sn]);
+    }
+    const uint32_t par = uint32_t(i / NS) & 1u;
+    const bool ok = mbar_wait(&bars[s], par);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(status, kStatusWaitTimeout);
+      // one more bounded wait for every copy still in flight
+      for (int k = 0; k < NS; ++k) {
+        const int wk = w + k * gridDim.x;
+        if (wk < nwork) mbar_wait(&bars[(i + k) % NS], uint32_t((i + k) / NS) & 1u);
+      }
+      return false;
+    }
+    compute(w, buf + s * stride);
+    __syncthreads();
+  }
+  return true;
+}
+
 __device__ __forceinline__ void block_work(const int2 *__restrict__ work, int &inst, int &tile) {
   if (work) {
     int2 w = work[blockIdx.x];
@@ -583,6 +640,18 @@ static cudaError_t launch_persistent(K kernel, const Launch &L, int threads, siz
   const int grid = persistent_grid(kernel, threads, smem, nwork);
   kernel<<<grid, threads, smem, L.stream>>>(L.descs, nwork);
   return cudaGetLastError();
+}
+
+// Opt-in shared memory per block of the current device (read once).
+static inline size_t smem_optin_limit() {
+  static int v = -1;
+  if (v < 0) {
+    int dev = 0, x = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&x, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    v = x;
+  }
+  return size_t(v);
 }
 
 static inline int pow2_log(int n) {

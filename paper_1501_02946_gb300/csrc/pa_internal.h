@@ -59,6 +59,11 @@ struct InstDesc {
   const float *wx, *wy; // [M][w]; wy carries a_m = h_m/(dx dy)
   const float *dwx, *dwy;  // [M][w] derivative taps d/dx_m and d/dy_m
   const int *cell_start;   // [Mx*My + 1] CSR offsets of the sorted sensors per cell
+  // per sorted sensor, for the interpolation tiles: ipack[i] holds
+  // wx[0..w), wy[0..w), by, m (as int bits) in ipack_words(w) floats;
+  // ipack_d[i] holds dwx[0..w), dwy[0..w) in ipackd_words(w) floats
+  const float4 *ipack;
+  const float4 *ipack_d;
   // forward spread entries: strip s (kSpreadP grid rows p0 = s*kSpreadP ..)
   // and column q own the entries sp_start[s*My + q] .. sp_start[s*My + q + 1]-1;
   // entry e is a sensor (caller index sp_m[e]) with its tap products
@@ -100,6 +105,10 @@ struct InstDesc {
 __host__ __device__ constexpr int wtw_T(int lgn) { return lgn == 8 ? 0 : (lgn == 9 ? 256 : 768); }
 __host__ __device__ constexpr int wtw_F(int lgm) { return lgm == 9 ? 1792 : (lgm == 10 ? 2304 : 3328); }
 constexpr int kWtwSize = 5376;
+
+// Floats per sensor of the interpolation packs (multiples of 4: 16-byte rows).
+__host__ __device__ constexpr int ipack_words(int w) { return ((2 * w + 2 + 3) / 4) * 4; }
+__host__ __device__ constexpr int ipackd_words(int w) { return ((2 * w + 3) / 4) * 4; }
 
 // Caller buffers of one call (device pointers).  Single-plan launches pass
 // them by value; batched launches pass a device table indexed by instance.
@@ -169,6 +178,8 @@ cudaError_t launch_imgy(const Launch &L, bool adjoint);
 cudaError_t launch_interp_width(const Launch &L, int width, bool grad, int ty);
 cudaError_t launch_rowifft(const Launch &L);
 cudaError_t launch_grad_reduce(const Launch &L, int M);
+// Rewrite ipack / ipack_d from perm, sby, wx, wy, dwx, dwy (after a sensor upload).
+cudaError_t build_interp_pack(const InstDesc &h, cudaStream_t s);
 
 // Device re-binning of new sensor positions (pa_rebin.cu): inputs, the plan
 // tables it rewrites and its scratch.

@@ -10,6 +10,10 @@
 // FFT back to the G0 cotangent) and k_interp (interpolation at the sensors,
 // optionally with the sensor-position gradient through the window
 // derivative).
+#include <cstring>
+
+#include <cudaTypedefs.h>
+
 #include "pa_device.cuh"
 
 namespace pa {
@@ -627,6 +631,226 @@ __global__ void __launch_bounds__(kThreadsInterp) k_interp(const InstDesc *__res
   }
 }
 
+// The same interpolation as a persistent kernel for single-plan launches with
+// Nt % 4 == 0: tiles w = blockIdx.x, blockIdx.x + gridDim.x, ... through two
+// shared-memory buffers, the copies of tile w + 1 in flight while tile w is
+// computed.  A tile whose halo lies inside the grid arrives as one 3-D box of
+// the tensor map g0map (dims Nt, My, Mx; box 32 x HY x HX) when use_map is
+// set; tiles at the periodic edges take one bulk copy per cell.  With the
+// grid, the packs (taps, column, caller index) of the tile's first SMAX
+// sensors arrive by bulk copies of the rows' contiguous sorted ranges, so
+// the interpolation reads only shared memory.  A group of 8 lanes takes one
+// sensor at a time, lane l8 the 4 samples n0 + 4 l8 .. + 3 (16-byte shared
+// loads, 128-byte output rows): a warp interpolates 4 sensors at once.
+template <int W, int TY, bool GRAD, int NSTAGE>
+struct InterpPipe {
+  static constexpr int TX = 8, NC = 32;
+  static constexpr int HX = TX + W - 1, HY = TY + W - 1, CELLS = HX * HY;
+  static constexpr int SMAX = TX * TY;  // packed sensors per tile
+  static constexpr int PW = ipack_words(W), PD = GRAD ? ipackd_words(W) : 0;
+  // floats per buffer, rounded to 128 bytes
+  static constexpr int BUF = ((CELLS * NC + SMAX * (PW + PD)) + 31) / 32 * 32;
+  static constexpr int NS = NSTAGE;      // pipeline stages (buffers)
+  static constexpr int THREADS = 256;
+  static constexpr size_t smem = size_t(NS * BUF) * sizeof(float) + 128;
+};
+
+template <int W, int TY, bool GRAD, int NS>
+__global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS) k_interp_pipe(const InstDesc *__restrict__ descs, IoPtrs io,
+                                                                int nwork, const __grid_constant__ CUtensorMap g0map,
+                                                                int use_map) {
+  using S = InterpPipe<W, TY, GRAD, NS>;
+  constexpr int TX = S::TX, HX = S::HX, HY = S::HY, NC = S::NC, CELLS = S::CELLS, SMAX = S::SMAX;
+  constexpr int PW = S::PW, PD = S::PD;
+  extern __shared__ float4 smem_f4[];
+  // box destinations 128-byte aligned (the launch adds 128 bytes of slack)
+  float *base = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_f4) + 127) & ~uintptr_t(127));
+  float2 *buf0 = reinterpret_cast<float2 *>(base);
+  __shared__ __align__(8) uint64_t bars[S::NS];
+  __shared__ int rlo[S::NS][TX], rpre[S::NS][TX + 1];
+  const InstDesc &d = descs[0];
+  const int Mx = d.Mx, My = d.My, Nt = d.Nt, M = d.M;
+  const int ntx = (Mx + TX - 1) / TX;
+  const int nchunks = (Nt + NC - 1) / NC;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int lane = tid & 31, l8 = tid & 7, grp = tid >> 3, ngrp = nthr >> 3;
+  const unsigned gmask = 0xffu << (lane & 24);
+  const float *G0 = d.G0;
+  auto decode = [&](int w, int &p0, int &q0, int &n0) {
+    p0 = ((w / nchunks) % ntx) * TX;
+    q0 = (w / (nchunks * ntx)) * TY;
+    n0 = (w % nchunks) * NC;
+  };
+  auto issue = [&](int w, float2 *buf, uint64_t *bar) {
+    int p0, q0, n0;
+    decode(w, p0, q0, n0);
+    const int par = int((reinterpret_cast<float *>(buf) - base) / S::BUF);
+    float *Gs = reinterpret_cast<float *>(buf);
+    float *packs = Gs + CELLS * NC, *packd = packs + SMAX * PW;
+    const int ps = p0 - W / 2 + 1, qs = q0 - W / 2 + 1;
+    const bool box = use_map && ps >= 0 && ps + HX <= Mx && qs >= 0 && qs + HY <= My;
+    uint32_t pack_bytes = 0;
+    if (tid < 32) {
+      // rows r < TX of the tile: sorted ranges, their prefix, and the packs
+      int lo = 0, cnt = 0;
+      if (lane < TX && p0 + lane < Mx) {
+        const size_t row = (size_t)(p0 + lane) * My;
+        lo = __ldg(d.cell_start + row + q0);
+        cnt = __ldg(d.cell_start + row + min(q0 + TY, My)) - lo;
+      }
+      int inc = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+      }
+      const int pre = inc - cnt, total = __shfl_sync(0xffffffffu, inc, TX - 1);
+      if (lane < TX) {
+        rlo[par][lane] = lo;
+        rpre[par][lane] = pre;
+        const int k = min(cnt, SMAX - pre);
+        if (k > 0) {
+          bulk_g2s(packs + pre * PW, d.ipack + (size_t)lo * (PW / 4), uint32_t(k * PW * 4), bar);
+          if (GRAD) bulk_g2s(packd + pre * PD, d.ipack_d + (size_t)lo * (PD / 4), uint32_t(k * PD * 4), bar);
+        }
+      }
+      if (lane == 0) rpre[par][TX] = total;
+      pack_bytes = uint32_t(min(total, SMAX) * (PW + PD) * 4);
+    }
+    if (box) {
+      if (tid == 0) {
+        mbar_arrive_expect_tx(bar, uint32_t(CELLS * NC * sizeof(float)) + pack_bytes);
+        tma_load_3d(Gs, &g0map, n0, qs, ps, bar);
+      }
+      return;
+    }
+    const uint32_t rb = uint32_t(min(NC, Nt - n0)) * sizeof(float);
+    if (tid == 0) mbar_arrive_expect_tx(bar, rb * CELLS + pack_bytes);
+    for (int cell = tid; cell < CELLS; cell += nthr) {
+      const int hr = cell / HY, hc = cell - hr * HY;
+      const int p = wrap(ps + hr, Mx), q = wrap(qs + hc, My);
+      bulk_g2s(Gs + cell * NC, G0 + ((size_t)p * My + q) * Nt + n0, rb, bar);
+    }
+  };
+  auto compute = [&](int w, float2 *buf) {
+    int p0, q0, n0;
+    decode(w, p0, q0, n0);
+    const int par = int((reinterpret_cast<float *>(buf) - base) / S::BUF);
+    const float *Gs = reinterpret_cast<const float *>(buf);
+    const float *packs = Gs + CELLS * NC, *packd = packs + SMAX * PW;
+    const int total = rpre[par][TX];
+    const int n = n0 + 4 * l8;
+    const int c = n0 / NC;
+#pragma unroll 1
+    for (int u = grp; u < total; u += ngrp) {
+      int r = 0;
+      while (r + 1 < TX && rpre[par][r + 1] <= u) ++r;
+      const int i = rlo[par][r] + (u - rpre[par][r]);
+      float pk[PW], pkd[PD > 0 ? PD : 1];
+      const float4 *src = u < SMAX ? reinterpret_cast<const float4 *>(packs + u * PW) : d.ipack + (size_t)i * (PW / 4);
+#pragma unroll
+      for (int k = 0; k < PW / 4; ++k) {
+        const float4 v = src[k];
+        pk[4 * k] = v.x;
+        pk[4 * k + 1] = v.y;
+        pk[4 * k + 2] = v.z;
+        pk[4 * k + 3] = v.w;
+      }
+      if (GRAD) {
+        const float4 *srcd =
+            u < SMAX ? reinterpret_cast<const float4 *>(packd + u * PD) : d.ipack_d + (size_t)i * (PD / 4);
+#pragma unroll
+        for (int k = 0; k < PD / 4; ++k) {
+          const float4 v = srcd[k];
+          pkd[4 * k] = v.x;
+          pkd[4 * k + 1] = v.y;
+          pkd[4 * k + 2] = v.z;
+          pkd[4 * k + 3] = v.w;
+        }
+      }
+      const int hr0 = r, hc0 = __float_as_int(pk[2 * W]) - q0;
+      const int m = __float_as_int(pk[2 * W + 1]);
+      float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (GRAD && n < Nt) gv = __ldg(reinterpret_cast<const float4 *>(io.g_in + (size_t)m * Nt + n));
+      float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), ax = a0, ay = a0;
+#pragma unroll
+      for (int rr = 0; rr < W; ++rr) {
+        const float4 *row = reinterpret_cast<const float4 *>(Gs + ((size_t)(hr0 + rr) * HY + hc0) * NC) + l8;
+        float4 rs = make_float4(0.f, 0.f, 0.f, 0.f), rsy = rs;
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+          const float4 v = row[t * (NC / 4)];
+          const float wy = pk[W + t];
+          rs.x = fmaf(wy, v.x, rs.x);
+          rs.y = fmaf(wy, v.y, rs.y);
+          rs.z = fmaf(wy, v.z, rs.z);
+          rs.w = fmaf(wy, v.w, rs.w);
+          if (GRAD) {
+            const float dwy = pkd[W + t];
+            rsy.x = fmaf(dwy, v.x, rsy.x);
+            rsy.y = fmaf(dwy, v.y, rsy.y);
+            rsy.z = fmaf(dwy, v.z, rsy.z);
+            rsy.w = fmaf(dwy, v.w, rsy.w);
+          }
+        }
+        const float wx = pk[rr];
+        a0.x = fmaf(wx, rs.x, a0.x);
+        a0.y = fmaf(wx, rs.y, a0.y);
+        a0.z = fmaf(wx, rs.z, a0.z);
+        a0.w = fmaf(wx, rs.w, a0.w);
+        if (GRAD) {
+          const float dwx = pkd[rr];
+          ax.x = fmaf(dwx, rs.x, ax.x);
+          ax.y = fmaf(dwx, rs.y, ax.y);
+          ax.z = fmaf(dwx, rs.z, ax.z);
+          ax.w = fmaf(dwx, rs.w, ax.w);
+          ay.x = fmaf(wx, rsy.x, ay.x);
+          ay.y = fmaf(wx, rsy.y, ay.y);
+          ay.z = fmaf(wx, rsy.z, ay.z);
+          ay.w = fmaf(wx, rsy.w, ay.w);
+        }
+      }
+      // Nt % 4 == 0: the 4 samples of a lane are all below Nt or all past it
+      if (io.g_out && n < Nt) *reinterpret_cast<float4 *>(io.g_out + (size_t)m * Nt + n) = a0;
+      if (GRAD) {
+        float px = 0.f, py = 0.f;
+        if (n < Nt) {
+          px = ax.x * gv.x + ax.y * gv.y + ax.z * gv.z + ax.w * gv.w;
+          py = ay.x * gv.x + ay.y * gv.y + ay.z * gv.z + ay.w * gv.w;
+        }
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1) {
+          px += __shfl_xor_sync(gmask, px, off);
+          py += __shfl_xor_sync(gmask, py, off);
+        }
+        if (l8 == 0) d.grad_part[(size_t)c * M + i] = make_float2(px, py);
+      }
+    }
+  };
+  tile_pipeline_n<S::NS>(nwork, buf0, S::BUF / 2, bars, d.status, issue, compute);
+}
+
+// ipack[i] = (wx[i][0..w), wy[i][0..w), sby[i], perm[i]); ipack_d[i] = (dwx, dwy)
+__global__ void k_build_ipack(const InstDesc *__restrict__ dummy, int M, int w, const int *__restrict__ perm,
+                              const int *__restrict__ sby, const float *__restrict__ wx, const float *__restrict__ wy,
+                              const float *__restrict__ dwx, const float *__restrict__ dwy, float *pk, float *pkd) {
+  (void)dummy;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const int PW = ipack_words(w), PD = ipackd_words(w);
+  float *o = pk + (size_t)i * PW, *od = pkd + (size_t)i * PD;
+  for (int t = 0; t < w; ++t) {
+    o[t] = wx[(size_t)i * w + t];
+    o[w + t] = wy[(size_t)i * w + t];
+    od[t] = dwx[(size_t)i * w + t];
+    od[w + t] = dwy[(size_t)i * w + t];
+  }
+  o[2 * w] = __int_as_float(sby[i]);
+  o[2 * w + 1] = __int_as_float(perm[i]);
+  for (int k = 2 * w + 2; k < PW; ++k) o[k] = 0.f;
+  for (int k = 2 * w; k < PD; ++k) od[k] = 0.f;
+}
+
 // Sum the per-chunk gradient partials and scatter to the caller's order.
 __global__ void k_grad_reduce(const InstDesc *__restrict__ descs, IoPtrs io0, const IoPtrs *__restrict__ io_table,
                               int inst_count) {
@@ -663,7 +887,7 @@ size_t smem_rowfft(const InstDesc &d) { return (size_t)d.My * kRowFftNCP * sizeo
 int blocks_colfft(const InstDesc &d) { return d.nY1 * ((d.Nt + kColNC - 1) / kColNC); }
 size_t smem_colfft(const InstDesc &d) { return (size_t)d.Mx * kColNC * sizeof(float2); }
 constexpr int kRowIfftNCP = 16;
-constexpr int kInterpTX = 8, kInterpTY = 32;
+constexpr int kInterpTX = 8;
 int interp_ty(const InstDesc &d) { return d.interp_ty; }
 int blocks_rowifft(const InstDesc &d) { return d.Mx * ((d.Nt + 2 * kRowIfftNCP - 1) / (2 * kRowIfftNCP)); }
 size_t smem_rowifft(const InstDesc &d) { return (size_t)d.My * kRowIfftNCP * sizeof(float2); }
@@ -745,8 +969,66 @@ cudaError_t launch_colfft(const Launch &L, bool adjoint) {
   return cudaGetLastError();
 }
 
+// Tensor map of the real grid G0 [Mx][My][Nt] (float) with box
+// 32 x hy x hx (samples, columns, rows) for the interpolation tiles, through
+// the driver's encoder (looked up once).  False (with the map zeroed) if the
+// encoder or the layout is not available.
+static bool encode_g0_box(const InstDesc &h, int hx, int hy, CUtensorMap *map) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static bool looked = false;
+  std::memset(map, 0, sizeof(*map));
+  if (!looked) {
+    looked = true;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  if (!encode || (h.Nt % 4) != 0 || hx > 256 || hy > 256 || (reinterpret_cast<uintptr_t>(h.G0) & 15u)) return false;
+  const cuuint64_t dims[3] = {cuuint64_t(h.Nt), cuuint64_t(h.My), cuuint64_t(h.Mx)};
+  const cuuint64_t strides[2] = {cuuint64_t(h.Nt) * sizeof(float), cuuint64_t(h.My) * h.Nt * sizeof(float)};
+  const cuuint32_t box[3] = {32u, cuuint32_t(hy), cuuint32_t(hx)};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h.G0, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    std::memset(map, 0, sizeof(*map));
+    return false;
+  }
+  return true;
+}
+
+// The pipelined kernel with NS stages, if its buffers fit (else false).
+template <int W, int TY, bool GRAD, int NS>
+static bool launch_interp_pipe(const Launch &L, cudaError_t &err) {
+  using IP = InterpPipe<W, TY, GRAD, NS>;
+  if (IP::smem > smem_optin_limit()) return false;
+  const InstDesc &h = *L.host;
+  auto kp = k_interp_pipe<W, TY, GRAD, NS>;
+  err = set_smem(kp, IP::smem);
+  if (err != cudaSuccess) return true;
+  CUtensorMap map;
+  const int use_map = encode_g0_box(h, IP::HX, IP::HY, &map) ? 1 : 0;
+  const int nwork = blocks_interp(h);
+  const int grid = persistent_grid(kp, IP::THREADS, IP::smem, nwork);
+  kp<<<grid, IP::THREADS, IP::smem, L.stream>>>(L.descs, L.io, nwork, map, use_map);
+  err = cudaGetLastError();
+  return true;
+}
+
 template <int W, int TY, bool GRAD>
 static cudaError_t launch_interp_w(const Launch &L) {
+  // single-plan launches with 16-byte sample rows take the pipelined kernel
+  // (two stages, two blocks per SM measured fastest; wider windows keep the
+  // per-cell kernel: their unrolled tap loops would not stay in registers)
+  if constexpr (W <= 8) {
+    if (L.host && !L.work && (L.host->Nt % 4) == 0) {
+      cudaError_t e = cudaSuccess;
+      if (launch_interp_pipe<W, TY, GRAD, 2>(L, e)) return e;
+    }
+  }
   auto kern = k_interp<W, kInterpTX, TY, GRAD>;
   cudaError_t e = set_smem(kern, L.smem);
   if (e != cudaSuccess) return e;
@@ -788,6 +1070,14 @@ cudaError_t launch_rowifft(const Launch &L) {
   cudaError_t e = set_smem(kern, L.smem);
   if (e != cudaSuccess) return e;
   kern<<<L.nblocks, kThreadsCol, L.smem, L.stream>>>(L.descs, L.work);
+  return cudaGetLastError();
+}
+
+cudaError_t build_interp_pack(const InstDesc &h, cudaStream_t s) {
+  if (h.M <= 0) return cudaSuccess;
+  k_build_ipack<<<(h.M + 255) / 256, 256, 0, s>>>(nullptr, h.M, h.w, h.perm, h.sby, h.wx, h.wy, h.dwx, h.dwy,
+                                                  reinterpret_cast<float *>(const_cast<float4 *>(h.ipack)),
+                                                  reinterpret_cast<float *>(const_cast<float4 *>(h.ipack_d)));
   return cudaGetLastError();
 }
 

@@ -302,6 +302,7 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
   PA_CUDA(cudaMemcpyAsync((void *)P->h.dwy, dwy.data(), sizeof(float) * dwy.size(), cudaMemcpyHostToDevice, stream));
   PA_CUDA(cudaMemcpyAsync((void *)P->h.cell_start, cs.data(), sizeof(int) * cs.size(), cudaMemcpyHostToDevice,
                           stream));
+  PA_CUDA(pa::build_interp_pack(P->h, stream));
 
   // Forward-spread entries.  Strip st covers grid rows p0 = st*P .. p0+P-1;
   // a sensor contributes to (st, q) for each column q of its w-column
@@ -858,6 +859,8 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
   const size_t o_wx = take(sizeof(float) * M * W), o_wy = take(sizeof(float) * M * W);
   const size_t o_dwx = take(sizeof(float) * M * W), o_dwy = take(sizeof(float) * M * W);
   const size_t o_cs = take(sizeof(int) * (size_t(Mx) * My + 1));
+  const size_t o_ipk = take(sizeof(float) * M * pa::ipack_words(width));
+  const size_t o_ipkd = take(sizeof(float) * M * pa::ipackd_words(width));
   const size_t o_ipx = take(sizeof(float) * ipx.size()), o_ipy = take(sizeof(float) * ipy.size());
   const size_t o_ipt = take(sizeof(float) * ipt.size());
   const size_t o_tw = take(sizeof(float2) * tw.size());
@@ -892,6 +895,8 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
   h.dwx = reinterpret_cast<const float *>(S + o_dwx);
   h.dwy = reinterpret_cast<const float *>(S + o_dwy);
   h.cell_start = reinterpret_cast<const int *>(S + o_cs);
+  h.ipack = reinterpret_cast<const float4 *>(S + o_ipk);
+  h.ipack_d = reinterpret_cast<const float4 *>(S + o_ipkd);
   h.invphx = reinterpret_cast<const float *>(S + o_ipx);
   h.invphy = reinterpret_cast<const float *>(S + o_ipy);
   h.invpht = reinterpret_cast<const float *>(S + o_ipt);
@@ -1000,6 +1005,7 @@ int pa_plan_update_positions_device(pa_plan *plan, const float *xy_dev, void *st
   int st0 = 0;
   PA_CUDA(cudaMemcpyAsync(&st0, h.status, sizeof(int), cudaMemcpyDeviceToHost, s));
   PA_CUDA(pa::rebin_sensors(a, s));
+  PA_CUDA(pa::build_interp_pack(h, s));
   PA_CUDA(pa::rebin_count_entries(a, s));
   int nent = 0, st1 = 0;
   PA_CUDA(cudaMemcpyAsync(&nent, a.sp_cnt + nkeys, sizeof(int), cudaMemcpyDeviceToHost, s));
