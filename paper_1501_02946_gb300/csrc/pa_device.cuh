@@ -481,6 +481,14 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
       : "memory");
 }
+// 2-D form: the box at (x, y).
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
 // Orders this thread's (and, after a block barrier, the block's) earlier
 // shared-memory accesses before later bulk copies into the same memory.
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -652,6 +660,19 @@ static inline size_t smem_optin_limit() {
     v = x;
   }
   return size_t(v);
+}
+
+// launch_persistent for kernels that also take a tensor map and its flag.
+template <typename K>
+static cudaError_t launch_persistent_map(K kernel, const Launch &L, int threads, size_t smem, int nwork,
+                                         const CUtensorMap &map, int use_map) {
+  if (smem > 40 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = persistent_grid(kernel, threads, smem, nwork);
+  kernel<<<grid, threads, smem, L.stream>>>(L.descs, nwork, map, use_map);
+  return cudaGetLastError();
 }
 
 static inline int pow2_log(int n) {

@@ -333,12 +333,16 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft_pipe(const InstDesc *__r
 
 // Persistent, double-buffered row FFT (k_rowfft) for My = 2^LGL and
 // Nt % 4 == 0 (one plan).
+// With use_map, a tile arrives as boxes of the 2-D tensor map over G0
+// (dims Nt, Mx My; box 32 x min(My, 256)) instead of one copy per row q.
 template <int LGL>
-__global__ void __launch_bounds__(kThreadsCol) k_rowfft_pipe(const InstDesc *__restrict__ descs, int nwork) {
+__global__ void __launch_bounds__(kThreadsCol) k_rowfft_pipe(const InstDesc *__restrict__ descs, int nwork,
+                                                             const __grid_constant__ CUtensorMap map, int use_map) {
   extern __shared__ float4 smem_f4[];
   __shared__ __align__(8) uint64_t bars[2];
-  constexpr int L = 1 << LGL, NCP = 16, LGNCP = 4;
-  float2 *buf0 = reinterpret_cast<float2 *>(smem_f4);  // [My][NCP] sample pairs
+  constexpr int L = 1 << LGL, NCP = 16, LGNCP = 4, BOX = L < 256 ? L : 256;
+  // [My][NCP] sample pairs; box destinations 128-byte aligned (128 bytes of slack)
+  float2 *buf0 = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(smem_f4) + 127) & ~uintptr_t(127));
   float2 *buf1 = buf0 + L * NCP;
   const InstDesc &d = descs[0];
   const int Nt = d.Nt, nY1 = d.nY1;
@@ -347,6 +351,13 @@ __global__ void __launch_bounds__(kThreadsCol) k_rowfft_pipe(const InstDesc *__r
   const float2 *tw = d.tw + d.fMy.tw;
   auto issue = [&](int w, float2 *buf, uint64_t *bar) {
     const int p = w / nchunks, n0 = (w - p * nchunks) * 2 * NCP;
+    if (use_map) {
+      if (tid == 0) {
+        mbar_arrive_expect_tx(bar, uint32_t(L * 2 * NCP * sizeof(float)));
+        for (int b = 0; b < L; b += BOX) tma_load_2d(buf + b * NCP, &map, n0, p * L + b, bar);
+      }
+      return;
+    }
     const uint32_t rb = uint32_t(min(2 * NCP, Nt - n0)) * sizeof(float);
     if (tid == 0) mbar_arrive_expect_tx(bar, rb * L);
     const float *G0 = d.G0 + (size_t)p * L * Nt + n0;
@@ -433,21 +444,32 @@ __global__ void __launch_bounds__(kThreadsCol) k_rowifft(const InstDesc *__restr
 // Persistent, double-buffered k_rowifft for My = 2^LGL and Nt % 4 == 0 (one
 // plan): the T rows of the next tile land in a staging buffer by bulk copies
 // while the current spectrum is built, transformed and written.
+// With use_map (nY1 <= 256), the staged rows arrive as one box of the 2-D
+// tensor map over T (floats; dims 2 Nt, Mx nY1; box 64 x nY1).
 template <int LGL>
-__global__ void __launch_bounds__(kThreadsCol) k_rowifft_pipe(const InstDesc *__restrict__ descs, int nwork) {
+__global__ void __launch_bounds__(kThreadsCol) k_rowifft_pipe(const InstDesc *__restrict__ descs, int nwork,
+                                                              const __grid_constant__ CUtensorMap map, int use_map) {
   extern __shared__ float4 smem_f4[];
   __shared__ __align__(8) uint64_t bars[2];
   constexpr int L = 1 << LGL, NCP = 16, LGNCP = 4;
   const InstDesc &d = descs[0];
   const int Nt = d.Nt, nY1 = d.nY1;
-  float2 *S = reinterpret_cast<float2 *>(smem_f4);  // [My][NCP] packed spectrum
-  float2 *st0 = S + L * NCP;                        // [nY1][2 NCP] staged T rows
-  float2 *st1 = st0 + nY1 * 2 * NCP;
+  // staging buffers first (box destinations 128-byte aligned; 128 bytes of slack)
+  float2 *st0 = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(smem_f4) + 127) & ~uintptr_t(127));
+  float2 *st1 = st0 + ((nY1 * 2 * NCP + 15) & ~15);  // [nY1][2 NCP] staged T rows
+  float2 *S = st1 + ((nY1 * 2 * NCP + 15) & ~15);    // [My][NCP] packed spectrum
   const int nchunks = (Nt + 2 * NCP - 1) / (2 * NCP);
   const int tid = threadIdx.x, nthr = blockDim.x, lgT = ilog2_pow2(nthr);
   const float2 *tw = d.tw + d.fMy.tw;
   auto issue = [&](int w, float2 *stg, uint64_t *bar) {
     const int p = w / nchunks, n0 = (w - p * nchunks) * 2 * NCP;
+    if (use_map) {
+      if (tid == 0) {
+        mbar_arrive_expect_tx(bar, uint32_t(nY1 * 2 * NCP * sizeof(float2)));
+        tma_load_2d(stg, &map, 2 * n0, p * nY1, bar);
+      }
+      return;
+    }
     const uint32_t rb = uint32_t(min(2 * NCP, Nt - n0)) * sizeof(float2);
     if (tid == 0) mbar_arrive_expect_tx(bar, rb * nY1);
     const float2 *Trow = d.T + (size_t)p * nY1 * Nt + n0;
@@ -919,15 +941,75 @@ cudaError_t launch_spread(const Launch &L, int spl) {
 // The persistent kernels are instantiated for lengths 2^5 .. 2^9 (two tile
 // buffers of at most 128 KB).
 
+// Tensor map of the real grid G0 [Mx][My][Nt] (float) with box
+// 32 x hy x hx (samples, columns, rows) for the interpolation tiles, through
+// the driver's encoder (looked up once).  False (with the map zeroed) if the
+// encoder or the layout is not available.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  return encode;
+}
+
+// 2-D float map: rows of `inner` floats, `outer` rows, row pitch in bytes;
+// box bx x by.  False (map zeroed) when unavailable.
+static bool encode_2d(const void *base, uint64_t inner, uint64_t outer, uint64_t pitch, uint32_t bx, uint32_t by,
+                      CUtensorMap *map) {
+  std::memset(map, 0, sizeof(*map));
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode || (reinterpret_cast<uintptr_t>(base) & 15u) || (pitch & 15u) || bx > 256 || by > 256) return false;
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {pitch};
+  const cuuint32_t box[2] = {bx, by};
+  const cuuint32_t estr[2] = {1u, 1u};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    std::memset(map, 0, sizeof(*map));
+    return false;
+  }
+  return true;
+}
+
+static bool encode_g0_box(const InstDesc &h, int hx, int hy, CUtensorMap *map) {
+  std::memset(map, 0, sizeof(*map));
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode || (h.Nt % 4) != 0 || hx > 256 || hy > 256 || (reinterpret_cast<uintptr_t>(h.G0) & 15u)) return false;
+  const cuuint64_t dims[3] = {cuuint64_t(h.Nt), cuuint64_t(h.My), cuuint64_t(h.Mx)};
+  const cuuint64_t strides[2] = {cuuint64_t(h.Nt) * sizeof(float), cuuint64_t(h.My) * h.Nt * sizeof(float)};
+  const cuuint32_t box[3] = {32u, cuuint32_t(hy), cuuint32_t(hx)};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h.G0, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    std::memset(map, 0, sizeof(*map));
+    return false;
+  }
+  return true;
+}
+
 cudaError_t launch_rowfft(const Launch &L) {
   if (L.host && !L.work && (L.host->Nt % 4) == 0) {
     const InstDesc &h = *L.host;
     const int lg = pow2_log(h.My);
     const int nwork = h.Mx * ((h.Nt + 31) / 32);
-    const size_t smem = 2 * size_t(h.My) * 16 * sizeof(float2);
+    const size_t smem = 2 * size_t(h.My) * 16 * sizeof(float2) + 128;
+    CUtensorMap map;
+    const int use_map = encode_2d(h.G0, uint64_t(h.Nt), uint64_t(h.Mx) * h.My, uint64_t(h.Nt) * sizeof(float), 32u,
+                                  uint32_t(h.My < 256 ? h.My : 256), &map) ? 1 : 0;
     switch (lg) {
 #define PA_ROWFFT_CASE(G) \
-  case G: return launch_persistent(k_rowfft_pipe<G>, L, kThreadsCol, smem, nwork);
+  case G: return launch_persistent_map(k_rowfft_pipe<G>, L, kThreadsCol, smem, nwork, map, use_map);
       PA_ROWFFT_CASE(5) PA_ROWFFT_CASE(6) PA_ROWFFT_CASE(7) PA_ROWFFT_CASE(8) PA_ROWFFT_CASE(9)
 #undef PA_ROWFFT_CASE
       default: break;
@@ -967,37 +1049,6 @@ cudaError_t launch_colfft(const Launch &L, bool adjoint) {
     k_colfft<false><<<L.nblocks, kThreadsCol, L.smem, L.stream>>>(L.descs, L.work);
   }
   return cudaGetLastError();
-}
-
-// Tensor map of the real grid G0 [Mx][My][Nt] (float) with box
-// 32 x hy x hx (samples, columns, rows) for the interpolation tiles, through
-// the driver's encoder (looked up once).  False (with the map zeroed) if the
-// encoder or the layout is not available.
-static bool encode_g0_box(const InstDesc &h, int hx, int hy, CUtensorMap *map) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  static bool looked = false;
-  std::memset(map, 0, sizeof(*map));
-  if (!looked) {
-    looked = true;
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
-  if (!encode || (h.Nt % 4) != 0 || hx > 256 || hy > 256 || (reinterpret_cast<uintptr_t>(h.G0) & 15u)) return false;
-  const cuuint64_t dims[3] = {cuuint64_t(h.Nt), cuuint64_t(h.My), cuuint64_t(h.Mx)};
-  const cuuint64_t strides[2] = {cuuint64_t(h.Nt) * sizeof(float), cuuint64_t(h.My) * h.Nt * sizeof(float)};
-  const cuuint32_t box[3] = {32u, cuuint32_t(hy), cuuint32_t(hx)};
-  const cuuint32_t estr[3] = {1u, 1u, 1u};
-  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h.G0, dims, strides, box, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    std::memset(map, 0, sizeof(*map));
-    return false;
-  }
-  return true;
 }
 
 // The pipelined kernel with NS stages, if its buffers fit (else false).
@@ -1057,10 +1108,15 @@ cudaError_t launch_rowifft(const Launch &L) {
     const InstDesc &h = *L.host;
     const int lg = pow2_log(h.My);
     const int nwork = h.Mx * ((h.Nt + 31) / 32);
-    const size_t smem = (size_t(h.My) * 16 + 2 * size_t(h.nY1) * 32) * sizeof(float2);
+    const size_t stage = size_t((h.nY1 * 32 + 15) & ~15);
+    const size_t smem = (size_t(h.My) * 16 + 2 * stage) * sizeof(float2) + 128;
+    CUtensorMap map;
+    // one box per tile: the staging rows hold exactly nY1 rows
+    const int use_map = h.nY1 <= 256 && encode_2d(h.T, 2 * uint64_t(h.Nt), uint64_t(h.Mx) * h.nY1,
+                                                  uint64_t(h.Nt) * sizeof(float2), 64u, uint32_t(h.nY1), &map) ? 1 : 0;
     switch (lg) {
 #define PA_ROWIFFT_CASE(G) \
-  case G: return launch_persistent(k_rowifft_pipe<G>, L, kThreadsCol, smem, nwork);
+  case G: return launch_persistent_map(k_rowifft_pipe<G>, L, kThreadsCol, smem, nwork, map, use_map);
       PA_ROWIFFT_CASE(5) PA_ROWIFFT_CASE(6) PA_ROWIFFT_CASE(7) PA_ROWIFFT_CASE(8) PA_ROWIFFT_CASE(9)
 #undef PA_ROWIFFT_CASE
       default: break;
