@@ -277,13 +277,20 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft(const InstDesc *__restri
 // Persistent, double-buffered column FFT for Mx = 2^LGL and even Nt (one
 // plan): the rows of the next tile arrive by bulk copies (TMA engine) while
 // the current tile is transformed.  Same arithmetic as k_colfft.
+// With use_map the rows arrive as boxes of a 3-D tensor map (floats): over T
+// (dims 2 Nt, nY1, Mx; box 32 x 1 x min(Mx, 256)) forward, over G1 (dims
+// 2 Nt, nY1, nX1; box 32 x 1 x (hx + 1)) for the adjoint, whose two boxes
+// start at rows hx and -1 (the row before 0 reads as zeros and lands on a
+// bin that is cleared anyway).
 template <bool ADJ, int LGL>
-__global__ void __launch_bounds__(kThreadsCol) k_colfft_pipe(const InstDesc *__restrict__ descs, int nwork) {
+__global__ void __launch_bounds__(kThreadsCol) k_colfft_pipe(const InstDesc *__restrict__ descs, int nwork,
+                                                             const __grid_constant__ CUtensorMap map, int use_map) {
   extern __shared__ float4 smem_f4[];
   __shared__ __align__(8) uint64_t bars[2];
-  constexpr int L = 1 << LGL, NC = kColNC, LGNC = 4;
+  constexpr int L = 1 << LGL, NC = kColNC, LGNC = 4, BOX = L < 256 ? L : 256;
   static_assert(NC == 1 << LGNC, "tile width");
-  float2 *buf0 = reinterpret_cast<float2 *>(smem_f4);
+  // box destinations 128-byte aligned (the launch adds 128 bytes of slack)
+  float2 *buf0 = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(smem_f4) + 127) & ~uintptr_t(127));
   float2 *buf1 = buf0 + L * NC;
   const InstDesc &d = descs[0];
   const int Nt = d.Nt, nY1 = d.nY1, nX1 = d.nX1, hx = d.hx;
@@ -292,6 +299,19 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft_pipe(const InstDesc *__r
   const float2 *tw = d.tw + d.fMx.tw;
   auto issue = [&](int w, float2 *buf, uint64_t *bar) {
     const int jy = w / nchunks, n0 = (w - jy * nchunks) * NC;
+    if (use_map) {
+      if (tid == 0) {
+        if (!ADJ) {
+          mbar_arrive_expect_tx(bar, uint32_t(L * NC * sizeof(float2)));
+          for (int b = 0; b < L; b += BOX) tma_load_3d(buf + b * NC, &map, 2 * n0, jy, b, bar);
+        } else {
+          mbar_arrive_expect_tx(bar, uint32_t(2 * (hx + 1) * NC * sizeof(float2)));
+          tma_load_3d(buf, &map, 2 * n0, jy, hx, bar);                       // ix = hx .. 2 hx
+          tma_load_3d(buf + (L - hx - 1) * NC, &map, 2 * n0, jy, -1, bar);  // ix = -1 .. hx - 1
+        }
+      }
+      return;
+    }
     const uint32_t rb = uint32_t(min(NC, Nt - n0)) * sizeof(float2);
     if (!ADJ) {
       if (tid == 0) mbar_arrive_expect_tx(bar, rb * L);
@@ -980,6 +1000,28 @@ static bool encode_2d(const void *base, uint64_t inner, uint64_t outer, uint64_t
   return true;
 }
 
+// 3-D float map: dims d0 (contiguous), d1, d2 with byte pitches p1, p2; box b0 x b1 x b2.
+static int encode_3d(const void *base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t p1, uint64_t p2, uint32_t b0,
+                     uint32_t b1, uint32_t b2, CUtensorMap *map) {
+  std::memset(map, 0, sizeof(*map));
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode || (reinterpret_cast<uintptr_t>(base) & 15u) || (p1 & 15u) || (p2 & 15u) || b0 > 256 || b1 > 256 ||
+      b2 > 256)
+    return 0;
+  const cuuint64_t dims[3] = {d0, d1, d2};
+  const cuuint64_t strides[2] = {p1, p2};
+  const cuuint32_t box[3] = {b0, b1, b2};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    std::memset(map, 0, sizeof(*map));
+    return 0;
+  }
+  return 1;
+}
+
 static bool encode_g0_box(const InstDesc &h, int hx, int hy, CUtensorMap *map) {
   std::memset(map, 0, sizeof(*map));
   PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
@@ -1027,12 +1069,23 @@ cudaError_t launch_colfft(const Launch &L, bool adjoint) {
     const InstDesc &h = *L.host;
     const int lg = pow2_log(h.Mx);
     const int nwork = h.nY1 * ((h.Nt + kColNC - 1) / kColNC);
-    const size_t smem = 2 * size_t(h.Mx) * kColNC * sizeof(float2);
+    const size_t smem = 2 * size_t(h.Mx) * kColNC * sizeof(float2) + 128;
+    CUtensorMap map;
+    int use_map = 0;
+    if (!adjoint) {
+      use_map = encode_3d(h.T, 2 * uint64_t(h.Nt), uint64_t(h.nY1), uint64_t(h.Mx), uint64_t(h.Nt) * sizeof(float2),
+                          uint64_t(h.nY1) * h.Nt * sizeof(float2), 32u, 1u, uint32_t(h.Mx < 256 ? h.Mx : 256), &map);
+    } else if (h.hx + 1 <= 256 && 2 * h.hx + 1 < h.Mx) {
+      use_map = encode_3d(h.G1, 2 * uint64_t(h.Nt), uint64_t(h.nY1), uint64_t(h.nX1), uint64_t(h.Nt) * sizeof(float2),
+                          uint64_t(h.nY1) * h.Nt * sizeof(float2), 32u, 1u, uint32_t(h.hx + 1), &map);
+    } else {
+      std::memset(&map, 0, sizeof(map));
+    }
     switch (lg) {
-#define PA_COLFFT_CASE(G)                                                                   \
-  case G:                                                                                   \
-    return adjoint ? launch_persistent(k_colfft_pipe<true, G>, L, kThreadsCol, smem, nwork)  \
-                   : launch_persistent(k_colfft_pipe<false, G>, L, kThreadsCol, smem, nwork);
+#define PA_COLFFT_CASE(G)                                                                                      \
+  case G:                                                                                                      \
+    return adjoint ? launch_persistent_map(k_colfft_pipe<true, G>, L, kThreadsCol, smem, nwork, map, use_map)  \
+                   : launch_persistent_map(k_colfft_pipe<false, G>, L, kThreadsCol, smem, nwork, map, use_map);
       PA_COLFFT_CASE(5) PA_COLFFT_CASE(6) PA_COLFFT_CASE(7) PA_COLFFT_CASE(8) PA_COLFFT_CASE(9)
 #undef PA_COLFFT_CASE
       default: break;
