@@ -10,6 +10,7 @@
 //           even-length Nyquist bin once, each through its real part.
 // Both keep depth innermost, so every global access is a contiguous run.
 #include "pa_device.cuh"
+#include "pa_tmap.h"
 
 namespace pa {
 
@@ -152,13 +153,18 @@ __global__ void __launch_bounds__(kThreadsImg) k_imgy(const InstDesc *__restrict
 // Persistent, double-buffered k_imgx for Nx = 2^LGL and even Nz (one plan):
 // the rows of the next tile arrive by bulk copies (TMA engine) while the
 // current tile is transformed.
+// With use_map, a tile arrives as two boxes of the 3-D tensor map over the
+// source (floats; dims 2 Nz, nY1, Nx; box 32 x 1 x Nx/2): rows a >= hx to
+// buffer rows 0.., rows a < hx to buffer rows Nx - hx.. (hx = Nx/2).
 template <bool ADJ, int LGL>
-__global__ void __launch_bounds__(kThreadsImg) k_imgx_pipe(const InstDesc *__restrict__ descs, int nwork) {
+__global__ void __launch_bounds__(kThreadsImg) k_imgx_pipe(const InstDesc *__restrict__ descs, int nwork,
+                                                           const __grid_constant__ CUtensorMap map, int use_map) {
   extern __shared__ float4 smem_f4[];
   __shared__ __align__(8) uint64_t bars[2];
   constexpr int L = 1 << LGL, ZC = kImgZC, LGZC = 4;
   static_assert(ZC == 1 << LGZC, "tile width");
-  float2 *buf0 = reinterpret_cast<float2 *>(smem_f4);
+  // box destinations 128-byte aligned (the launch adds 128 bytes of slack)
+  float2 *buf0 = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(smem_f4) + 127) & ~uintptr_t(127));
   float2 *buf1 = buf0 + L * ZC;
   const InstDesc &d = descs[0];
   const int Nz = d.Nz, nY1 = d.nY1, hx = d.hx;
@@ -169,6 +175,14 @@ __global__ void __launch_bounds__(kThreadsImg) k_imgx_pipe(const InstDesc *__res
   float2 *dst = ADJ ? d.Fz : d.U;
   auto issue = [&](int w, float2 *buf, uint64_t *bar) {
     const int iy = w / nzc, z0 = (w - iy * nzc) * ZC;
+    if (use_map) {
+      if (tid == 0) {
+        mbar_arrive_expect_tx(bar, uint32_t(L * ZC * sizeof(float2)));
+        tma_load_3d(buf, &map, 2 * z0, iy, L / 2, bar);
+        tma_load_3d(buf + (L / 2) * ZC, &map, 2 * z0, iy, 0, bar);
+      }
+      return;
+    }
     const uint32_t rb = uint32_t(min(ZC, Nz - z0)) * sizeof(float2);
     if (tid == 0) mbar_arrive_expect_tx(bar, rb * L);
     for (int a = tid; a < L; a += nthr)
@@ -189,8 +203,13 @@ __global__ void __launch_bounds__(kThreadsImg) k_imgx_pipe(const InstDesc *__res
 // Persistent, double-buffered k_imgy for Ny = 2^LGL and Nz % 4 == 0 (one
 // plan).  Forward: the half-spectrum rows U[x][jy] land in a staging buffer;
 // adjoint: the image rows f[x][y] land directly as depth pairs.
+// With use_map, forward staging rows arrive as one box of the 2-D map over U
+// (floats; dims 2 Nz, Nx nY1; box 64 x nY1), adjoint image rows as two boxes
+// of the 2-D map over f_in (dims Nz, Nx Ny; box 32 x Ny/2), rows y >= hy to
+// buffer rows 0.., rows y < hy to buffer rows Ny - hy.. (hy = Ny/2).
 template <bool ADJ, int LGL>
-__global__ void __launch_bounds__(kThreadsImg) k_imgy_pipe(const InstDesc *__restrict__ descs, int nwork, IoPtrs io) {
+__global__ void __launch_bounds__(kThreadsImg) k_imgy_pipe(const InstDesc *__restrict__ descs, int nwork, IoPtrs io,
+                                                           const __grid_constant__ CUtensorMap map, int use_map) {
   extern __shared__ float4 smem_f4[];
   __shared__ __align__(8) uint64_t bars[2];
   constexpr int L = 1 << LGL, ZP = kImgZP, LGZP = 4;
@@ -201,13 +220,29 @@ __global__ void __launch_bounds__(kThreadsImg) k_imgy_pipe(const InstDesc *__res
   const int nzc = (Nz + 2 * ZP - 1) / (2 * ZP);
   const int tid = threadIdx.x, nthr = blockDim.x, lgT = ilog2_pow2(nthr);
   const float2 *tw = d.tw + d.fNy.tw;
-  float2 *B = reinterpret_cast<float2 *>(smem_f4);  // [Ny][ZP] depth pairs
-  // forward: two staging buffers [nY1][2 ZP]; adjoint: two tile buffers [Ny][ZP]
+  // box destinations 128-byte aligned (the launch adds 128 bytes of slack)
+  float2 *B = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(smem_f4) + 127) & ~uintptr_t(127));
+  // [Ny][ZP] depth pairs; forward: two staging buffers [nY1][2 ZP] (rounded
+  // to 128 bytes); adjoint: two tile buffers [Ny][ZP]
+  const int stage = (nY1 * 2 * ZP + 15) & ~15;
   float2 *b0 = ADJ ? B : B + L * ZP;
-  float2 *b1 = ADJ ? B + L * ZP : b0 + nY1 * 2 * ZP;
+  float2 *b1 = ADJ ? B + L * ZP : b0 + stage;
   auto issue = [&](int w, float2 *buf, uint64_t *bar) {
     const int x = w / nzc, z0 = (w - x * nzc) * 2 * ZP;
     const int nz = min(2 * ZP, Nz - z0);
+    if (use_map) {
+      if (tid == 0) {
+        if (!ADJ) {
+          mbar_arrive_expect_tx(bar, uint32_t(nY1 * 2 * ZP * sizeof(float2)));
+          tma_load_2d(buf, &map, 2 * z0, x * nY1, bar);
+        } else {
+          mbar_arrive_expect_tx(bar, uint32_t(L * ZP * sizeof(float2)));
+          tma_load_2d(buf, &map, z0, x * L + L / 2, bar);
+          tma_load_2d(buf + (L / 2) * ZP, &map, z0, x * L, bar);
+        }
+      }
+      return;
+    }
     if (!ADJ) {
       const uint32_t rb = uint32_t(nz) * sizeof(float2);
       if (tid == 0) mbar_arrive_expect_tx(bar, rb * nY1);
@@ -286,12 +321,18 @@ cudaError_t launch_imgx(const Launch &L, bool adjoint) {
   if (L.host && !L.work && (L.host->Nz % 2) == 0) {
     const InstDesc &h = *L.host;
     const int nwork = h.nY1 * ((h.Nz + kImgZC - 1) / kImgZC);
-    const size_t smem = 2 * size_t(h.Nx) * kImgZC * sizeof(float2);
+    const size_t smem = 2 * size_t(h.Nx) * kImgZC * sizeof(float2) + 128;
+    CUtensorMap map;
+    const int use_map = h.Nx / 2 <= 256 && encode_3d(adjoint ? (const void *)h.U : (const void *)h.Fz,
+                                                     2 * uint64_t(h.Nz), uint64_t(h.nY1), uint64_t(h.Nx),
+                                                     uint64_t(h.Nz) * sizeof(float2),
+                                                     uint64_t(h.nY1) * h.Nz * sizeof(float2), 32u, 1u,
+                                                     uint32_t(h.Nx / 2), &map);
     switch (pow2_log(h.Nx)) {
-#define PA_IMGX_CASE(G)                                                                        \
-  case G:                                                                                      \
-    return adjoint ? launch_persistent(k_imgx_pipe<true, G>, L, kThreadsImg, smem, nwork)      \
-                   : launch_persistent(k_imgx_pipe<false, G>, L, kThreadsImg, smem, nwork);
+#define PA_IMGX_CASE(G)                                                                                    \
+  case G:                                                                                                  \
+    return adjoint ? launch_persistent_map(k_imgx_pipe<true, G>, L, kThreadsImg, smem, nwork, map, use_map)  \
+                   : launch_persistent_map(k_imgx_pipe<false, G>, L, kThreadsImg, smem, nwork, map, use_map);
       PA_IMGX_CASE(5) PA_IMGX_CASE(6) PA_IMGX_CASE(7) PA_IMGX_CASE(8) PA_IMGX_CASE(9)
 #undef PA_IMGX_CASE
       default: break;
@@ -311,13 +352,14 @@ cudaError_t launch_imgx(const Launch &L, bool adjoint) {
 }
 
 template <typename K>
-static cudaError_t launch_persistent_io(K kernel, const Launch &L, size_t smem, int nwork) {
+static cudaError_t launch_persistent_io(K kernel, const Launch &L, size_t smem, int nwork, const CUtensorMap &map,
+                                        int use_map) {
   if (smem > 40 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
   }
   const int grid = persistent_grid(kernel, kThreadsImg, smem, nwork);
-  kernel<<<grid, kThreadsImg, smem, L.stream>>>(L.descs, nwork, L.io);
+  kernel<<<grid, kThreadsImg, smem, L.stream>>>(L.descs, nwork, L.io, map, use_map);
   return cudaGetLastError();
 }
 
@@ -325,13 +367,23 @@ cudaError_t launch_imgy(const Launch &L, bool adjoint) {
   if (L.host && !L.work && (L.host->Nz % 4) == 0) {
     const InstDesc &h = *L.host;
     const int nwork = h.Nx * ((h.Nz + 2 * kImgZP - 1) / (2 * kImgZP));
-    const size_t smem = adjoint ? 2 * size_t(h.Ny) * kImgZP * sizeof(float2)
-                                : (size_t(h.Ny) * kImgZP + 2 * size_t(h.nY1) * 2 * kImgZP) * sizeof(float2);
+    const size_t stage = size_t((h.nY1 * 2 * kImgZP + 15) & ~15);
+    const size_t smem = (adjoint ? 2 * size_t(h.Ny) * kImgZP : size_t(h.Ny) * kImgZP + 2 * stage) * sizeof(float2) + 128;
+    CUtensorMap map;
+    int use_map = 0;
+    if (!adjoint) {
+      use_map = h.nY1 <= 256 && encode_2d(h.U, 2 * uint64_t(h.Nz), uint64_t(h.Nx) * h.nY1,
+                                          uint64_t(h.Nz) * sizeof(float2), 2u * 2 * kImgZP, uint32_t(h.nY1), &map);
+    } else {
+      use_map = h.Ny / 2 <= 256 && L.io.f_in &&
+                encode_2d(L.io.f_in, uint64_t(h.Nz), uint64_t(h.Nx) * h.Ny, uint64_t(h.Nz) * sizeof(float),
+                          2u * kImgZP, uint32_t(h.Ny / 2), &map);
+    }
     switch (pow2_log(h.Ny)) {
-#define PA_IMGY_CASE(G)                                                                  \
-  case G:                                                                                \
-    return adjoint ? launch_persistent_io(k_imgy_pipe<true, G>, L, smem, nwork)         \
-                   : launch_persistent_io(k_imgy_pipe<false, G>, L, smem, nwork);
+#define PA_IMGY_CASE(G)                                                                       \
+  case G:                                                                                     \
+    return adjoint ? launch_persistent_io(k_imgy_pipe<true, G>, L, smem, nwork, map, use_map) \
+                   : launch_persistent_io(k_imgy_pipe<false, G>, L, smem, nwork, map, use_map);
       PA_IMGY_CASE(5) PA_IMGY_CASE(6) PA_IMGY_CASE(7) PA_IMGY_CASE(8) PA_IMGY_CASE(9)
 #undef PA_IMGY_CASE
       default: break;
