@@ -269,6 +269,15 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
+    if args.profile_step:
+        # one forward + adjoint between cudaProfilerStart/Stop, for
+        # `ncu --profile-from-start off`; no timing line
+        torch.cuda.profiler.start()
+        step()
+        torch.cuda.synchronize(dev)
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profiled": "one forward + adjoint step", "launch_shapes": shapes}))
+        return 0
     plan.profile(True)
     plan.profile_read()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -488,6 +497,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", action="store_true", help="time the uneven 64-instance batch instead")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run one step between cudaProfilerStart/Stop (for ncu --profile-from-start off) and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -509,6 +509,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 }
 // Status-word bit recorded by a kernel whose bounded wait ran out.
 constexpr int kStatusWaitTimeout = 1;
+// Status-word bit: a kernel found its dynamic shared memory less than
+// 128-byte aligned (what its tensor copies need) and did no work.
+constexpr int kStatusSmemAlign = 4;
+__device__ __forceinline__ bool smem_aligned_128(const void *p, int *status) {
+  if ((smem_addr(p) & 127u) == 0) return true;
+  if (threadIdx.x == 0) atomicOr(status, kStatusSmemAlign);
+  return false;
+}
 
 // Persistent loop over the work items w = blockIdx.x, blockIdx.x + gridDim.x,
 // ... with two tile buffers: while item i is computed in one buffer, the bulk

@@ -159,14 +159,14 @@ __global__ void __launch_bounds__(kThreadsImg) k_imgy(const InstDesc *__restrict
 template <bool ADJ, int LGL>
 __global__ void __launch_bounds__(kThreadsImg) k_imgx_pipe(const InstDesc *__restrict__ descs, int nwork,
                                                            const __grid_constant__ CUtensorMap map, int use_map) {
-  extern __shared__ float4 smem_f4[];
+  extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
   __shared__ __align__(8) uint64_t bars[2];
   constexpr int L = 1 << LGL, ZC = kImgZC, LGZC = 4;
   static_assert(ZC == 1 << LGZC, "tile width");
-  // box destinations 128-byte aligned (the launch adds 128 bytes of slack)
-  float2 *buf0 = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(smem_f4) + 127) & ~uintptr_t(127));
+  float2 *buf0 = reinterpret_cast<float2 *>(smem_a128);
   float2 *buf1 = buf0 + L * ZC;
   const InstDesc &d = descs[0];
+  if (!smem_aligned_128(smem_a128, d.status)) return;
   const int Nz = d.Nz, nY1 = d.nY1, hx = d.hx;
   const int nzc = (Nz + ZC - 1) / ZC;
   const int tid = threadIdx.x, nthr = blockDim.x, lgT = ilog2_pow2(nthr);
@@ -210,18 +210,18 @@ __global__ void __launch_bounds__(kThreadsImg) k_imgx_pipe(const InstDesc *__res
 template <bool ADJ, int LGL>
 __global__ void __launch_bounds__(kThreadsImg) k_imgy_pipe(const InstDesc *__restrict__ descs, int nwork, IoPtrs io,
                                                            const __grid_constant__ CUtensorMap map, int use_map) {
-  extern __shared__ float4 smem_f4[];
+  extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
   __shared__ __align__(8) uint64_t bars[2];
   constexpr int L = 1 << LGL, ZP = kImgZP, LGZP = 4;
   static_assert(ZP == 1 << LGZP, "tile width");
   const InstDesc &d = descs[0];
+  if (!smem_aligned_128(smem_a128, d.status)) return;
   const int Nz = d.Nz, nY1 = d.nY1, hy = d.hy;
   const bool ny_even = (L & 1) == 0;
   const int nzc = (Nz + 2 * ZP - 1) / (2 * ZP);
   const int tid = threadIdx.x, nthr = blockDim.x, lgT = ilog2_pow2(nthr);
   const float2 *tw = d.tw + d.fNy.tw;
-  // box destinations 128-byte aligned (the launch adds 128 bytes of slack)
-  float2 *B = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(smem_f4) + 127) & ~uintptr_t(127));
+  float2 *B = reinterpret_cast<float2 *>(smem_a128);
   // [Ny][ZP] depth pairs; forward: two staging buffers [nY1][2 ZP] (rounded
   // to 128 bytes); adjoint: two tile buffers [Ny][ZP]
   const int stage = (nY1 * 2 * ZP + 15) & ~15;
@@ -321,7 +321,7 @@ cudaError_t launch_imgx(const Launch &L, bool adjoint) {
   if (L.host && !L.work && (L.host->Nz % 2) == 0) {
     const InstDesc &h = *L.host;
     const int nwork = h.nY1 * ((h.Nz + kImgZC - 1) / kImgZC);
-    const size_t smem = 2 * size_t(h.Nx) * kImgZC * sizeof(float2) + 128;
+    const size_t smem = 2 * size_t(h.Nx) * kImgZC * sizeof(float2);
     CUtensorMap map;
     const int use_map = h.Nx / 2 <= 256 && encode_3d(adjoint ? (const void *)h.U : (const void *)h.Fz,
                                                      2 * uint64_t(h.Nz), uint64_t(h.nY1), uint64_t(h.Nx),
@@ -368,7 +368,7 @@ cudaError_t launch_imgy(const Launch &L, bool adjoint) {
     const InstDesc &h = *L.host;
     const int nwork = h.Nx * ((h.Nz + 2 * kImgZP - 1) / (2 * kImgZP));
     const size_t stage = size_t((h.nY1 * 2 * kImgZP + 15) & ~15);
-    const size_t smem = (adjoint ? 2 * size_t(h.Ny) * kImgZP : size_t(h.Ny) * kImgZP + 2 * stage) * sizeof(float2) + 128;
+    const size_t smem = (adjoint ? 2 * size_t(h.Ny) * kImgZP : size_t(h.Ny) * kImgZP + 2 * stage) * sizeof(float2);
     CUtensorMap map;
     int use_map = 0;
     if (!adjoint) {

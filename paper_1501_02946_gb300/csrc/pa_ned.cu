@@ -284,14 +284,14 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft(const InstDesc *__restri
 template <bool ADJ, int LGL>
 __global__ void __launch_bounds__(kThreadsCol) k_colfft_pipe(const InstDesc *__restrict__ descs, int nwork,
                                                              const __grid_constant__ CUtensorMap map, int use_map) {
-  extern __shared__ float4 smem_f4[];
+  extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
   __shared__ __align__(8) uint64_t bars[2];
   constexpr int L = 1 << LGL, NC = kColNC, LGNC = 4, BOX = L < 256 ? L : 256;
   static_assert(NC == 1 << LGNC, "tile width");
-  // box destinations 128-byte aligned (the launch adds 128 bytes of slack)
-  float2 *buf0 = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(smem_f4) + 127) & ~uintptr_t(127));
+  float2 *buf0 = reinterpret_cast<float2 *>(smem_a128);
   float2 *buf1 = buf0 + L * NC;
   const InstDesc &d = descs[0];
+  if (!smem_aligned_128(smem_a128, d.status)) return;
   const int Nt = d.Nt, nY1 = d.nY1, nX1 = d.nX1, hx = d.hx;
   const int nchunks = (Nt + NC - 1) / NC;
   const int tid = threadIdx.x, nthr = blockDim.x, lgT = ilog2_pow2(nthr);
@@ -357,13 +357,13 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft_pipe(const InstDesc *__r
 template <int LGL>
 __global__ void __launch_bounds__(kThreadsCol) k_rowfft_pipe(const InstDesc *__restrict__ descs, int nwork,
                                                              const __grid_constant__ CUtensorMap map, int use_map) {
-  extern __shared__ float4 smem_f4[];
+  extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
   __shared__ __align__(8) uint64_t bars[2];
   constexpr int L = 1 << LGL, NCP = 16, LGNCP = 4, BOX = L < 256 ? L : 256;
-  // [My][NCP] sample pairs; box destinations 128-byte aligned (128 bytes of slack)
-  float2 *buf0 = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(smem_f4) + 127) & ~uintptr_t(127));
+  float2 *buf0 = reinterpret_cast<float2 *>(smem_a128);  // [My][NCP] sample pairs
   float2 *buf1 = buf0 + L * NCP;
   const InstDesc &d = descs[0];
+  if (!smem_aligned_128(smem_a128, d.status)) return;
   const int Nt = d.Nt, nY1 = d.nY1;
   const int nchunks = (Nt + 2 * NCP - 1) / (2 * NCP);
   const int tid = threadIdx.x, nthr = blockDim.x, lgT = ilog2_pow2(nthr);
@@ -468,13 +468,14 @@ __global__ void __launch_bounds__(kThreadsCol) k_rowifft(const InstDesc *__restr
 template <int LGL>
 __global__ void __launch_bounds__(kThreadsCol) k_rowifft_pipe(const InstDesc *__restrict__ descs, int nwork,
                                                               const __grid_constant__ CUtensorMap map, int use_map) {
-  extern __shared__ float4 smem_f4[];
+  extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
   __shared__ __align__(8) uint64_t bars[2];
   constexpr int L = 1 << LGL, NCP = 16, LGNCP = 4;
   const InstDesc &d = descs[0];
+  if (!smem_aligned_128(smem_a128, d.status)) return;
   const int Nt = d.Nt, nY1 = d.nY1;
-  // staging buffers first (box destinations 128-byte aligned; 128 bytes of slack)
-  float2 *st0 = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(smem_f4) + 127) & ~uintptr_t(127));
+  // staging buffers first
+  float2 *st0 = reinterpret_cast<float2 *>(smem_a128);
   float2 *st1 = st0 + ((nY1 * 2 * NCP + 15) & ~15);  // [nY1][2 NCP] staged T rows
   float2 *S = st1 + ((nY1 * 2 * NCP + 15) & ~15);    // [My][NCP] packed spectrum
   const int nchunks = (Nt + 2 * NCP - 1) / (2 * NCP);
@@ -693,7 +694,7 @@ struct InterpPipe {
   static constexpr int BUF = ((CELLS * NC + SMAX * (PW + PD)) + 31) / 32 * 32;
   static constexpr int NS = NSTAGE;      // pipeline stages (buffers)
   static constexpr int THREADS = 256;
-  static constexpr size_t smem = size_t(NS * BUF) * sizeof(float) + 128;
+  static constexpr size_t smem = size_t(NS * BUF) * sizeof(float);
 };
 
 template <int W, int TY, bool GRAD, int NS>
@@ -703,13 +704,13 @@ __global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS) k_interp
   using S = InterpPipe<W, TY, GRAD, NS>;
   constexpr int TX = S::TX, HX = S::HX, HY = S::HY, NC = S::NC, CELLS = S::CELLS, SMAX = S::SMAX;
   constexpr int PW = S::PW, PD = S::PD;
-  extern __shared__ float4 smem_f4[];
-  // box destinations 128-byte aligned (the launch adds 128 bytes of slack)
-  float *base = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_f4) + 127) & ~uintptr_t(127));
+  extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
+  float *base = reinterpret_cast<float *>(smem_a128);
   float2 *buf0 = reinterpret_cast<float2 *>(base);
   __shared__ __align__(8) uint64_t bars[S::NS];
   __shared__ int rlo[S::NS][TX], rpre[S::NS][TX + 1];
   const InstDesc &d = descs[0];
+  if (!smem_aligned_128(smem_a128, d.status)) return;
   const int Mx = d.Mx, My = d.My, Nt = d.Nt, M = d.M;
   const int ntx = (Mx + TX - 1) / TX;
   const int nchunks = (Nt + NC - 1) / NC;
@@ -788,25 +789,27 @@ __global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS) k_interp
       while (r + 1 < TX && rpre[par][r + 1] <= u) ++r;
       const int i = rlo[par][r] + (u - rpre[par][r]);
       float pk[PW], pkd[PD > 0 ? PD : 1];
-      const float4 *src = u < SMAX ? reinterpret_cast<const float4 *>(packs + u * PW) : d.ipack + (size_t)i * (PW / 4);
+      // shared-memory packs, or (past SMAX sensors) the global ones: two
+      // separate loops keep the shared loads in the shared address space
+      auto unpack = [](float *dst, float4 v) {
+        dst[0] = v.x;
+        dst[1] = v.y;
+        dst[2] = v.z;
+        dst[3] = v.w;
+      };
+      if (u < SMAX) {
 #pragma unroll
-      for (int k = 0; k < PW / 4; ++k) {
-        const float4 v = src[k];
-        pk[4 * k] = v.x;
-        pk[4 * k + 1] = v.y;
-        pk[4 * k + 2] = v.z;
-        pk[4 * k + 3] = v.w;
-      }
-      if (GRAD) {
-        const float4 *srcd =
-            u < SMAX ? reinterpret_cast<const float4 *>(packd + u * PD) : d.ipack_d + (size_t)i * (PD / 4);
+        for (int k = 0; k < PW / 4; ++k) unpack(pk + 4 * k, reinterpret_cast<const float4 *>(packs + u * PW)[k]);
+        if (GRAD) {
 #pragma unroll
-        for (int k = 0; k < PD / 4; ++k) {
-          const float4 v = srcd[k];
-          pkd[4 * k] = v.x;
-          pkd[4 * k + 1] = v.y;
-          pkd[4 * k + 2] = v.z;
-          pkd[4 * k + 3] = v.w;
+          for (int k = 0; k < PD / 4; ++k) unpack(pkd + 4 * k, reinterpret_cast<const float4 *>(packd + u * PD)[k]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < PW / 4; ++k) unpack(pk + 4 * k, __ldg(d.ipack + (size_t)i * (PW / 4) + k));
+        if (GRAD) {
+#pragma unroll
+          for (int k = 0; k < PD / 4; ++k) unpack(pkd + 4 * k, __ldg(d.ipack_d + (size_t)i * (PD / 4) + k));
         }
       }
       const int hr0 = r, hc0 = __float_as_int(pk[2 * W]) - q0;
@@ -987,7 +990,7 @@ cudaError_t launch_rowfft(const Launch &L) {
     const InstDesc &h = *L.host;
     const int lg = pow2_log(h.My);
     const int nwork = h.Mx * ((h.Nt + 31) / 32);
-    const size_t smem = 2 * size_t(h.My) * 16 * sizeof(float2) + 128;
+    const size_t smem = 2 * size_t(h.My) * 16 * sizeof(float2);
     CUtensorMap map;
     const int use_map = encode_2d(h.G0, uint64_t(h.Nt), uint64_t(h.Mx) * h.My, uint64_t(h.Nt) * sizeof(float), 32u,
                                   uint32_t(h.My < 256 ? h.My : 256), &map) ? 1 : 0;
@@ -1011,7 +1014,7 @@ cudaError_t launch_colfft(const Launch &L, bool adjoint) {
     const InstDesc &h = *L.host;
     const int lg = pow2_log(h.Mx);
     const int nwork = h.nY1 * ((h.Nt + kColNC - 1) / kColNC);
-    const size_t smem = 2 * size_t(h.Mx) * kColNC * sizeof(float2) + 128;
+    const size_t smem = 2 * size_t(h.Mx) * kColNC * sizeof(float2);
     CUtensorMap map;
     int use_map = 0;
     if (!adjoint) {
@@ -1104,7 +1107,7 @@ cudaError_t launch_rowifft(const Launch &L) {
     const int lg = pow2_log(h.My);
     const int nwork = h.Mx * ((h.Nt + 31) / 32);
     const size_t stage = size_t((h.nY1 * 32 + 15) & ~15);
-    const size_t smem = (size_t(h.My) * 16 + 2 * stage) * sizeof(float2) + 128;
+    const size_t smem = (size_t(h.My) * 16 + 2 * stage) * sizeof(float2);
     CUtensorMap map;
     // one box per tile: the staging rows hold exactly nY1 rows
     const int use_map = h.nY1 <= 256 && encode_2d(h.T, 2 * uint64_t(h.Nt), uint64_t(h.Mx) * h.nY1,
