@@ -497,26 +497,24 @@ __global__ void __launch_bounds__(kThreadsCol) k_rowifft_pipe(const InstDesc *__
   };
   auto compute = [&](int w, float2 *stg) {
     const int p = w / nchunks, n0 = (w - p * nchunks) * 2 * NCP;
-    // bins jy and My - jy from the staged rows; the rest of S is zero
-    for (int idx = tid; idx < L * NCP; idx += nthr) {
-      const int q = idx >> LGNCP, kk = idx & (NCP - 1);
-      const int jy = q <= L / 2 ? q : L - q;
-      float2 v = make_float2(0.f, 0.f);
-      if (jy < nY1) {
-        const int n = n0 + 2 * kk;
-        const float sc = __ldg(d.invphy + jy);
-        const float2 a = n < Nt ? cscale(stg[jy * 2 * NCP + 2 * kk], sc) : make_float2(0.f, 0.f);
-        const float2 b = n + 1 < Nt ? cscale(stg[jy * 2 * NCP + 2 * kk + 1], sc) : make_float2(0.f, 0.f);
-        if (q == 0 || 2 * q == L) {  // bins that are their own mirror
-          v = make_float2(a.x, b.x);
-        } else if (q == jy) {
-          v = make_float2(0.5f * (a.x - b.y), 0.5f * (a.y + b.x));
-        } else {
-          v = make_float2(0.5f * (a.x + b.y), 0.5f * (b.x - a.y));
-        }
+    // bins jy and My - jy from the staged rows (one item reads a sample pair
+    // and fills both); the bins nY1 .. My - nY1, which no jy reaches, are zero
+    for (int idx = tid; idx < nY1 * NCP; idx += nthr) {
+      const int jy = idx >> LGNCP, kk = idx & (NCP - 1);
+      const int n = n0 + 2 * kk;
+      const float sc = __ldg(d.invphy + jy);
+      const float4 ab = *reinterpret_cast<const float4 *>(stg + jy * 2 * NCP + 2 * kk);
+      const float2 a = n < Nt ? make_float2(sc * ab.x, sc * ab.y) : make_float2(0.f, 0.f);
+      const float2 b = n + 1 < Nt ? make_float2(sc * ab.z, sc * ab.w) : make_float2(0.f, 0.f);
+      if (jy == 0 || 2 * jy == L) {  // bins that are their own mirror
+        S[jy * NCP + kk] = make_float2(a.x, b.x);
+      } else {
+        S[jy * NCP + kk] = make_float2(0.5f * (a.x - b.y), 0.5f * (a.y + b.x));
+        S[(L - jy) * NCP + kk] = make_float2(0.5f * (a.x + b.y), 0.5f * (b.x - a.y));
       }
-      S[idx] = v;
     }
+    for (int idx = tid; idx < (L - 2 * nY1 + 1) * (NCP / 2); idx += nthr)
+      reinterpret_cast<float4 *>(S + nY1 * NCP)[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     fft_fixed<LGL, +1>(S, NCP, LGNCP, lgT, tw, tid);
     float *G0 = d.G0 + (size_t)p * L * Nt + n0;
@@ -723,6 +721,22 @@ __global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS) k_interp
     q0 = (w / (nchunks * ntx)) * TY;
     n0 = (w % nchunks) * NC;
   };
+  // sorted range of row `lane` of tile w (warp 0, lanes < TX); the ranges of
+  // the tile issued next are loaded one issue ahead, so their latency hides
+  // behind a compute phase
+  auto row_range = [&](int w, int &lo, int &hi) {
+    lo = hi = 0;
+    if (w < nwork && lane < TX) {
+      int p0, q0, n0;
+      decode(w, p0, q0, n0);
+      if (p0 + lane < Mx) {
+        const size_t row = (size_t)(p0 + lane) * My;
+        lo = __ldg(d.cell_start + row + q0);
+        hi = __ldg(d.cell_start + row + min(q0 + TY, My));
+      }
+    }
+  };
+  int pf_w = -1, pf_lo = 0, pf_hi = 0;
   auto issue = [&](int w, float2 *buf, uint64_t *bar) {
     int p0, q0, n0;
     decode(w, p0, q0, n0);
@@ -734,12 +748,16 @@ __global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS) k_interp
     uint32_t pack_bytes = 0;
     if (tid < 32) {
       // rows r < TX of the tile: sorted ranges, their prefix, and the packs
-      int lo = 0, cnt = 0;
-      if (lane < TX && p0 + lane < Mx) {
-        const size_t row = (size_t)(p0 + lane) * My;
-        lo = __ldg(d.cell_start + row + q0);
-        cnt = __ldg(d.cell_start + row + min(q0 + TY, My)) - lo;
+      int lo, hi;
+      if (pf_w == w) {
+        lo = pf_lo;
+        hi = pf_hi;
+      } else {
+        row_range(w, lo, hi);
       }
+      pf_w = w + gridDim.x;
+      row_range(pf_w, pf_lo, pf_hi);
+      const int cnt = hi - lo;
       int inc = cnt;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
