@@ -55,14 +55,33 @@ __device__ __forceinline__ void load_samples(const float *__restrict__ row, int 
   }
 }
 
+// acc += w * v on four components as two packed two-wide FMAs
+__device__ __forceinline__ void fma4(float w, const float4 &v, float4 &acc) {
+  const float2 ww = make_float2(w, w);
+  const float2 lo = __ffma2_rn(ww, make_float2(v.x, v.y), make_float2(acc.x, acc.y));
+  const float2 hi = __ffma2_rn(ww, make_float2(v.z, v.w), make_float2(acc.z, acc.w));
+  acc = make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
 template <int S>
 __device__ __forceinline__ void fma_entry(float (&acc)[kSpreadP][S], const float4 &w, const float (&v)[S]) {
+  // packed two-wide FMAs over sample pairs (each component rounds as fmaf)
 #pragma unroll
-  for (int u = 0; u < S; ++u) {
-    acc[0][u] = fmaf(w.x, v[u], acc[0][u]);
-    acc[1][u] = fmaf(w.y, v[u], acc[1][u]);
-    acc[2][u] = fmaf(w.z, v[u], acc[2][u]);
-    acc[3][u] = fmaf(w.w, v[u], acc[3][u]);
+  for (int u = 0; u < S; u += 2) {
+    const float2 vv = make_float2(v[u], v[u + 1]);
+    float2 a;
+    a = __ffma2_rn(make_float2(w.x, w.x), vv, make_float2(acc[0][u], acc[0][u + 1]));
+    acc[0][u] = a.x;
+    acc[0][u + 1] = a.y;
+    a = __ffma2_rn(make_float2(w.y, w.y), vv, make_float2(acc[1][u], acc[1][u + 1]));
+    acc[1][u] = a.x;
+    acc[1][u + 1] = a.y;
+    a = __ffma2_rn(make_float2(w.z, w.z), vv, make_float2(acc[2][u], acc[2][u + 1]));
+    acc[2][u] = a.x;
+    acc[2][u + 1] = a.y;
+    a = __ffma2_rn(make_float2(w.w, w.w), vv, make_float2(acc[3][u], acc[3][u + 1]));
+    acc[3][u] = a.x;
+    acc[3][u + 1] = a.y;
   }
 }
 
@@ -101,28 +120,52 @@ __global__ void __launch_bounds__(kThreadsSpread, 2) k_spread(const InstDesc *__
 #pragma unroll
     for (int u = 0; u < S; ++u) acc[r][u] = 0.f;
 
-  constexpr int B = 4;  // entries in flight per warp
-  int e = e0;
-  for (; e + B <= e1; e += B) {
-    int m[B];
-    float4 w[B];
-    float v[B][S];
-#pragma unroll
-    for (int b = 0; b < B; ++b) {
-      m[b] = __ldg(em + e + b);
-      w[b] = __ldg(ew + e + b);
+  // Entries in windows of 32: lane j loads entry j's caller index and tap
+  // products (one coalesced load each), entry b reaches every lane by a
+  // shuffle.  Within a window the g rows of batch k + 1 (B entries) load
+  // while batch k is summed, so only the g loads remain on the path.
+  constexpr int B = 4;
+  for (int e = e0; e < e1; e += 32) {
+    const int cnt = min(32, e1 - e);
+    int mj = 0;
+    float4 wj = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane < cnt) {
+      mj = __ldg(em + e + lane);
+      wj = __ldg(ew + e + lane);
     }
+    const int nb = (cnt + B - 1) / B;
+    float va[B][S], vb[B][S];
+    auto load_batch = [&](int k, float (&v)[B][S]) {
 #pragma unroll
-    for (int b = 0; b < B; ++b) load_samples<S>(g + (size_t)m[b] * Nt, n, Nt, vec, v[b]);
+      for (int b = 0; b < B; ++b) {
+        const int j = k * B + b;
+        const int m = __shfl_sync(0xffffffffu, mj, j & 31);
+        if (j < cnt) {
+          load_samples<S>(g + (size_t)m * Nt, n, Nt, vec, v[b]);
+        } else {
 #pragma unroll
-    for (int b = 0; b < B; ++b) fma_entry<S>(acc, w[b], v[b]);
-  }
-  for (; e < e1; ++e) {
-    const int m = __ldg(em + e);
-    const float4 w = __ldg(ew + e);
-    float v[S];
-    load_samples<S>(g + (size_t)m * Nt, n, Nt, vec, v);
-    fma_entry<S>(acc, w, v);
+          for (int u = 0; u < S; ++u) v[b][u] = 0.f;
+        }
+      }
+    };
+    auto sum_batch = [&](int k, const float (&v)[B][S]) {
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int j = (k * B + b) & 31;
+        const float4 w = make_float4(__shfl_sync(0xffffffffu, wj.x, j), __shfl_sync(0xffffffffu, wj.y, j),
+                                     __shfl_sync(0xffffffffu, wj.z, j), __shfl_sync(0xffffffffu, wj.w, j));
+        fma_entry<S>(acc, w, v[b]);  // entries past cnt carry zero products and samples
+      }
+    };
+    load_batch(0, va);
+#pragma unroll 1
+    for (int k = 0; k < nb; k += 2) {
+      if (k + 1 < nb) load_batch(k + 1, vb);
+      sum_batch(k, va);
+      if (k + 1 >= nb) break;
+      if (k + 2 < nb) load_batch(k + 2, va);
+      sum_batch(k + 1, vb);
+    }
   }
   if (n >= Nt) return;
   const bool vst = rows16 && (n + S <= Nt);
@@ -843,10 +886,7 @@ __global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS) k_interp
         for (int t = 0; t < W; ++t) {
           const float4 v = row[t * (NC / 4)];
           const float wy = pk[W + t];
-          rs.x = fmaf(wy, v.x, rs.x);
-          rs.y = fmaf(wy, v.y, rs.y);
-          rs.z = fmaf(wy, v.z, rs.z);
-          rs.w = fmaf(wy, v.w, rs.w);
+          fma4(wy, v, rs);
           if (GRAD) {
             const float dwy = pkd[W + t];
             rsy.x = fmaf(dwy, v.x, rsy.x);
@@ -856,10 +896,7 @@ __global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS) k_interp
           }
         }
         const float wx = pk[rr];
-        a0.x = fmaf(wx, rs.x, a0.x);
-        a0.y = fmaf(wx, rs.y, a0.y);
-        a0.z = fmaf(wx, rs.z, a0.z);
-        a0.w = fmaf(wx, rs.w, a0.w);
+        fma4(wx, rs, a0);
         if (GRAD) {
           const float dwx = pkd[rr];
           ax.x = fmaf(dwx, rs.x, ax.x);

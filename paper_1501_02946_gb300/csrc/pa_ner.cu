@@ -44,8 +44,7 @@ __device__ __forceinline__ float2 ner_interp(const float2 *H, int CB, ff tau, co
 #pragma unroll
   for (int t = 0; t < W; ++t) {
     const float2 h = H[prow(idx) * CB];
-    acc.x = fmaf(wt[t], h.x, acc.x);
-    acc.y = fmaf(wt[t], h.y, acc.y);
+    acc = __ffma2_rn(make_float2(wt[t], wt[t]), h, acc);
     idx = (idx + 1 == Mt) ? 0 : idx + 1;
   }
   return cmul(acc, centring_phase(d, tau));
@@ -88,8 +87,7 @@ __device__ __forceinline__ float2 cubic_interp(const float2 *H, int CB, ff tau, 
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     const float2 h = H[prow(idx) * CB];
-    acc.x = fmaf(wt[t], h.x, acc.x);
-    acc.y = fmaf(wt[t], h.y, acc.y);
+    acc = __ffma2_rn(make_float2(wt[t], wt[t]), h, acc);
     idx = (idx + 1 == Nt) ? 0 : idx + 1;
   }
   return acc;

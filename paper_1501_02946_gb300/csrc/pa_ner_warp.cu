@@ -149,8 +149,7 @@ __device__ __forceinline__ float2 interp_split(float2 *He, float2 *Ho, ff tau, c
 #pragma unroll
   for (int t = 0; t < W; ++t) {
     const float2 h = (t & 1) ? bb[t >> 1] : ba[t >> 1];
-    acc.x = fmaf(wt[t], h.x, acc.x);
-    acc.y = fmaf(wt[t], h.y, acc.y);
+    acc = __ffma2_rn(make_float2(wt[t], wt[t]), h, acc);
   }
   return cmul(acc, centring_phase(d, tau));
 }
