@@ -19,6 +19,16 @@
 // of a window never need a modulo.  The adjoint is the exact transpose.
 #include "pa_ner_common.cuh"
 
+// Resident blocks per SM the register allocation is held to (forward kernels
+// with Nt <= 512 and adjoint kernels; larger forward transforms keep their
+// registers).
+#ifndef PA_NER_FWD_MINB
+#define PA_NER_FWD_MINB 4
+#endif
+#ifndef PA_NER_ADJ_MINB
+#define PA_NER_ADJ_MINB 4
+#endif
+
 namespace pa {
 
 namespace {
@@ -186,7 +196,7 @@ __device__ __forceinline__ void flush_point(float2 *He, float2 *Ho, int pu, int 
 // of a two-source column, which lead at slot v with kind 2) is transformed in
 // t, interpolated at tau(j, l), weighted and transformed back over depth.
 template <int LGT, int LGZ, int W>
-__global__ void __launch_bounds__(128) k_ner_warp(const InstDesc *__restrict__ descs,
+__global__ void __launch_bounds__(128, LGT <= 9 ? PA_NER_FWD_MINB : 1) k_ner_warp(const InstDesc *__restrict__ descs,
                                                   const __grid_constant__ HornerTable ht) {
   extern __shared__ float4 smem_f4[];
   constexpr int Nt = 1 << LGT, Nz = 1 << LGZ;
@@ -255,7 +265,7 @@ __global__ void __launch_bounds__(128) k_ner_warp(const InstDesc *__restrict__ d
 // combination into the Nt centred samples, 1/phihat, into the G1 row of the
 // slot (summed over a two-source group).
 template <int LGT, int LGZ, int W>
-__global__ void __launch_bounds__(128, 3) k_ner_warp_adj(const InstDesc *__restrict__ descs,
+__global__ void __launch_bounds__(128, PA_NER_ADJ_MINB) k_ner_warp_adj(const InstDesc *__restrict__ descs,
                                                       const __grid_constant__ HornerTable ht) {
   extern __shared__ float4 smem_f4[];
   constexpr int Nt = 1 << LGT, Nz = 1 << LGZ;
