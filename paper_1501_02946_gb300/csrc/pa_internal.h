@@ -29,7 +29,17 @@ struct FftPlan {
 // grid is phi(fr + w/2 - 1 - t) = sum_d c[t][d] s^d with s = 2 fr - 1, where
 // phi is the Kaiser-Bessel window normalised to phi(0) = 1.
 struct HornerTable {
-  float c[kMaxWidth][kMaxDeg + 1];
+  // coefficient d of taps 2i (x) and 2i + 1 (y) side by side, so that a pair
+  // of taps evaluates as packed two-wide FMAs
+  float2 c2[kMaxWidth / 2][kMaxDeg + 1];
+  __host__ __device__ float coef(int t, int d) const { return (t & 1) ? c2[t >> 1][d].y : c2[t >> 1][d].x; }
+  __host__ void set(int t, int d, float v) {
+    if (t & 1) {
+      c2[t >> 1][d].y = v;
+    } else {
+      c2[t >> 1][d].x = v;
+    }
+  }
 };
 
 // One reconstruction instance as the kernels see it.  Every kernel reads

@@ -17,13 +17,17 @@ struct HornerDeg {
 
 __device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
 
-// tau(j, l) = sign(l) sqrt(ax jx^2 + ay jy^2 + az l^2) in double-float.
-__device__ __forceinline__ ff tau_of(const InstDesc &d, int jx, int jy, int l) {
-  const float jx2 = float(jx * jx), jy2 = float(jy * jy), l2 = float(l * l);
-  ff t2 = ff_add(ff_add(ff_mul_f({d.ax_hi, d.ax_lo}, jx2), ff_mul_f({d.ay_hi, d.ay_lo}, jy2)),
-                 ff_mul_f({d.az_hi, d.az_lo}, l2));
-  ff t = ff_sqrt(t2);
+// tau(j, l) = sign(l) sqrt(ax jx^2 + ay jy^2 + az l^2) in double-float; the
+// column's part ax jx^2 + ay jy^2 is tau_base(d, jx, jy).
+__device__ __forceinline__ ff tau_base(const InstDesc &d, int jx, int jy) {
+  return ff_add(ff_mul_f({d.ax_hi, d.ax_lo}, float(jx * jx)), ff_mul_f({d.ay_hi, d.ay_lo}, float(jy * jy)));
+}
+__device__ __forceinline__ ff tau_at(const InstDesc &d, ff base, int l) {
+  ff t = ff_sqrt(ff_add(base, ff_mul_f({d.az_hi, d.az_lo}, float(l * l))));
   return l < 0 ? ff_neg(t) : t;
+}
+__device__ __forceinline__ ff tau_of(const InstDesc &d, int jx, int jy, int l) {
+  return tau_at(d, tau_base(d, jx, jy), l);
 }
 
 // W(j, l) = 2 c |kz| / |K| with W(0, 0) = 2c and W(j != 0, 0) = 0.
@@ -67,12 +71,14 @@ template <int W>
 __device__ __forceinline__ void window_taps(float fr, const HornerTable &ht, float *wt) {
   constexpr int D = HornerDeg<W>::v;
   const float s = 2.f * fr - 1.f;
+  const float2 ss = make_float2(s, s);
 #pragma unroll
-  for (int t = 0; t < W; ++t) {
-    float a = ht.c[t][D];
+  for (int i = 0; i < W / 2; ++i) {  // taps 2i and 2i + 1 as packed two-wide Horner steps
+    float2 a = ht.c2[i][D];
 #pragma unroll
-    for (int k = D - 1; k >= 0; --k) a = fmaf(a, s, ht.c[t][k]);
-    wt[t] = a;
+    for (int k = D - 1; k >= 0; --k) a = __ffma2_rn(a, ss, ht.c2[i][k]);
+    wt[2 * i] = a.x;
+    wt[2 * i + 1] = a.y;
   }
 }
 

@@ -237,12 +237,13 @@ __global__ void __launch_bounds__(128, LGT <= 9 ? PA_NER_FWD_MINB : 1) k_ner_war
     }
     __syncwarp();
     const bool nyq = sl.kind >= 2;
+    const ff tb = tau_base(d, ci.jx, ci.jy);
 #pragma unroll 1
     for (int il = lane; il < Nz; il += 32) {
       const int l = il - hz;
       float2 F = make_float2(0.f, 0.f);
       if (!(l == 0 && (ci.jx != 0 || ci.jy != 0))) {
-        const ff tau = tau_of(d, ci.jx, ci.jy, l);
+        const ff tau = tau_at(d, tb, l);
         const float wgt = weight_of(d, tau, l) * d.scale;
         const bool lnyq = l == -hz;  // Nz is even
         const bool two = !nyq && lnyq;
@@ -295,6 +296,7 @@ __global__ void __launch_bounds__(128, PA_NER_ADJ_MINB) k_ner_warp_adj(const Ins
     for (int i = lane; i < 2 * HH; i += 32) He[i] = make_float2(0.f, 0.f);
     __syncwarp();
     const bool nyq = ci.xnyq || ci.ynyq;
+    const ff tb = tau_base(d, ci.jx, ci.jy);
     // The points u(l) = 2 tau(j, l) increase with l, so the taps of a lane's
     // consecutive samples overlap: they accumulate in a register window
     // acc[t] of the grid points base + t, which slides forward (adding the
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(128, PA_NER_ADJ_MINB) k_ner_warp_adj(const Ins
     for (int j = 0; j < C; ++j) {
       const int l = lane * C + j - hz;
       if (l == 0 && (ci.jx != 0 || ci.jy != 0)) continue;
-      const ff tau = tau_of(d, ci.jx, ci.jy, l);
+      const ff tau = tau_at(d, tb, l);
       const float wgt = weight_of(d, tau, l) * d.scale;
       const float2 val = cscale(Fs[l < 0 ? l + Nz : l], wgt);
       if (l == -hz) {  // the depth Nyquist sample also reaches -tau: outside the window's order

@@ -183,7 +183,7 @@ void fit_horner(const Kb &kb, int D, HornerTable &ht) {
       T0 = T1;
       T1 = T2;
     }
-    for (int k = 0; k <= D; ++k) ht.c[t][k] = float(out[k]);
+    for (int k = 0; k <= D; ++k) ht.set(t, k, float(out[k]));
   }
 }
 
