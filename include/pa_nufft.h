@@ -72,6 +72,13 @@ typedef struct {
   double dx, dy, dz;
 } pa_grid;
 
+/* Output grid of the d = 2 operator: nx x nz pixels (x along the sensor line,
+ * z the depth) with spacings dx, dz in metres. */
+typedef struct {
+  int32_t nx, nz;
+  double dx, dz;
+} pa_grid2;
+
 /*
  * Create a reconstruction plan (Sec. 3: the set-up of both NUFFTs).
  *   out        receives the plan (set to NULL on failure).
@@ -98,6 +105,33 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy,
                    const double *weights, int64_t n_t, double dt, double c,
                    const pa_grid *grid, int sigma, int width, int flags,
                    void *stream);
+
+/*
+ * Create a plan for the d = 2 operator (Sec. 2 with d - 1 = 1; the paper's
+ * 2-D setting of Sec. 6): sensors on the line z = 0 at x_m, images
+ *   f[p][k] = Re( 1/(nx nz) sum_{jx,l} F(jx,l) e^{i(kx x_p + kz z_k)} ),
+ *   F = (dt/dz) W G-hat,  G1(jx,n) = sum_m (h_m/dx) g[m][n] e^{-i kx x_m},
+ * with omega, W and the NER step exactly as in 3-D (ky = 0).
+ *   sensor_x   host, [M] doubles in metres; copied; reduced modulo X.
+ *   weights    host, [M] detector lengths h_m in m (> 0), or NULL for X/M
+ *              (Sec. 2 requires sum h_m = X).
+ *   grid       output grid; sigma, width, n_t, dt, c as in pa_plan_create;
+ *              flags: PA_FLAG_DEFAULT or PA_FLAG_BLOCK_NER.
+ * The plan works with pa_reconstruct (f: device [nx][nz] float),
+ * pa_reconstruct_adjoint, pa_reconstruct_cubic, pa_position_grad (grad_xy
+ * [M][2]: d/dx_m, and 0 in the second column), pa_status, pa_plan_info,
+ * pa_plan_buffer (G1 [nX1][1][n_t], image spectrum [nx][1][nz]), the
+ * profiling calls and pa_plan_destroy.  pa_plan_update_positions[_device],
+ * pa_plan_autotune, pa_position_grad_noalloc and batches return
+ * PA_ERR_INVALID_ARG for it.  Sizes as in pa_plan_create for nx, nz, n_t.
+ */
+int pa_plan_create_2d(pa_plan **out, int64_t n_sensors, const double *sensor_x,
+                      const double *weights, int64_t n_t, double dt, double c,
+                      const pa_grid2 *grid, int sigma, int width, int flags,
+                      void *stream);
+
+/* *d = 2 for a plan of pa_plan_create_2d, 3 otherwise. */
+int pa_plan_dims(const pa_plan *plan, int *d);
 
 /*
  * Forward reconstruction f = A g (eq:disc_rec via NEDNER-NUFFT, Sec. 3).

@@ -262,3 +262,49 @@ def half_spectrum_voxels(half, grid, pts):
         E = np.exp(1j * np.add.outer(kx * x, ky * y))
         out[i] = np.sum(E * S[:, :, k]).real
     return out
+
+
+# ---------------------------------------------------------------------------
+# The d = 2 operator (Sec. 2 with d - 1 = 1: sensors on the line z = 0 at
+# x_m, images f[p, k]).  eq:disc_rec for d = 2 is the general formula with a
+# one-dimensional x: a_m = h_m / dx, G1(jx, n) = sum_m a_m g[m, n]
+# exp(-i kx x_m), omega and W as above with ky = 0, and
+# f[p, k] = Re 1/(nx nz) sum_{jx,l} F(jx, l) exp(i (kx x_p + kz z_k)).  The
+# functions below evaluate exactly that through the general sums on a grid
+# with one y row of unit spacing (ny = 1, dy = 1: the y index set is {0}, so
+# ky = 0, a_m = h_m/(dx * 1) and 1/(nx * 1 * nz)).
+
+class Grid2:
+    """(nx, nz, dx, dz) of the d = 2 operator, seen as the general grid with
+    one y row of unit spacing."""
+
+    def __init__(self, nx, nz, dx, dz):
+        self.nx, self.ny, self.nz = int(nx), 1, int(nz)
+        self.dx, self.dy, self.dz = float(dx), 1.0, float(dz)
+
+    @property
+    def shape(self):
+        return (self.nx, self.nz)
+
+    def as_tuple(self):
+        return (self.nx, self.ny, self.nz, self.dx, self.dy, self.dz)
+
+
+def _line(x):
+    x = np.asarray(x, dtype=np.float64).reshape(-1)
+    return np.stack([x, np.zeros_like(x)], axis=1)
+
+
+def reconstruct_2d(x, h, g, dt, c, grid2):
+    """f[p, k] of the d = 2 operator; x: (M,) positions, h: (M,) lengths."""
+    return reconstruct(_line(x), h, g, dt, c, grid2)[:, 0, :]
+
+
+def reconstruct_adjoint_2d(x, h, fbar, dt, c, grid2, nt):
+    """Exact transpose of reconstruct_2d."""
+    return reconstruct_adjoint(_line(x), h, np.asarray(fbar)[:, None, :], dt, c, grid2, nt)
+
+
+def position_grad_2d(x, h, g, fbar, dt, c, grid2):
+    """d/dx_m of <fbar, reconstruct_2d(x, h, g)>, shape (M,)."""
+    return position_grad(_line(x), h, g, np.asarray(fbar)[:, None, :], dt, c, grid2)[:, 0]

@@ -18,9 +18,9 @@ from ctypes import byref, c_int, c_int64, c_void_p
 import numpy as np
 
 from . import _lib
-from ._lib import PaError, PaGrid, check
+from ._lib import PaError, PaGrid, PaGrid2, check
 
-__all__ = ["Plan", "Batch", "reconstruct", "ReconstructFunction", "PaError", "library_path"]
+__all__ = ["Plan", "Plan2D", "Batch", "reconstruct", "ReconstructFunction", "PaError", "library_path"]
 
 library_path = _lib.LIB_PATH
 
@@ -260,6 +260,62 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Plan2D(Plan):
+    """A plan of the d = 2 operator (pa_plan_create_2d): sensors on the line
+    z = 0, images f[nx][nz].
+
+    x: (M,) sensor positions in metres; weights: (M,) detector lengths in m
+    or None (X/M each); grid: (nx, nz, dx, dz).  reconstruct, adjoint,
+    reconstruct_cubic and position_grad (d/dx_m in column 0, zeros in
+    column 1) work as for Plan."""
+
+    def __init__(self, x, n_t, dt, c, grid, weights=None, sigma=2, width=8, device=None, warp_ner=True):
+        torch = _torch()
+        lib = _lib.load()
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1))
+        self.M = x.shape[0]
+        self.n_t = int(n_t)
+        self.dt = float(dt)
+        self.c = float(c)
+        nx, nz, dx, dz = grid
+        self.grid = (int(nx), int(nz), float(dx), float(dz))
+        self.sigma = int(sigma)
+        self.width = int(width)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        w = None
+        if weights is not None:
+            w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).reshape(-1))
+            if w.shape[0] != self.M:
+                raise ValueError("weights must have one entry per sensor")
+        g = PaGrid2(*self.grid)
+        ptr = c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib.pa_plan_create_2d(byref(ptr), self.M, x.ctypes.data_as(c_void_p),
+                                       None if w is None else w.ctypes.data_as(c_void_p),
+                                       self.n_t, self.dt, self.c, byref(g), self.sigma, self.width,
+                                       0 if warp_ner else 2,  # PA_FLAG_BLOCK_NER
+                                       _stream_ptr(self.device))
+        check(rc)
+        self._ptr = ptr
+        self._xy = np.stack([x, np.zeros_like(x)], axis=1)
+
+    @property
+    def image_shape(self):
+        return (self.grid[0], self.grid[1])
+
+    def buffer(self, which):
+        torch = _torch()
+        lib = _lib.load()
+        nbytes = c_int64()
+        nx, nz = self.image_shape
+        shape = (2 * (nx // 2) + 1, 1, self.n_t) if which == 0 else (nx, 1, nz)
+        out = torch.empty(shape, dtype=torch.complex64, device=self.device)
+        check(lib.pa_plan_buffer(self.handle, which, c_void_p(out.data_ptr()), out.numel() * 8, byref(nbytes),
+                                 _stream_ptr(self.device)))
+        return out
 
 
 class Batch:

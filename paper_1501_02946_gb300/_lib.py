@@ -27,10 +27,17 @@ class PaGrid(ctypes.Structure):
                 ("dx", c_double), ("dy", c_double), ("dz", c_double)]
 
 
+class PaGrid2(ctypes.Structure):
+    _fields_ = [("nx", c_int32), ("nz", c_int32), ("dx", c_double), ("dz", c_double)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "pa_plan_create": (c_int, [POINTER(c_void_p), c_int64, c_void_p, c_void_p, c_int64, c_double, c_double,
                                POINTER(PaGrid), c_int, c_int, c_int, c_void_p]),
+    "pa_plan_create_2d": (c_int, [POINTER(c_void_p), c_int64, c_void_p, c_void_p, c_int64, c_double, c_double,
+                                  POINTER(PaGrid2), c_int, c_int, c_int, c_void_p]),
+    "pa_plan_dims": (c_int, [c_void_p, POINTER(c_int)]),
     "pa_reconstruct": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pa_reconstruct_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pa_position_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -188,6 +188,13 @@ cudaError_t launch_imgy(const Launch &L, bool adjoint);
 cudaError_t launch_interp_width(const Launch &L, int width, bool grad, int ty);
 cudaError_t launch_rowifft(const Launch &L);
 cudaError_t launch_grad_reduce(const Launch &L, int M);
+// The d = 2 operator's own stages (pa_d2.cu): 1-D spread into T, its
+// transpose from T (with the position-gradient partials when grad), and the
+// real part of the single jy column and its transpose.
+cudaError_t launch_spread_x(const Launch &L, const InstDesc &h);
+cudaError_t launch_interp_x(const Launch &L, const InstDesc &h, bool grad);
+cudaError_t launch_real_out(const Launch &L, const InstDesc &h);
+cudaError_t launch_real_in(const Launch &L, const InstDesc &h);
 // Rewrite ipack / ipack_d from perm, sby, wx, wy, dwx, dwy (after a sensor upload).
 cudaError_t build_interp_pack(const InstDesc &h, cudaStream_t s);
 
@@ -232,6 +239,7 @@ struct PlanView {
   const HornerTable *ht;
   int device;
   long long n_sensors;
+  int dims;                 // 3, or 2 for a plan of pa_plan_create_2d
 };
 int plan_view(const pa_plan *P, PlanView *v);
 // Record an error message for pa_last_error() and return `code`.

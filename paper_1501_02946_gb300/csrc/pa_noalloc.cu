@@ -60,6 +60,7 @@ extern "C" int pa_position_grad_noalloc(pa_plan *plan, const float *g_dev, const
   pa::PlanView v{};
   if (!plan || !g_dev || !grad_f_dev || !grad_xy_dev || pa::plan_view(plan, &v) != PA_OK)
     return pa::set_error(PA_ERR_INVALID_ARG, "NULL argument");
+  if (v.dims != 3) return pa::set_error(PA_ERR_INVALID_ARG, "pa_position_grad_noalloc: not supported for 2-D plans");
   const pa::InstDesc &h = *v.h;
   const size_t need = size_t(h.nchunk_adj) * size_t(h.M);
   if (need > kPartials)

@@ -211,6 +211,8 @@ struct pa_plan {
   // device re-binning scratch (first pa_plan_update_positions_device call)
   char *d_rebin = nullptr;
   size_t rebin_bytes = 0;
+  // d = 2 operator (pa_plan_create_2d): Ny = 1, My = 1, sensors at (x_m, 0)
+  bool d2 = false;
   // lattice path: sensors on the output lattice (see pa_plan_is_lattice)
   bool lattice_allowed = true;
   bool lattice = false;
@@ -288,9 +290,14 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
       const double ddx = frx[m] + 0.5 * w - 1.0 - t;
       const double ddy = fry[m] + 0.5 * w - 1.0 - t;
       wx[size_t(i) * w + t] = float(kb.phi(ddx));
-      wy[size_t(i) * w + t] = float(a * kb.phi(ddy));
       dwx[size_t(i) * w + t] = float(kb.dphi(ddx) * Mx / X);
-      dwy[size_t(i) * w + t] = float(a * kb.dphi(ddy) * My / Y);
+      if (P->d2) {  // no window in y: a_m in tap 0
+        wy[size_t(i) * w + t] = t == 0 ? float(a) : 0.f;
+        dwy[size_t(i) * w + t] = 0.f;
+      } else {
+        wy[size_t(i) * w + t] = float(a * kb.phi(ddy));
+        dwy[size_t(i) * w + t] = float(a * kb.dphi(ddy) * My / Y);
+      }
     }
   }
   PA_CUDA(cudaMemcpyAsync((void *)P->h.perm, perm.data(), sizeof(int) * M, cudaMemcpyHostToDevice, stream));
@@ -456,6 +463,26 @@ int run_forward(pa_plan *P, const IoPtrs &io, cudaStream_t s, bool cubic) {
   L.io = io;
   const InstDesc &h = P->h;
   int rc;
+  if (P->d2) {
+    // d = 2: 1-D spread into T, then the column FFT, NER and inverse x DFT of
+    // the 3-D path on the one jy column, then the real part
+    if ((rc = timed(P, 0, s, [&] { return pa::launch_spread_x(L, h); }, "spread_x")) != PA_OK) return rc;
+    L.nblocks = pa::blocks_colfft(h);
+    L.smem = pa::smem_colfft(h);
+    if ((rc = timed(P, 1, s, [&] { return pa::launch_colfft(L, false); }, "colfft")) != PA_OK) return rc;
+    L.threads = h.ner_threads;
+    L.nblocks = pa::blocks_ner(h);
+    L.smem = pa::smem_ner(h);
+    if (cubic) {
+      if ((rc = timed(P, 11, s, [&] { return pa::launch_cubic(L); }, "cubic")) != PA_OK) return rc;
+    } else {
+      if ((rc = timed(P, 2, s, [&] { return pa::launch_ner(L, P->w, P->ht, false); }, "ner")) != PA_OK) return rc;
+    }
+    L.nblocks = pa::blocks_imgx(h);
+    L.smem = pa::smem_imgx(h);
+    if ((rc = timed(P, 3, s, [&] { return pa::launch_imgx(L, false); }, "imgx")) != PA_OK) return rc;
+    return timed(P, 4, s, [&] { return pa::launch_real_out(L, h); }, "real_out");
+  }
   if (P->lattice) {
     // sensors on the lattice: place, then DFT over the lattice (sigma = 1)
     const InstDesc &hl = P->hl;
@@ -509,6 +536,25 @@ int run_adjoint(pa_plan *P, const IoPtrs &io, cudaStream_t s, bool grad) {
   L.io = io;
   const InstDesc &h = P->h;
   int rc;
+  if (P->d2) {
+    if ((rc = timed(P, 5, s, [&] { return pa::launch_real_in(L, h); }, "real_in")) != PA_OK) return rc;
+    L.nblocks = pa::blocks_imgx(h);
+    L.smem = pa::smem_imgx(h);
+    if ((rc = timed(P, 6, s, [&] { return pa::launch_imgx(L, true); }, "imgx_adj")) != PA_OK) return rc;
+    L.threads = h.ner_threads;
+    L.nblocks = pa::blocks_ner_adj(h);
+    L.smem = pa::smem_ner(h);
+    if ((rc = timed(P, 7, s, [&] { return pa::launch_ner_stage(L, P->w, P->ht, 1); }, "ner_adj")) != PA_OK) return rc;
+    L.nblocks = pa::blocks_colfft(h);
+    L.smem = pa::smem_colfft(h);
+    if ((rc = timed(P, 8, s, [&] { return pa::launch_colfft(L, true); }, "colfft_adj")) != PA_OK) return rc;
+    if ((rc = timed(P, 9, s, [&] { return pa::launch_interp_x(L, h, grad); }, "interp_x")) != PA_OK) return rc;
+    if (grad) {
+      L.nblocks = std::min(1024, int((P->M + 255) / 256));
+      if ((rc = timed(P, 10, s, [&] { return pa::launch_grad_reduce(L, 1); }, "grad_reduce")) != PA_OK) return rc;
+    }
+    return PA_OK;
+  }
   L.nblocks = pa::blocks_imgy(h);
   L.smem = pa::smem_imgy(h);
   if ((rc = timed(P, 5, s, [&] { return pa::launch_imgy(L, true); }, "imgy_adj")) != PA_OK) return rc;
@@ -567,6 +613,7 @@ int plan_view(const pa_plan *P, PlanView *v) {
   v->ht = &P->ht;
   v->device = P->device;
   v->n_sensors = P->M;
+  v->dims = P->d2 ? 2 : 3;
   return PA_OK;
 }
 int set_error(int code, const char *msg) { return fail(code, msg ? msg : ""); }
@@ -678,9 +725,11 @@ const char *pa_last_error(void) { return g_err.c_str(); }
 
 const char *pa_version(void) { return "pa_nufft 0.1 (sm_103a)"; }
 
-int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, const double *weights, int64_t n_t,
-                   double dt, double c, const pa_grid *grid, int sigma, int width, int flags, void *stream) {
-  g_err.clear();
+namespace {
+// Plan creation for d = 3 and (d2: Ny = 1, no oversampling or window in y,
+// sensors at (x_m, 0)) for d = 2.
+int create_plan(pa_plan **out, int64_t n_sensors, const double *sensor_xy, const double *weights, int64_t n_t,
+                double dt, double c, const pa_grid *grid, int sigma, int width, int flags, void *stream, bool d2) {
   if (!out) return fail(PA_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!sensor_xy || !grid) return fail(PA_ERR_INVALID_ARG, "sensor_xy or grid is NULL");
@@ -688,7 +737,7 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
   if (n_t < 2 || n_t > 4096) return fail(PA_ERR_INVALID_ARG, "n_t out of range [2, 4096]");
   if (!(dt > 0) || !std::isfinite(dt)) return fail(PA_ERR_INVALID_ARG, "dt must be finite and > 0");
   if (!(c > 0) || !std::isfinite(c)) return fail(PA_ERR_INVALID_ARG, "c must be finite and > 0");
-  if (grid->nx < 2 || grid->ny < 2 || grid->nz < 2) return fail(PA_ERR_INVALID_ARG, "grid sizes must be >= 2");
+  if (grid->nx < 2 || (!d2 && grid->ny < 2) || grid->nz < 2) return fail(PA_ERR_INVALID_ARG, "grid sizes must be >= 2");
   if (!(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0) || !std::isfinite(grid->dx) ||
       !std::isfinite(grid->dy) || !std::isfinite(grid->dz))
     return fail(PA_ERR_INVALID_ARG, "grid spacings must be finite and > 0");
@@ -705,14 +754,16 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
         return fail(PA_ERR_INVALID_ARG, "weights must be finite and > 0");
   }
   const long Nx = grid->nx, Ny = grid->ny, Nz = grid->nz, Nt = n_t;
-  const long Mx = sigma * Nx, My = sigma * Ny, Mt = sigma * Nt;
+  const long Mx = sigma * Nx, My = d2 ? 1 : sigma * Ny, Mt = sigma * Nt;
   for (long L : {Nx, Ny, Nz, Nt, Mx, My, Mt})
     if (!smooth7(L)) return fail(PA_ERR_UNSUPPORTED_SIZE, "a transform length is not a product of 2, 3, 5, 7");
   if (Mx > 4096 || My > 512 || Nz > 4096 || Nx > 4096 || Ny > 4096 || Mt > 4096)
     return fail(PA_ERR_UNSUPPORTED_SIZE, "a transform length exceeds the supported maximum");
-  if (Mx < 2 * width || My < 2 * width) return fail(PA_ERR_UNSUPPORTED_SIZE, "sigma*nx and sigma*ny must be >= 2*width");
+  if (Mx < 2 * width || (!d2 && My < 2 * width))
+    return fail(PA_ERR_UNSUPPORTED_SIZE, "sigma*nx and sigma*ny must be >= 2*width");
 
   pa_plan *P = new pa_plan();
+  P->d2 = d2;
   P->M = n_sensors;
   P->Nt = n_t;
   P->dt = dt;
@@ -822,7 +873,7 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
   const Kb kb(width, sigma);
   std::vector<float> ipx(h.nX1), ipy(h.nY1), ipt(Nt);
   for (int ix = 0; ix < h.nX1; ++ix) ipx[ix] = float(1.0 / kb.phihat(double(ix - h.hx) / Mx));
-  for (int iy = 0; iy < h.nY1; ++iy) ipy[iy] = float(1.0 / kb.phihat(double(iy) / My));
+  for (int iy = 0; iy < h.nY1; ++iy) ipy[iy] = d2 ? 1.f : float(1.0 / kb.phihat(double(iy) / My));
   for (long n = 0; n < Nt; ++n) ipt[n] = float(1.0 / kb.phihat(double(n - h.nc) / Mt));
   const double Z = Nz * grid->dz;
   const double cT = c * Nt * dt;
@@ -911,7 +962,7 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
 
   int rc = upload_sensors(P, sensor_xy, s);
   if (rc == PA_OK) {
-    P->lattice_allowed = (flags & PA_FLAG_NO_LATTICE) == 0;
+    P->lattice_allowed = !d2 && (flags & PA_FLAG_NO_LATTICE) == 0;
     rc = setup_lattice(P, sensor_xy, s);
   }
   if (rc != PA_OK) {
@@ -935,10 +986,43 @@ int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, co
   *out = P;
   return PA_OK;
 }
+}  // namespace
+
+int pa_plan_create(pa_plan **out, int64_t n_sensors, const double *sensor_xy, const double *weights, int64_t n_t,
+                   double dt, double c, const pa_grid *grid, int sigma, int width, int flags, void *stream) {
+  g_err.clear();
+  return create_plan(out, n_sensors, sensor_xy, weights, n_t, dt, c, grid, sigma, width, flags, stream, false);
+}
+
+int pa_plan_create_2d(pa_plan **out, int64_t n_sensors, const double *sensor_x, const double *weights, int64_t n_t,
+                      double dt, double c, const pa_grid2 *grid, int sigma, int width, int flags, void *stream) {
+  g_err.clear();
+  if (out) *out = nullptr;
+  if (!sensor_x || !grid) return fail(PA_ERR_INVALID_ARG, "sensor_x or grid is NULL");
+  if (n_sensors < 1 || n_sensors > (int64_t(1) << 30)) return fail(PA_ERR_INVALID_ARG, "n_sensors out of range");
+  if ((flags & PA_FLAG_NO_LATTICE) != 0) return fail(PA_ERR_INVALID_ARG, "unknown flags");
+  // the 3-D plan with one y row of unit spacing: h_m/(dx dy) = h_m/dx and
+  // 1/(nx ny nz) = 1/(nx nz)
+  std::vector<double> xy(size_t(2 * n_sensors));
+  for (int64_t m = 0; m < n_sensors; ++m) {
+    xy[size_t(2 * m)] = sensor_x[m];
+    xy[size_t(2 * m + 1)] = 0.0;
+  }
+  const pa_grid g3{grid->nx, 1, grid->nz, grid->dx, 1.0, grid->dz};
+  return create_plan(out, n_sensors, xy.data(), weights, n_t, dt, c, &g3, sigma, width, flags, stream, true);
+}
+
+int pa_plan_dims(const pa_plan *plan, int *d) {
+  g_err.clear();
+  if (!plan || !d) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  *d = plan->d2 ? 2 : 3;
+  return PA_OK;
+}
 
 int pa_plan_update_positions(pa_plan *plan, const double *sensor_xy, void *stream) {
   g_err.clear();
   if (!plan || !sensor_xy) return fail(PA_ERR_INVALID_ARG, "plan or sensor_xy is NULL");
+  if (plan->d2) return fail(PA_ERR_INVALID_ARG, "not supported for 2-D plans");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int rc = upload_sensors(plan, sensor_xy, s);
   if (rc != PA_OK) return rc;
@@ -950,6 +1034,7 @@ int pa_plan_update_positions(pa_plan *plan, const double *sensor_xy, void *strea
 int pa_plan_update_positions_device(pa_plan *plan, const float *xy_dev, void *stream) {
   g_err.clear();
   if (!plan || !xy_dev) return fail(PA_ERR_INVALID_ARG, "plan or xy_dev is NULL");
+  if (plan->d2) return fail(PA_ERR_INVALID_ARG, "not supported for 2-D plans");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   pa_plan *P = plan;
   P->lattice = false;  // positions on the device are not tested for the lattice
@@ -1049,6 +1134,7 @@ int pa_plan_update_positions_device(pa_plan *plan, const float *xy_dev, void *st
 int pa_plan_autotune(pa_plan *plan, void *stream, int *choice) {
   g_err.clear();
   if (!plan) return fail(PA_ERR_INVALID_ARG, "plan is NULL");
+  if (plan->d2) return fail(PA_ERR_INVALID_ARG, "not supported for 2-D plans");
   pa_plan *P = plan;
   InstDesc &h = P->h;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -1313,6 +1399,7 @@ int pa_batch_create(pa_batch **out, int n, pa_plan *const *plans, void *stream) 
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
     if (!plans[i]) return fail(PA_ERR_INVALID_ARG, "NULL plan in batch");
+    if (plans[i]->d2) return fail(PA_ERR_INVALID_ARG, "2-D plans cannot be batched");
     if (plans[i]->w != plans[0]->w || plans[i]->sigma != plans[0]->sigma)
       return fail(PA_ERR_INVALID_ARG, "all plans of a batch need the same sigma and width");
   }

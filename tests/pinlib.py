@@ -179,3 +179,76 @@ def pin_position_grad_fd(position_grad=None, n_coords=12, seed=9):
     fd = (L(P.xy + eps * d) - L(P.xy - eps * d)) / (2 * eps)
     errs.append(abs(fd - np.sum(G * d)) / (scale * np.linalg.norm(d)))
     return max(errs)
+
+
+# --------------------------------------------------------------- d = 2 pins
+def pin_plane_wave_2d():
+    """d = 2: a laterally uniform source F(z) seen by sensors on every x node
+    records F(c t)/2 (1-D d'Alembert, the same in any dimension); the 2-D
+    reconstruction returns F(z_k) at every x."""
+    nx, nz, dz, c = 6, 48, 1e-4, 1500.0
+    dt, nt = dz / c, nz
+    grid = ndft.Grid2(nx, nz, 1e-4, dz)
+    x = (np.arange(nx) - nx // 2) * grid.dx
+    h = np.full(nx, grid.dx)
+    F = synth.gaussian_profile(1.6e-3, 2.2e-4, 1.0)
+    g = synth.plane_profile_data(nx, nt, dt, c, F)
+    f = ndft.reconstruct_2d(x, h, g, dt, c, grid)
+    ref = np.broadcast_to(F(np.arange(nz) * dz)[None, :], f.shape)
+    return rel(f, ref)
+
+
+def pin_2d_is_y_invariant_3d():
+    """Data that do not depend on y, recorded by every y node of a full y
+    lattice, reconstruct in 3-D to the same image at every y; with ky = 0
+    alone surviving, that image is the d = 2 reconstruction of the data along
+    one row (weights h_m dy per 3-D sensor)."""
+    rng = np.random.default_rng(21)
+    nx, ny, nz, nt = 7, 5, 12, 20
+    dx, dy, dz, c, dt = 1e-4, 1.3e-4, 1e-4, 1500.0, 3e-8
+    x = (np.arange(nx) - nx // 2) * dx + rng.uniform(-0.4, 0.4, nx) * dx
+    hx = rng.uniform(0.5, 1.5, nx) * dx
+    g = rng.normal(size=(nx, nt))
+    y = (np.arange(ny) - ny // 2) * dy
+    xy = np.array([(xm, yq) for xm in x for yq in y])
+    h3 = np.array([hm * dy for hm in hx for _ in y])
+    g3 = np.repeat(g, ny, axis=0)
+    f3 = ndft.reconstruct(xy, h3, g3, dt, c, synth.Grid(nx, ny, nz, dx, dy, dz))
+    f2 = ndft.reconstruct_2d(x, hx, g, dt, c, ndft.Grid2(nx, nz, dx, dz))
+    return max(rel(f3[:, q, :], f2) for q in range(ny))
+
+
+def pin_adjoint_dot_2d():
+    rng = np.random.default_rng(22)
+    nx, nz, nt = 9, 14, 24
+    grid = ndft.Grid2(nx, nz, 1e-4, 1e-4)
+    x = (np.arange(nx) - nx // 2) * grid.dx + rng.uniform(-0.4, 0.4, nx) * grid.dx
+    h = rng.uniform(0.5, 1.5, nx) * grid.dx
+    g = rng.normal(size=(nx, nt))
+    fb = rng.normal(size=(nx, nz))
+    dt, c = 2e-8, 1500.0
+    lhs = np.vdot(ndft.reconstruct_2d(x, h, g, dt, c, grid), fb)
+    rhs = np.vdot(g, ndft.reconstruct_adjoint_2d(x, h, fb, dt, c, grid, nt))
+    return abs(lhs - rhs) / max(abs(lhs), abs(rhs))
+
+
+def pin_position_grad_2d():
+    """FP64 central differences of <fbar, f(x)> against position_grad_2d."""
+    rng = np.random.default_rng(23)
+    nx, nz, nt = 8, 10, 16
+    grid = ndft.Grid2(nx, nz, 1e-4, 1e-4)
+    x = (np.arange(nx) - nx // 2) * grid.dx + rng.uniform(-0.4, 0.4, nx) * grid.dx
+    h = np.full(nx, grid.dx)
+    g = rng.normal(size=(nx, nt))
+    fb = rng.normal(size=(nx, nz))
+    dt, c = 2e-8, 1500.0
+    grad = ndft.position_grad_2d(x, h, g, fb, dt, c, grid)
+    eps = 1e-9
+    fd = np.empty(nx)
+    for m in range(nx):
+        xp, xm = x.copy(), x.copy()
+        xp[m] += eps
+        xm[m] -= eps
+        fd[m] = (np.vdot(fb, ndft.reconstruct_2d(xp, h, g, dt, c, grid)) -
+                 np.vdot(fb, ndft.reconstruct_2d(xm, h, g, dt, c, grid))) / (2 * eps)
+    return rel(grad, fd)

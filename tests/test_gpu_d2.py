@@ -1,0 +1,96 @@
+"""The d = 2 operator (pa_plan_create_2d): forward, adjoint and position
+gradient against the direct FP64 sums (oracle reconstruct_2d and its
+transpose), dot-product tests, even and odd nx, the warp and the block NER
+kernels, and the arguments the 2-D plans refuse."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ndft
+
+from test_gpu_parity import TOL, dev, host, pa, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1501_02946_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def line_case(nx, nz, nt, ns, seed, dx=1e-4, dz=1e-4):
+    rng = np.random.default_rng(seed)
+    X = nx * dx
+    # ns sensors, jittered around an equispaced line over the aperture
+    x = (np.arange(ns) + 0.5) * (X / ns) - X / 2 + rng.uniform(-0.4, 0.4, ns) * (X / ns)
+    h = rng.uniform(0.6, 1.4, ns) * (X / ns)
+    g = rng.normal(size=(ns, nt))
+    return x, h, g, ndft.Grid2(nx, nz, dx, dz)
+
+
+CASES = [(16, 32, 64, 16), (15, 24, 50, 21), (32, 256, 256, 40), (24, 36, 40, 17), (64, 512, 256, 50)]
+
+
+@pytest.mark.parametrize("nx,nz,nt,ns", CASES)
+def test_2d_forward_adjoint_match_direct_sums(nx, nz, nt, ns):
+    x, h, g, grid = line_case(nx, nz, nt, ns, seed=nx + nz)
+    dt, c = 20e-9, 1500.0
+    plan = pa().Plan2D(x, nt, dt, c, (nx, nz, grid.dx, grid.dz), weights=h)
+    f = host(plan.reconstruct(dev(g)))
+    assert f.shape == (nx, nz)
+    err = rel(f, ndft.reconstruct_2d(x, h, g, dt, c, grid))
+    print(f"2-D {nx}x{nz} nt={nt} M={ns} warp={plan.warp_ner}: forward rel L2 = {err:.3e}")
+    assert err <= TOL
+    fb = np.random.default_rng(3).normal(size=(nx, nz))
+    gb = host(plan.adjoint(dev(fb)))
+    errb = rel(gb, ndft.reconstruct_adjoint_2d(x, h, fb, dt, c, grid, nt))
+    print(f"2-D {nx}x{nz} nt={nt}: adjoint rel L2 = {errb:.3e}")
+    assert errb <= TOL
+    lhs = float(np.vdot(f, fb))
+    rhs = float(np.vdot(g.astype(np.float32).astype(np.float64), gb))
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs))
+    assert plan.status() == 0
+
+
+@pytest.mark.parametrize("nx,nz,nt,ns", CASES[:3])
+def test_2d_position_grad_matches_oracle(nx, nz, nt, ns):
+    x, h, g, grid = line_case(nx, nz, nt, ns, seed=7)
+    dt, c = 20e-9, 1500.0
+    plan = pa().Plan2D(x, nt, dt, c, (nx, nz, grid.dx, grid.dz), weights=h)
+    fb = np.random.default_rng(4).normal(size=(nx, nz))
+    gg, gxy = plan.position_grad(dev(g), dev(fb))
+    gxy = host(gxy)
+    ref = ndft.position_grad_2d(x, h, g, fb, dt, c, grid)
+    err = rel(gxy[:, 0], ref)
+    print(f"2-D {nx}x{nz}: position gradient rel L2 = {err:.3e}")
+    assert err <= TOL
+    assert np.all(gxy[:, 1] == 0.0)
+    assert rel(host(gg), ndft.reconstruct_adjoint_2d(x, h, fb, dt, c, grid, nt)) <= TOL
+
+
+def test_2d_warp_and_block_ner_agree():
+    x, h, g, grid = line_case(32, 256, 256, 40, seed=9)
+    a = pa().Plan2D(x, 256, 20e-9, 1500.0, (32, 256, grid.dx, grid.dz), weights=h)
+    b = pa().Plan2D(x, 256, 20e-9, 1500.0, (32, 256, grid.dx, grid.dz), weights=h, warp_ner=False)
+    assert a.warp_ner and not b.warp_ner
+    gd = dev(g)
+    assert rel(host(a.reconstruct(gd)), host(b.reconstruct(gd))) <= 1e-5
+
+
+def test_2d_default_weights_are_x_over_m():
+    x, h, g, grid = line_case(16, 32, 64, 12, seed=11)
+    dt, c = 20e-9, 1500.0
+    plan = pa().Plan2D(x, 64, dt, c, (16, 32, grid.dx, grid.dz))
+    hdef = np.full(12, 16 * grid.dx / 12)
+    assert rel(host(plan.reconstruct(dev(g))), ndft.reconstruct_2d(x, hdef, g, dt, c, grid)) <= TOL
+
+
+def test_2d_plans_refuse_unsupported_calls():
+    x, h, g, grid = line_case(16, 32, 64, 12, seed=12)
+    plan = pa().Plan2D(x, 64, 20e-9, 1500.0, (16, 32, grid.dx, grid.dz), weights=h)
+    with pytest.raises(pa().PaError):
+        plan.autotune()
+    with pytest.raises(pa().PaError):
+        plan.update_positions(np.zeros((12, 2)))

@@ -195,3 +195,20 @@ def test_half_spectrum_voxels_round_trip(shape):
     got = ndft.half_spectrum_voxels(half, grid, pts)
     ref = np.array([f[p, q, k] for p, q, k in pts])
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------- d = 2
+def test_plane_wave_profile_recovered_2d():
+    assert pinlib.pin_plane_wave_2d() <= 1e-9
+
+
+def test_2d_matches_y_invariant_3d():
+    assert pinlib.pin_2d_is_y_invariant_3d() <= 1e-12
+
+
+def test_adjoint_dot_2d():
+    assert pinlib.pin_adjoint_dot_2d() <= 1e-12
+
+
+def test_position_grad_2d_matches_finite_differences():
+    assert pinlib.pin_position_grad_2d() <= 1e-6
