@@ -364,6 +364,22 @@ def run_ours(args):
     lat_ms = timed_calls(lattice_step, k_parts) if plan_l.is_lattice else None
     plan_l.close()
     del g_l
+    # the d = 2 operator: 256 sensors on a 51.2 mm line (jittered, centre-dense),
+    # 1024 samples at 20 ns, image 512 x 512 at 100 um
+    rng2 = np.random.default_rng(1507)
+    nx2, nz2, nt2, m2 = 512, 512, 1024, 256
+    X2 = nx2 * 1e-4
+    x2 = np.sort(np.concatenate([rng2.uniform(-X2 / 2, X2 / 2, m2 // 2),
+                                 rng2.normal(0.0, X2 / 8, m2 // 2).clip(-X2 / 2, X2 / 2 - 1e-7)]))
+    plan_2 = pa.Plan2D(x2, nt2, 20e-9, P.c, (nx2, nz2, 1e-4, 1e-4))
+    g_2 = torch.randn(m2, nt2, device=dev, dtype=torch.float32)
+    f_2 = torch.empty(nx2, nz2, device=dev, dtype=torch.float32)
+    def d2_step():
+        plan_2.reconstruct(g_2, out=f_2)
+        plan_2.adjoint(f_2, out=g_2)
+    d2_ms = timed_calls(d2_step, k_parts)
+    plan_2.close()
+    del g_2, f_2
     parts = {"forward": {"ms": fwd_ms, "voxels_per_s": voxels / (fwd_ms / 1e3)},
              "adjoint": {"ms": adj_ms, "voxels_per_s": voxels / (adj_ms / 1e3)},
              "cubic_baseline_forward": {"ms": cub_ms, "voxels_per_s": voxels / (cub_ms / 1e3)},
@@ -371,6 +387,9 @@ def run_ours(args):
              "lattice_sensors_fwd_adj": None if lat_ms is None else
              {"ms": lat_ms, "voxels_per_s": voxels / (lat_ms / 1e3),
               "workload": f"{Nx}x{Ny} sensors on the output lattice, same samples and output"},
+             "d2_fwd_adj": {"ms": d2_ms, "pixels_per_s": nx2 * nz2 / (d2_ms / 1e3),
+                            "workload": f"d = 2: {m2} sensors on a {X2 * 1e3:.1f} mm line, {nt2} samples at 20 ns, "
+                                        f"image {nx2}x{nz2} at 100 um"},
              "own_row_col_transforms_ms": (prof["ned_rowfft"][0] / prof["ned_rowfft"][1]
                                            + prof["ned_colfft"][0] / prof["ned_colfft"][1])
              if "ned_rowfft" in prof and "ned_colfft" in prof else None,

@@ -30,7 +30,8 @@ def line_case(nx, nz, nt, ns, seed, dx=1e-4, dz=1e-4):
     return x, h, g, ndft.Grid2(nx, nz, dx, dz)
 
 
-CASES = [(16, 32, 64, 16), (15, 24, 50, 21), (32, 256, 256, 40), (24, 36, 40, 17), (64, 512, 256, 50)]
+CASES = [(16, 32, 64, 16), (15, 24, 50, 21), (32, 256, 256, 40), (24, 36, 40, 17), (64, 512, 256, 50),
+         (300, 64, 128, 90)]
 
 
 @pytest.mark.parametrize("nx,nz,nt,ns", CASES)
@@ -94,3 +95,34 @@ def test_2d_plans_refuse_unsupported_calls():
         plan.autotune()
     with pytest.raises(pa().PaError):
         plan.update_positions(np.zeros((12, 2)))
+
+
+def test_2d_bench_size_dot_and_columns():
+    """The 512 x 512, 1024-sample, 256-sensor workload of the bench: dot test
+    of forward and adjoint, and three image columns against the direct sums
+    (oracle column_depth_profile on the one-row grid)."""
+    rng = np.random.default_rng(1507)
+    nx, nz, nt, M = 512, 512, 1024, 256
+    X = nx * 1e-4
+    x = np.sort(np.concatenate([rng.uniform(-X / 2, X / 2, M // 2),
+                                rng.normal(0.0, X / 8, M // 2).clip(-X / 2, X / 2 - 1e-7)]))
+    dt, c = 20e-9, 1500.0
+    plan = pa().Plan2D(x, nt, dt, c, (nx, nz, 1e-4, 1e-4))
+    g = rng.normal(size=(M, nt))
+    gd = dev(g)
+    f = host(plan.reconstruct(gd))
+    spec = plan.buffer(1).cpu().numpy()  # before the adjoint reuses the buffer
+    fb = rng.normal(size=(nx, nz))
+    gb = host(plan.adjoint(dev(fb)))
+    lhs = float(np.vdot(f, fb))
+    rhs = float(np.vdot(g.astype(np.float32).astype(np.float64), gb))
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs))
+    # spectrum columns jx of the image spectrum after NER (buffer 1) against O1
+    grid = ndft.Grid2(nx, nz, 1e-4, 1e-4)
+    h = np.full(M, X / M)
+    for jx in (0, 37, -101):
+        ref = ndft.column_depth_profile(np.stack([x, np.zeros_like(x)], 1), h, g, dt, c, grid, jx, 0)
+        got = spec[jx + nx // 2, 0, :]
+        err = rel(got, ref)
+        print(f"2-D bench size column jx={jx}: rel L2 = {err:.3e}")
+        assert err <= TOL
