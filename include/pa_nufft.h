@@ -134,6 +134,34 @@ int pa_plan_create_2d(pa_plan **out, int64_t n_sensors, const double *sensor_x,
 int pa_plan_dims(const pa_plan *plan, int *d);
 
 /*
+ * Image quality measures of the paper's appendix, on device images (FP64
+ * accumulation, deterministic block-ordered sums; synchronise `stream`;
+ * scratch from the stream-ordered allocator).
+ * pa_correlation: *rho = Cov(a, b) / sqrt(Var(a) Var(b)) over the n >= 2
+ *   floats at a_dev and b_dev (eq:corrcoeff, population moments).
+ * pa_tenenbaum: *value = (1/N) sum over the images of the stack
+ *   u[n0][n1][n2] (images over the first two axes, N = n0 n1 n2) of
+ *   (g * U)^2 + (g^T * U)^2 at the pixels where the 3x3 Sobel operator g lies
+ *   inside the image; n0, n1 >= 3.  A 3-D reconstruction f[nx][ny][nz] is the
+ *   stack of its nz depth images; a 2-D image f[nx][nz] is n2 = 1.
+ */
+/*
+ * Gradient of L = <grad_f, A(h) g> with respect to the detector weights h_m
+ * of eq:disc_rec (A is linear in h): grad_h[m] = (1/h_m) sum_n g[m][n]
+ * (A^T grad_f)[m][n], the caller's sensor order.  Runs the adjoint into
+ * scratch from the stream-ordered allocator; asynchronous on `stream`.
+ * With weights that depend on the positions (Voronoi areas, say) the chain
+ * rule adds sum_k grad_h[k] dh_k/dx_m to pa_position_grad's result.
+ * 2-D and 3-D plans.  g_dev [M][n_t], grad_f_dev as pa_reconstruct's
+ * output, grad_h_dev [M] float.
+ */
+int pa_weight_grad(pa_plan *plan, const float *g_dev, const float *grad_f_dev, float *grad_h_dev,
+                   void *stream);
+
+int pa_correlation(const float *a_dev, const float *b_dev, int64_t n, double *rho, void *stream);
+int pa_tenenbaum(const float *u_dev, int64_t n0, int64_t n1, int64_t n2, double *value, void *stream);
+
+/*
  * Forward reconstruction f = A g (eq:disc_rec via NEDNER-NUFFT, Sec. 3).
  *   g_dev  device [M][n_t] float, sensor order as given to pa_plan_create.
  *   f_dev  device [nx][ny][nz] float (written entirely).

@@ -11,6 +11,8 @@ Modules
           directly, its exact transpose and its sensor-position gradient.
   nufft   O2: the NEDNER-NUFFT algorithm in the paper's order (NED, NER,
           inverse FFT; Sec. 3), in FP64 with a wide window, and its transpose.
+  metrics the appendix's quality measures: correlation coefficient and the
+          normalised Tenenbaum (Sobel) sharpness.
 
 Parity status: every function here is pinned by tests under
 ``tests/test_oracle_pins.py`` (closed forms, lattice special cases, integer
@@ -18,4 +20,4 @@ frequency special cases, exact invariants, dot-product and finite-difference
 checks); nothing is "parity unpinned" except the absolute amplitude of the
 uniform-ball physics check, which limited view makes only loosely determined.
 """
-from . import window, ndft, nufft  # noqa: F401
+from . import window, ndft, nufft, metrics  # noqa: F401

@@ -308,3 +308,11 @@ def reconstruct_adjoint_2d(x, h, fbar, dt, c, grid2, nt):
 def position_grad_2d(x, h, g, fbar, dt, c, grid2):
     """d/dx_m of <fbar, reconstruct_2d(x, h, g)>, shape (M,)."""
     return position_grad(_line(x), h, g, np.asarray(fbar)[:, None, :], dt, c, grid2)[:, 0]
+
+
+def weight_grad(xy, h, g, fbar, dt, c, grid):
+    """Gradient of L = <fbar, reconstruct(xy, h, g)> with respect to the
+    weights h (M,): reconstruct is linear in h, so dL/dh_m = (1/h_m)
+    sum_n g[m, n] (reconstruct_adjoint(fbar))[m, n]."""
+    gb = reconstruct_adjoint(xy, h, fbar, dt, c, grid, g.shape[1])
+    return np.sum(g * gb, axis=1) / h

@@ -20,7 +20,8 @@ import numpy as np
 from . import _lib
 from ._lib import PaError, PaGrid, PaGrid2, check
 
-__all__ = ["Plan", "Plan2D", "Batch", "reconstruct", "ReconstructFunction", "PaError", "library_path"]
+__all__ = ["Plan", "Plan2D", "Batch", "reconstruct", "ReconstructFunction", "PaError", "library_path",
+           "correlation", "tenenbaum"]
 
 library_path = _lib.LIB_PATH
 
@@ -164,6 +165,16 @@ class Plan:
                                            c_void_p(grad_g.data_ptr()) if grad_g is not None else None,
                                            c_void_p(grad_xy.data_ptr()), _stream_ptr(g.device)))
         return grad_g, grad_xy
+
+    def weight_grad(self, g, grad_f):
+        """dL/dh [M] for L = <grad_f, A(h) g> (pa_weight_grad)."""
+        torch = _torch()
+        _check_tensor(g, self.data_shape, "g")
+        _check_tensor(grad_f, self.image_shape, "grad_f")
+        out = torch.empty(self.M, dtype=torch.float32, device=g.device)
+        check(_lib.load().pa_weight_grad(self.handle, c_void_p(g.data_ptr()), c_void_p(grad_f.data_ptr()),
+                                         c_void_p(out.data_ptr()), _stream_ptr(g.device)))
+        return out
 
     def position_grad_noalloc(self, g, grad_f, want_grad_g=True):
         """position_grad whose scratch is the library's static device array
@@ -405,3 +416,32 @@ def ReconstructFunction():
 def reconstruct(g, xy, plan):
     """Differentiable reconstruction: f = A(xy) g."""
     return ReconstructFunction().apply(g, xy, plan)
+
+
+# ------------------------------------------------------------ quality measures
+def correlation(a, b):
+    """Correlation coefficient of two CUDA float32 tensors with the same number
+    of elements (pa_correlation)."""
+    if a.numel() != b.numel():
+        raise ValueError("correlation needs tensors of equal size")
+    a = a.contiguous()
+    b = b.contiguous()
+    v = ctypes.c_double()
+    check(_lib.load().pa_correlation(c_void_p(a.data_ptr()), c_void_p(b.data_ptr()), a.numel(), byref(v),
+                                     _stream_ptr(a.device)))
+    return v.value
+
+
+def tenenbaum(u):
+    """Normalised Tenenbaum sharpness of a CUDA float32 image [n0][n1] or stack
+    [n0][n1][n2] of images over the first two axes (pa_tenenbaum)."""
+    u = u.contiguous()
+    if u.dim() == 2:
+        n0, n1, n2 = u.shape[0], u.shape[1], 1
+    elif u.dim() == 3:
+        n0, n1, n2 = u.shape
+    else:
+        raise ValueError("tenenbaum takes a 2-D image or a 3-D stack")
+    v = ctypes.c_double()
+    check(_lib.load().pa_tenenbaum(c_void_p(u.data_ptr()), n0, n1, n2, byref(v), _stream_ptr(u.device)))
+    return v.value

@@ -195,6 +195,10 @@ cudaError_t launch_spread_x(const Launch &L, const InstDesc &h);
 cudaError_t launch_interp_x(const Launch &L, const InstDesc &h, bool grad);
 cudaError_t launch_real_out(const Launch &L, const InstDesc &h);
 cudaError_t launch_real_in(const Launch &L, const InstDesc &h);
+// grad_h[m] = inv_h[m] * sum_n g[m][n] gb[m][n] (pa_metrics.cu): the
+// gradient with respect to the weights h_m, given gb = A^T grad_f.
+cudaError_t launch_weight_grad(const float *g, const float *gb, const float *inv_h, int M, int Nt, float *grad_h,
+                               cudaStream_t s);
 // Rewrite ipack / ipack_d from perm, sby, wx, wy, dwx, dwy (after a sensor upload).
 cudaError_t build_interp_pack(const InstDesc &h, cudaStream_t s);
 

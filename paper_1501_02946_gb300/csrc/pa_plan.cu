@@ -213,6 +213,7 @@ struct pa_plan {
   size_t rebin_bytes = 0;
   // d = 2 operator (pa_plan_create_2d): Ny = 1, My = 1, sensors at (x_m, 0)
   bool d2 = false;
+  float *d_invh = nullptr;        // [M] 1/h_m in the caller's order (static buffer)
   // lattice path: sensors on the output lattice (see pa_plan_is_lattice)
   bool lattice_allowed = true;
   bool lattice = false;
@@ -910,6 +911,7 @@ int create_plan(pa_plan **out, int64_t n_sensors, const double *sensor_xy, const
   const size_t o_wx = take(sizeof(float) * M * W), o_wy = take(sizeof(float) * M * W);
   const size_t o_dwx = take(sizeof(float) * M * W), o_dwy = take(sizeof(float) * M * W);
   const size_t o_cs = take(sizeof(int) * (size_t(Mx) * My + 1));
+  const size_t o_invh = take(sizeof(float) * M);
   const size_t o_ipk = take(sizeof(float) * M * pa::ipack_words(width));
   const size_t o_ipkd = take(sizeof(float) * M * pa::ipackd_words(width));
   const size_t o_ipx = take(sizeof(float) * ipx.size()), o_ipy = take(sizeof(float) * ipy.size());
@@ -946,6 +948,7 @@ int create_plan(pa_plan **out, int64_t n_sensors, const double *sensor_xy, const
   h.dwx = reinterpret_cast<const float *>(S + o_dwx);
   h.dwy = reinterpret_cast<const float *>(S + o_dwy);
   h.cell_start = reinterpret_cast<const int *>(S + o_cs);
+  P->d_invh = reinterpret_cast<float *>(S + o_invh);
   h.ipack = reinterpret_cast<const float4 *>(S + o_ipk);
   h.ipack_d = reinterpret_cast<const float4 *>(S + o_ipkd);
   h.invphx = reinterpret_cast<const float *>(S + o_ipx);
@@ -972,7 +975,10 @@ int create_plan(pa_plan **out, int64_t n_sensors, const double *sensor_xy, const
   auto up = [&](const void *dst, const void *src, size_t bytes) {
     return cudaMemcpyAsync(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice, s);
   };
-  ce = up(h.invphx, ipx.data(), sizeof(float) * ipx.size());
+  std::vector<float> invh(static_cast<size_t>(n_sensors));
+  for (int64_t m = 0; m < n_sensors; ++m) invh[size_t(m)] = float(1.0 / P->weights[size_t(m)]);
+  ce = up(P->d_invh, invh.data(), sizeof(float) * invh.size());
+  if (ce == cudaSuccess) ce = up(h.invphx, ipx.data(), sizeof(float) * ipx.size());
   if (ce == cudaSuccess) ce = up(h.invphy, ipy.data(), sizeof(float) * ipy.size());
   if (ce == cudaSuccess) ce = up(h.invpht, ipt.data(), sizeof(float) * ipt.size());
   if (ce == cudaSuccess) ce = up(h.tw, tw.data(), sizeof(float2) * tw.size());
@@ -1292,6 +1298,26 @@ int pa_position_grad(pa_plan *plan, const float *g_dev, const float *grad_f_dev,
   io.g_out = grad_g_dev;
   io.grad_xy = grad_xy_dev;
   return run_adjoint(plan, io, reinterpret_cast<cudaStream_t>(stream), true);
+}
+
+int pa_weight_grad(pa_plan *plan, const float *g_dev, const float *grad_f_dev, float *grad_h_dev, void *stream) {
+  g_err.clear();
+  if (!plan || !g_dev || !grad_f_dev || !grad_h_dev) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  float *gb = nullptr;
+  const size_t n = size_t(plan->M) * size_t(plan->Nt);
+  if (cudaMallocAsync(reinterpret_cast<void **>(&gb), sizeof(float) * n, s) != cudaSuccess)
+    return fail(PA_ERR_OOM, "pa_weight_grad: scratch allocation failed");
+  IoPtrs io{};
+  io.f_in = grad_f_dev;
+  io.g_out = gb;
+  int rc = run_adjoint(plan, io, s, false);
+  if (rc == PA_OK) {
+    const cudaError_t e = pa::launch_weight_grad(g_dev, gb, plan->d_invh, int(plan->M), int(plan->Nt), grad_h_dev, s);
+    if (e != cudaSuccess) rc = fail(PA_ERR_CUDA, std::string("weight_grad: ") + cudaGetErrorString(e));
+  }
+  cudaFreeAsync(gb, s);
+  return rc;
 }
 
 int pa_profile_enable(pa_plan *plan, int enable) {

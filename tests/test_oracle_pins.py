@@ -212,3 +212,18 @@ def test_adjoint_dot_2d():
 
 def test_position_grad_2d_matches_finite_differences():
     assert pinlib.pin_position_grad_2d() <= 1e-6
+
+
+def test_weight_grad_is_the_per_sensor_image():
+    """L is linear in h: dL/dh_m = <fbar, reconstruct(xy, e_m, g)> with e_m the
+    m-th unit weight vector (one reconstruction per sensor)."""
+    P = synth.tiny()
+    rng = np.random.default_rng(31)
+    fb = rng.normal(size=P.grid.shape)
+    got = ndft.weight_grad(P.xy, P.h, P.g, fb, P.dt, P.c, P.grid)
+    ref = np.empty(P.xy.shape[0])
+    for m in range(P.xy.shape[0]):
+        e = np.zeros(P.xy.shape[0])
+        e[m] = 1.0
+        ref[m] = np.vdot(fb, ndft.reconstruct(P.xy, e, P.g, P.dt, P.c, P.grid))
+    assert pinlib.rel(got, ref) <= 1e-11
