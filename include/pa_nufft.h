@@ -158,6 +158,22 @@ int pa_plan_dims(const pa_plan *plan, int *d);
 int pa_weight_grad(pa_plan *plan, const float *g_dev, const float *grad_f_dev, float *grad_h_dev,
                    void *stream);
 
+/*
+ * Detector weights from the sensor positions: the Voronoi cells of the plan's
+ * sensors in the periodic domain of eq:disc_rec (the X x Y torus for 3-D
+ * plans, the circle X for 2-D plans), whose sizes sum to X Y (X):
+ * pa_voronoi_weights writes the cell areas (lengths) to h_dev [M] float in
+ * the caller's order.  pa_voronoi_grad adds the chain-rule term
+ * sum_k grad_h[k] dh_k/dx_m to grad_xy_dev [M][2] (2-D plans: column 0),
+ * so that pa_position_grad followed by pa_weight_grad and pa_voronoi_grad
+ * gives dL/dx for weights that follow the positions.  Both use the plan's
+ * current positions and binning; asynchronous on `stream`.  A cell with more
+ * vertices than the kernel's buffer leaves its entries unwritten and sets a
+ * status bit (pa_status).
+ */
+int pa_voronoi_weights(pa_plan *plan, float *h_dev, void *stream);
+int pa_voronoi_grad(pa_plan *plan, const float *grad_h_dev, float *grad_xy_dev, void *stream);
+
 int pa_correlation(const float *a_dev, const float *b_dev, int64_t n, double *rho, void *stream);
 int pa_tenenbaum(const float *u_dev, int64_t n0, int64_t n1, int64_t n2, double *value, void *stream);
 

@@ -13,6 +13,7 @@ Modules
           inverse FFT; Sec. 3), in FP64 with a wide window, and its transpose.
   metrics the appendix's quality measures: correlation coefficient and the
           normalised Tenenbaum (Sobel) sharpness.
+  voronoi detector weights as periodic Voronoi cell sizes and their gradient.
 
 Parity status: every function here is pinned by tests under
 ``tests/test_oracle_pins.py`` (closed forms, lattice special cases, integer
@@ -20,4 +21,4 @@ frequency special cases, exact invariants, dot-product and finite-difference
 checks); nothing is "parity unpinned" except the absolute amplitude of the
 uniform-ball physics check, which limited view makes only loosely determined.
 """
-from . import window, ndft, nufft, metrics  # noqa: F401
+from . import window, ndft, nufft, metrics, voronoi  # noqa: F401

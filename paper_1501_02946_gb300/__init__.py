@@ -176,6 +176,22 @@ class Plan:
                                          c_void_p(out.data_ptr()), _stream_ptr(g.device)))
         return out
 
+    def voronoi_weights(self):
+        """Voronoi cell sizes [M] of the plan's sensors in the periodic domain
+        (pa_voronoi_weights)."""
+        torch = _torch()
+        out = torch.empty(self.M, dtype=torch.float32, device=self.device)
+        check(_lib.load().pa_voronoi_weights(self.handle, c_void_p(out.data_ptr()), _stream_ptr(self.device)))
+        return out
+
+    def voronoi_grad(self, grad_h, grad_xy):
+        """grad_xy [M, 2] += sum_k grad_h[k] dh_k/dx (pa_voronoi_grad); returns grad_xy."""
+        _check_tensor(grad_xy, (self.M, 2), "grad_xy")
+        gh = grad_h.contiguous()
+        check(_lib.load().pa_voronoi_grad(self.handle, c_void_p(gh.data_ptr()), c_void_p(grad_xy.data_ptr()),
+                                          _stream_ptr(self.device)))
+        return grad_xy
+
     def position_grad_noalloc(self, g, grad_f, want_grad_g=True):
         """position_grad whose scratch is the library's static device array
         (no device allocation in the call; see include/pa_nufft.h)."""

@@ -40,6 +40,8 @@ SIGNATURES = {
     "pa_plan_dims": (c_int, [c_void_p, POINTER(c_int)]),
     "pa_correlation": (c_int, [c_void_p, c_void_p, c_int64, POINTER(c_double), c_void_p]),
     "pa_weight_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "pa_voronoi_weights": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "pa_voronoi_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pa_tenenbaum": (c_int, [c_void_p, c_int64, c_int64, c_int64, POINTER(c_double), c_void_p]),
     "pa_reconstruct": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pa_reconstruct_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -69,6 +69,7 @@ struct InstDesc {
   const float *wx, *wy; // [M][w]; wy carries a_m = h_m/(dx dy)
   const float *dwx, *dwy;  // [M][w] derivative taps d/dx_m and d/dy_m
   const int *cell_start;   // [Mx*My + 1] CSR offsets of the sorted sensors per cell
+  const double2 *pos;      // [M] positions reduced into [-X/2, X/2) x [-Y/2, Y/2), caller order
   // per sorted sensor, for the interpolation tiles: ipack[i] holds
   // wx[0..w), wy[0..w), by, m (as int bits) in ipack_words(w) floats;
   // ipack_d[i] holds dwx[0..w), dwy[0..w) in ipackd_words(w) floats
@@ -199,6 +200,22 @@ cudaError_t launch_real_in(const Launch &L, const InstDesc &h);
 // gradient with respect to the weights h_m, given gb = A^T grad_f.
 cudaError_t launch_weight_grad(const float *g, const float *gb, const float *inv_h, int M, int Nt, float *grad_h,
                                cudaStream_t s);
+// Periodic Voronoi weights and their chain-rule gradient (pa_voronoi.cu).
+struct VoronoiLaunch {
+  int M, Mx, My;
+  double X, Y;
+  int line;                 // 1: 2-D plan (sensors on the circle X)
+  const double2 *pos;       // [M] reduced positions, caller order
+  const int *perm, *sbx, *sby, *cell_start;
+  float *h;                 // [M] weights out, or null
+  const float *grad_h;      // [M] gradient in, or null
+  float *grad_xy;           // [M][2] accumulated, or null
+  int *status;
+};
+cudaError_t launch_voronoi(const VoronoiLaunch &v, cudaStream_t s);
+// Status-word bit: a Voronoi cell outgrew its vertex buffer (its weight and
+// gradient were not written).
+constexpr int kStatusVoronoi = 8;
 // Rewrite ipack / ipack_d from perm, sby, wx, wy, dwx, dwy (after a sensor upload).
 cudaError_t build_interp_pack(const InstDesc &h, cudaStream_t s);
 
@@ -209,6 +226,7 @@ struct RebinArgs {
   double X, Y, ax;         // period lengths and 1/(dx dy)
   double beta, phi0;       // Kaiser-Bessel window of the plan
   const float *xy;         // [M][2] new positions (caller's device buffer)
+  double2 *pos;            // [M] reduced positions (plan table, output)
   const double *weights;   // [M] detector areas h_m
   int *status;             // plan status word (non-finite positions)
   // plan tables (outputs)

@@ -257,12 +257,14 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
   const Kb kb(w, P->sigma);
   std::vector<int> bx(M), by(M);
   std::vector<double> frx(M), fry(M);
+  std::vector<double2> pos(M);
   for (int m = 0; m < M; ++m) {
     const double x = xy[2 * m], y = xy[2 * m + 1];
     if (!std::isfinite(x) || !std::isfinite(y)) return fail(PA_ERR_INVALID_ARG, "non-finite sensor position");
     double ux = x / X, uy = y / Y;
     ux -= std::floor(ux + 0.5);
     uy -= std::floor(uy + 0.5);
+    pos[m] = make_double2(ux * X, uy * Y);
     const double Ux = Mx * ux, Uy = My * uy;
     const double fbx = std::floor(Ux), fby = std::floor(Uy);
     frx[m] = Ux - fbx;
@@ -301,6 +303,7 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
       }
     }
   }
+  PA_CUDA(cudaMemcpyAsync((void *)P->h.pos, pos.data(), sizeof(double2) * M, cudaMemcpyHostToDevice, stream));
   PA_CUDA(cudaMemcpyAsync((void *)P->h.perm, perm.data(), sizeof(int) * M, cudaMemcpyHostToDevice, stream));
   PA_CUDA(cudaMemcpyAsync((void *)P->h.sbx, sbx.data(), sizeof(int) * M, cudaMemcpyHostToDevice, stream));
   PA_CUDA(cudaMemcpyAsync((void *)P->h.sby, sby.data(), sizeof(int) * M, cudaMemcpyHostToDevice, stream));
@@ -912,6 +915,7 @@ int create_plan(pa_plan **out, int64_t n_sensors, const double *sensor_xy, const
   const size_t o_dwx = take(sizeof(float) * M * W), o_dwy = take(sizeof(float) * M * W);
   const size_t o_cs = take(sizeof(int) * (size_t(Mx) * My + 1));
   const size_t o_invh = take(sizeof(float) * M);
+  const size_t o_pos = take(sizeof(double2) * M);
   const size_t o_ipk = take(sizeof(float) * M * pa::ipack_words(width));
   const size_t o_ipkd = take(sizeof(float) * M * pa::ipackd_words(width));
   const size_t o_ipx = take(sizeof(float) * ipx.size()), o_ipy = take(sizeof(float) * ipy.size());
@@ -949,6 +953,7 @@ int create_plan(pa_plan **out, int64_t n_sensors, const double *sensor_xy, const
   h.dwy = reinterpret_cast<const float *>(S + o_dwy);
   h.cell_start = reinterpret_cast<const int *>(S + o_cs);
   P->d_invh = reinterpret_cast<float *>(S + o_invh);
+  h.pos = reinterpret_cast<const double2 *>(S + o_pos);
   h.ipack = reinterpret_cast<const float4 *>(S + o_ipk);
   h.ipack_d = reinterpret_cast<const float4 *>(S + o_ipkd);
   h.invphx = reinterpret_cast<const float *>(S + o_ipx);
@@ -1077,6 +1082,7 @@ int pa_plan_update_positions_device(pa_plan *plan, const float *xy_dev, void *st
   a.beta = kb.beta;
   a.phi0 = kb.phi0;
   a.xy = xy_dev;
+  a.pos = const_cast<double2 *>(h.pos);
   a.weights = reinterpret_cast<const double *>(R + o_w);
   a.status = h.status;
   a.perm = const_cast<int *>(h.perm);
@@ -1318,6 +1324,45 @@ int pa_weight_grad(pa_plan *plan, const float *g_dev, const float *grad_f_dev, f
   }
   cudaFreeAsync(gb, s);
   return rc;
+}
+
+namespace {
+pa::VoronoiLaunch voronoi_launch(pa_plan *P) {
+  pa::VoronoiLaunch v{};
+  const InstDesc &h = P->h;
+  v.M = int(P->M);
+  v.Mx = h.Mx;
+  v.My = h.My;
+  v.X = P->grid.nx * P->grid.dx;
+  v.Y = P->grid.ny * P->grid.dy;
+  v.line = P->d2 ? 1 : 0;
+  v.pos = h.pos;
+  v.perm = h.perm;
+  v.sbx = h.sbx;
+  v.sby = h.sby;
+  v.cell_start = h.cell_start;
+  v.status = h.status;
+  return v;
+}
+}  // namespace
+
+int pa_voronoi_weights(pa_plan *plan, float *h_dev, void *stream) {
+  g_err.clear();
+  if (!plan || !h_dev) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  pa::VoronoiLaunch v = voronoi_launch(plan);
+  v.h = h_dev;
+  PA_CUDA(pa::launch_voronoi(v, reinterpret_cast<cudaStream_t>(stream)));
+  return PA_OK;
+}
+
+int pa_voronoi_grad(pa_plan *plan, const float *grad_h_dev, float *grad_xy_dev, void *stream) {
+  g_err.clear();
+  if (!plan || !grad_h_dev || !grad_xy_dev) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  pa::VoronoiLaunch v = voronoi_launch(plan);
+  v.grad_h = grad_h_dev;
+  v.grad_xy = grad_xy_dev;
+  PA_CUDA(pa::launch_voronoi(v, reinterpret_cast<cudaStream_t>(stream)));
+  return PA_OK;
 }
 
 int pa_profile_enable(pa_plan *plan, int enable) {

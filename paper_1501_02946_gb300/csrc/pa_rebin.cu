@@ -62,6 +62,7 @@ __global__ void k_rb_coords(RebinArgs a) {
   double ux = x / a.X, uy = y / a.Y;
   ux -= floor(ux + 0.5);
   uy -= floor(uy + 0.5);
+  a.pos[m] = make_double2(ux * a.X, uy * a.Y);
   const double Ux = a.Mx * ux, Uy = a.My * uy;
   const double fbx = floor(Ux), fby = floor(Uy);
   a.frx[m] = Ux - fbx;
