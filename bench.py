@@ -449,10 +449,10 @@ def run_ours(args):
 
 def run_batch(args):
     """The uneven batch (64 instances, N uniform over the 7-smooth integers in
-    [64, 256], T in {256, 512, 1024}, output N x N x 2T): one pa_batch_run
-    (one launch per stage over all instances, replayed as a CUDA graph)
-    against 64 sequential single-plan reconstructions.  Seeded random data
-    (timing only)."""
+    [64, 256], T in {256, 512, 1024}, output N x N x 2T): pa_batch_run
+    (the instances' launches as concurrent branches of a CUDA graph; and the
+    mode with one launch per stage over all instances) against 64 sequential
+    single-plan reconstructions.  Seeded random data (timing only)."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -472,7 +472,8 @@ def run_batch(args):
         gs.append(torch.randn(n_side * n_side, n_t, device=dev, dtype=torch.float32))
         fs.append(torch.empty(n_side, n_side, 2 * n_t, device=dev, dtype=torch.float32))
         voxels += n_side * n_side * 2 * n_t
-    batch = pa.Batch(plans)
+    batch = pa.Batch(plans)               # concurrent per-instance branches
+    batch_st = pa.Batch(plans, mode=1)    # one launch per stage over all instances
     stream = torch.cuda.current_stream(dev)
 
     def seq():
@@ -482,8 +483,11 @@ def run_batch(args):
     def bat():
         batch.run(gs, fs)
 
+    def bat_st():
+        batch_st.run(gs, fs)
+
     res = {}
-    for name, fn in (("batch_graph", bat), ("sequential_64", seq)):
+    for name, fn in (("batch_graph", bat), ("batch_graph_stage_launches", bat_st), ("sequential_64", seq)):
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize(dev)
@@ -503,6 +507,7 @@ def run_batch(args):
            "comparison": res, "speedup_vs_sequential": res["sequential_64"]["ms"] / res["batch_graph"]["ms"]}
     print(json.dumps(out))
     batch.close()
+    batch_st.close()
     for p in plans:
         p.close()
     return 0

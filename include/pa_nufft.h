@@ -264,15 +264,23 @@ int pa_reconstruct_cubic(pa_plan *plan, const float *g_dev, float *f_dev, void *
 int pa_plan_destroy(pa_plan *plan);
 
 /*
- * Batched reconstruction of many independent plans of uneven sizes: every
- * stage runs as one launch over all instances, and the launch sequence is
- * captured once in a CUDA graph and replayed.
+ * Batched forward reconstruction of many independent 3-D plans of uneven
+ * sizes, replayed as one CUDA graph.
  *   pa_batch_create: plans[n] (not owned; must outlive the batch; same sigma
  *                    and width), n >= 1.
  *   pa_batch_run:    g_dev[i] / f_dev[i] host arrays of n device pointers.
+ *                    The first call with a set of buffers runs the launches
+ *                    directly and captures the graph; later calls with the
+ *                    same buffers replay it (other buffers: a new capture).
+ *   pa_batch_set_mode: 0 (default): each instance's own single-plan launches
+ *                    (the fastest kernels its sizes have), as 4 concurrent
+ *                    branches of the graph, largest instances first;
+ *                    1: one launch per stage over all instances (work lists
+ *                    of (instance, tile)).  Both compute the same results.
  */
 int pa_batch_create(pa_batch **out, int n, pa_plan *const *plans, void *stream);
 int pa_batch_run(pa_batch *batch, const float *const *g_dev, float *const *f_dev, void *stream);
+int pa_batch_set_mode(pa_batch *batch, int mode);
 int pa_batch_destroy(pa_batch *batch);
 
 /*

@@ -346,10 +346,12 @@ class Plan2D(Plan):
 
 
 class Batch:
-    """Many plans of uneven sizes reconstructed together (pa_batch_*): one
-    launch per stage over all instances, replayed as a CUDA graph."""
+    """Many plans of uneven sizes reconstructed together (pa_batch_*),
+    replayed as a CUDA graph.  mode 0: each instance's own single-plan
+    launches as concurrent graph branches; mode 1: one launch per stage over
+    all instances."""
 
-    def __init__(self, plans):
+    def __init__(self, plans, mode=0):
         torch = _torch()
         self.plans = list(plans)
         n = len(self.plans)
@@ -358,6 +360,7 @@ class Batch:
         check(_lib.load().pa_batch_create(byref(ptr), n, arr, _stream_ptr(self.plans[0].device)))
         self._ptr = ptr
         self.device = self.plans[0].device
+        check(_lib.load().pa_batch_set_mode(self._ptr, int(mode)))
         del torch
 
     def run(self, gs, fs):

@@ -244,6 +244,13 @@ struct pa_batch {
   int width = 8;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
+  // mode 0: every instance's own single-plan launches, as concurrent branches
+  // of one CUDA graph; mode 1: one launch per stage over all instances
+  int mode = 0;
+  std::vector<const float *> cap_g;  // caller buffers the graph was captured with
+  std::vector<float *> cap_f;
+  std::vector<cudaStream_t> side;    // branch streams (mode 0)
+  std::vector<cudaEvent_t> ev;       // fork + one join per branch
 };
 
 namespace {
@@ -1561,6 +1568,99 @@ static int batch_launches(pa_batch *B, cudaStream_t s) {
   return PA_OK;
 }
 
+static void batch_drop_graph(pa_batch *B) {
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  B->exec = nullptr;
+  B->graph = nullptr;
+}
+
+// Mode 0: the instances' single-plan forward launches (the fastest kernels
+// each size has: warp NER, tensor-map pipelines) as kBranches concurrent
+// branches of one graph, largest instances first, each branch taking the
+// next instance when it has the least estimated work.
+constexpr int kBranches = 4;
+
+static int batch_run_branches(pa_batch *B, const float *const *g_dev, float *const *f_dev, cudaStream_t s) {
+  const int n = int(B->plans.size());
+  bool same = B->exec != nullptr && int(B->cap_g.size()) == n;
+  for (int i = 0; same && i < n; ++i) same = B->cap_g[i] == g_dev[i] && B->cap_f[i] == f_dev[i];
+  if (same) {
+    PA_CUDA(cudaGraphLaunch(B->exec, s));
+    return PA_OK;
+  }
+  batch_drop_graph(B);
+  auto io_of = [&](int i) {
+    IoPtrs io{};
+    io.g_in = g_dev[i];
+    io.f_out = f_dev[i];
+    return io;
+  };
+  // this call: the launches directly (also sets the kernels' attributes
+  // outside the capture); later calls with the same buffers replay the graph
+  for (int i = 0; i < n; ++i) {
+    const int rc = run_forward(B->plans[i], io_of(i), s, false);
+    if (rc != PA_OK) return rc;
+  }
+  if (B->side.empty()) {
+    B->side.resize(kBranches);
+    B->ev.resize(kBranches + 1);
+    for (auto &st : B->side) PA_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    for (auto &e : B->ev) PA_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  auto cost = [&](int i) {
+    const InstDesc &h = B->plans[i]->h;
+    return double(h.Mx) * h.My * h.Nt + double(h.Nx) * h.Ny * h.Nz;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  cudaStream_t cap;
+  PA_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  int rc = PA_OK;
+  cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (ce == cudaSuccess) {
+    ce = cudaEventRecord(B->ev[0], cap);
+    for (int k = 0; ce == cudaSuccess && k < kBranches; ++k) ce = cudaStreamWaitEvent(B->side[k], B->ev[0], 0);
+    double load[kBranches] = {0.0};
+    for (int j = 0; ce == cudaSuccess && rc == PA_OK && j < n; ++j) {
+      const int i = order[j];
+      int k = 0;
+      for (int q = 1; q < kBranches; ++q)
+        if (load[q] < load[k]) k = q;
+      load[k] += cost(i);
+      rc = run_forward(B->plans[i], io_of(i), B->side[k], false);
+    }
+    for (int k = 0; ce == cudaSuccess && k < kBranches; ++k) {
+      ce = cudaEventRecord(B->ev[k + 1], B->side[k]);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cap, B->ev[k + 1], 0);
+    }
+    const cudaError_t ce2 = cudaStreamEndCapture(cap, &B->graph);
+    if (ce == cudaSuccess) ce = ce2;
+  }
+  cudaStreamDestroy(cap);
+  if (ce != cudaSuccess || rc != PA_OK) {
+    batch_drop_graph(B);
+    return rc != PA_OK ? rc : fail(PA_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  }
+  PA_CUDA(cudaGraphInstantiate(&B->exec, B->graph, 0));
+  B->cap_g.assign(g_dev, g_dev + n);
+  B->cap_f.assign(f_dev, f_dev + n);
+  return PA_OK;
+}
+
+int pa_batch_set_mode(pa_batch *B, int mode) {
+  g_err.clear();
+  if (!B || (mode != 0 && mode != 1)) return fail(PA_ERR_INVALID_ARG, "bad batch mode");
+  if (mode != B->mode) {
+    batch_drop_graph(B);
+    B->cap_g.clear();
+    B->cap_f.clear();
+    B->mode = mode;
+  }
+  return PA_OK;
+}
+
 int pa_batch_run(pa_batch *B, const float *const *g_dev, float *const *f_dev, void *stream) {
   g_err.clear();
   if (!B || !g_dev || !f_dev) return fail(PA_ERR_INVALID_ARG, "NULL argument");
@@ -1573,6 +1673,7 @@ int pa_batch_run(pa_batch *B, const float *const *g_dev, float *const *f_dev, vo
     io[i].g_in = g_dev[i];
     io[i].f_out = f_dev[i];
   }
+  if (B->mode == 0) return batch_run_branches(B, g_dev, f_dev, s);
   // pageable source: the copy has consumed `io` when the call returns
   PA_CUDA(cudaMemcpyAsync(B->d_io, io.data(), sizeof(IoPtrs) * n, cudaMemcpyHostToDevice, s));
   if (!B->exec) {
@@ -1602,6 +1703,8 @@ int pa_batch_destroy(pa_batch *B) {
   cudaDeviceSynchronize();
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->graph) cudaGraphDestroy(B->graph);
+  for (auto st : B->side) cudaStreamDestroy(st);
+  for (auto e : B->ev) cudaEventDestroy(e);
   cudaFree(B->d_descs);
   cudaFree(B->d_io);
   cudaFree(B->d_work);

@@ -326,13 +326,14 @@ def test_cubic_baseline_is_less_accurate():
     assert e_nufft < e_cubic < 1.0
 
 
-def test_batch_matches_single_plans():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_matches_single_plans(mode):
     rng = np.random.default_rng(5)
     probs = [synth.batch_instance(rng, n, t, n_balls=2) for n, t in ((16, 32), (21, 48), (12, 64), (20, 40))]
     plans = [plan_of(P) for P in probs]
     gs = [dev(P.g) for P in probs]
     singles = [host(p.reconstruct(g)) for p, g in zip(plans, gs)]
-    B = pa().Batch(plans)
+    B = pa().Batch(plans, mode=mode)
     fs = [torch.empty(p.image_shape, device="cuda") for p in plans]
     for _ in range(3):  # first run captures the graph, later runs replay it
         for f in fs:
@@ -342,6 +343,28 @@ def test_batch_matches_single_plans():
             assert np.array_equal(host(f), s)
     ref = ndft.reconstruct(probs[1].xy, probs[1].h, probs[1].g, probs[1].dt, probs[1].c, probs[1].grid)
     assert rel(singles[1], ref) <= TOL
+
+
+def test_batch_with_fast_path_sizes():
+    """Instances whose single plans take the warp NER and tensor-map kernels:
+    mode 0 replays exactly those launches (bit-identical), mode 1 runs the
+    general stage kernels over all instances (same operator to rounding)."""
+    rng = np.random.default_rng(6)
+    probs = [synth.batch_instance(rng, n, t, n_balls=2) for n, t in ((64, 256), (70, 128), (32, 512), (64, 128))]
+    plans = [plan_of(P) for P in probs]
+    gs = [dev(P.g) for P in probs]
+    singles = [host(p.reconstruct(g)) for p, g in zip(plans, gs)]
+    for mode in (0, 1):
+        B = pa().Batch(plans, mode=mode)
+        fs = [torch.empty(p.image_shape, device="cuda") for p in plans]
+        for _ in range(2):
+            B.run(gs, fs)
+            for f, s in zip(fs, singles):
+                if mode == 0:
+                    assert np.array_equal(host(f), s)
+                else:
+                    assert rel(host(f), s) <= 1e-5
+        B.close()
 
 
 # ----------------------------------------------------------- full size
