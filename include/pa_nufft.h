@@ -172,6 +172,13 @@ int pa_weight_grad(pa_plan *plan, const float *g_dev, const float *grad_f_dev, f
  * status bit (pa_status).
  */
 int pa_voronoi_weights(pa_plan *plan, float *h_dev, void *stream);
+/*
+ * Replace the plan's detector weights by h_dev [M] float (device, caller's
+ * order, finite and > 0; say the output of pa_voronoi_weights): the tables
+ * that carry h_m are rescaled on the device.  Synchronises `stream` (the
+ * weights are also kept on the host for later position updates).
+ */
+int pa_plan_set_weights_device(pa_plan *plan, const float *h_dev, void *stream);
 int pa_voronoi_grad(pa_plan *plan, const float *grad_h_dev, float *grad_xy_dev, void *stream);
 
 int pa_correlation(const float *a_dev, const float *b_dev, int64_t n, double *rho, void *stream);

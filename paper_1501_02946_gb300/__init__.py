@@ -184,6 +184,15 @@ class Plan:
         check(_lib.load().pa_voronoi_weights(self.handle, c_void_p(out.data_ptr()), _stream_ptr(self.device)))
         return out
 
+    def set_weights(self, h):
+        """New detector weights [M] (CUDA tensor or host array) for this plan
+        (pa_plan_set_weights_device)."""
+        torch = _torch()
+        t = torch.as_tensor(h, dtype=torch.float32, device=self.device).contiguous().reshape(-1)
+        if t.numel() != self.M:
+            raise ValueError("set_weights needs one weight per sensor")
+        check(_lib.load().pa_plan_set_weights_device(self.handle, c_void_p(t.data_ptr()), _stream_ptr(self.device)))
+
     def voronoi_grad(self, grad_h, grad_xy):
         """grad_xy [M, 2] += sum_k grad_h[k] dh_k/dx (pa_voronoi_grad); returns grad_xy."""
         _check_tensor(grad_xy, (self.M, 2), "grad_xy")
@@ -395,11 +404,14 @@ def _autograd():
         sensor positions xy (through the window derivative)."""
 
         @staticmethod
-        def forward(ctx, g, xy, plan):
+        def forward(ctx, g, xy, plan, voronoi=False):
             xy_np = xy.detach().to("cpu", torch.float64).numpy()
             if not np.array_equal(xy_np, plan.positions):
                 plan.update_positions(xy_np)
+            if voronoi:
+                plan.set_weights(plan.voronoi_weights())
             ctx.plan = plan
+            ctx.voronoi = voronoi
             ctx.xy_meta = (xy.dtype, xy.device)
             ctx.save_for_backward(g)
             return plan.reconstruct(g.contiguous())
@@ -413,11 +425,13 @@ def _autograd():
             grad_g = grad_xy = None
             if need_xy:
                 grad_g, gxy = plan.position_grad(g.contiguous(), grad_f, want_grad_g=need_g)
+                if ctx.voronoi:  # the weights follow the positions
+                    plan.voronoi_grad(plan.weight_grad(g.contiguous(), grad_f), gxy)
                 dtype, device = ctx.xy_meta
                 grad_xy = gxy.to(device=device, dtype=dtype)
             elif need_g:
                 grad_g = plan.adjoint(grad_f)
-            return grad_g, grad_xy, None
+            return grad_g, grad_xy, None, None
 
     return ReconstructFunction
 
@@ -432,9 +446,11 @@ def ReconstructFunction():
     return _RF
 
 
-def reconstruct(g, xy, plan):
-    """Differentiable reconstruction: f = A(xy) g."""
-    return ReconstructFunction().apply(g, xy, plan)
+def reconstruct(g, xy, plan, voronoi=False):
+    """Differentiable reconstruction: f = A(xy) g.  With voronoi=True the
+    detector weights are the Voronoi cells of xy (set on every call) and the
+    position gradient includes their dependence on xy."""
+    return ReconstructFunction().apply(g, xy, plan, voronoi)
 
 
 # ------------------------------------------------------------ quality measures

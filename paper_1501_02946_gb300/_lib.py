@@ -41,6 +41,7 @@ SIGNATURES = {
     "pa_correlation": (c_int, [c_void_p, c_void_p, c_int64, POINTER(c_double), c_void_p]),
     "pa_weight_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pa_voronoi_weights": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "pa_plan_set_weights_device": (c_int, [c_void_p, c_void_p, c_void_p]),
     "pa_voronoi_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pa_tenenbaum": (c_int, [c_void_p, c_int64, c_int64, c_int64, POINTER(c_double), c_void_p]),
     "pa_reconstruct": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),

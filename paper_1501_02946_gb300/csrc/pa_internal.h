@@ -200,6 +200,23 @@ cudaError_t launch_real_in(const Launch &L, const InstDesc &h);
 // gradient with respect to the weights h_m, given gb = A^T grad_f.
 cudaError_t launch_weight_grad(const float *g, const float *gb, const float *inv_h, int M, int Nt, float *grad_h,
                                cudaStream_t s);
+// New detector weights h_new for a plan (pa_metrics.cu): ratio = h_new /
+// h_old per sensor, the tables that carry h_m scaled by it (wy, dwy in
+// sorted order, the spread entries' tap products, the lattice amplitudes),
+// and inv_h rewritten.
+struct WeightRescale {
+  int M, w;
+  const float *h_new;
+  float *inv_h;            // [M] 1/h (in: old, out: new)
+  float *ratio;            // [M] scratch
+  const int *perm;
+  float *wy, *dwy;         // [M][w], sorted order
+  size_t n_entries;
+  const int *sp_m;
+  float4 *sp_w;
+  float *lat_amp;          // [M] caller order, or null
+};
+cudaError_t rescale_weights(const WeightRescale &r, cudaStream_t s);
 // Periodic Voronoi weights and their chain-rule gradient (pa_voronoi.cu).
 struct VoronoiLaunch {
   int M, Mx, My;

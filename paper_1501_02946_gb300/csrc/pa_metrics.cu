@@ -111,7 +111,49 @@ __global__ void k_weight_grad(const float *__restrict__ g, const float *__restri
   if (lane == 0) grad_h[w] = float(s * double(__ldg(inv_h + w)));
 }
 
+__global__ void k_ratio(WeightRescale r) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= r.M) return;
+  const float hn = __ldg(r.h_new + m);
+  r.ratio[m] = hn * r.inv_h[m];
+  r.inv_h[m] = 1.f / hn;
+  if (r.lat_amp) r.lat_amp[m] *= r.ratio[m];
+}
+
+__global__ void k_scale_sorted(WeightRescale r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= r.M) return;
+  const float q = r.ratio[__ldg(r.perm + i)];
+  for (int t = 0; t < r.w; ++t) {
+    r.wy[(size_t)i * r.w + t] *= q;
+    r.dwy[(size_t)i * r.w + t] *= q;
+  }
+}
+
+__global__ void k_scale_entries(WeightRescale r) {
+  for (size_t e = blockIdx.x * size_t(blockDim.x) + threadIdx.x; e < r.n_entries; e += size_t(gridDim.x) * blockDim.x) {
+    const float q = r.ratio[__ldg(r.sp_m + e)];
+    float4 v = r.sp_w[e];
+    v.x *= q;
+    v.y *= q;
+    v.z *= q;
+    v.w *= q;
+    r.sp_w[e] = v;
+  }
+}
+
 }  // namespace
+
+cudaError_t rescale_weights(const WeightRescale &r, cudaStream_t s) {
+  const int b = (r.M + 255) / 256;
+  k_ratio<<<b, 256, 0, s>>>(r);
+  k_scale_sorted<<<b, 256, 0, s>>>(r);
+  if (r.n_entries) {
+    const size_t be = (r.n_entries + 255) / 256;
+    k_scale_entries<<<int(be < 4096 ? be : 4096), 256, 0, s>>>(r);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_weight_grad(const float *g, const float *gb, const float *inv_h, int M, int Nt, float *grad_h,
                                cudaStream_t s) {

@@ -214,6 +214,7 @@ struct pa_plan {
   // d = 2 operator (pa_plan_create_2d): Ny = 1, My = 1, sensors at (x_m, 0)
   bool d2 = false;
   float *d_invh = nullptr;        // [M] 1/h_m in the caller's order (static buffer)
+  size_t n_entries = 0;           // spread entries (sp_m / sp_w)
   // lattice path: sensors on the output lattice (see pa_plan_is_lattice)
   bool lattice_allowed = true;
   bool lattice = false;
@@ -359,6 +360,7 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
   for_each_entry([&](int st, int q, int, float, const float *) { sp_start[size_t(st) * My + q + 1]++; });
   for (size_t k = 0; k + 1 < sp_start.size(); ++k) sp_start[k + 1] += sp_start[k];
   const size_t nent = size_t(sp_start.back());
+  P->n_entries = nent;
   std::vector<int> sp_m(nent);
   std::vector<float4> sp_w(nent);
   {
@@ -1120,6 +1122,7 @@ int pa_plan_update_positions_device(pa_plan *plan, const float *xy_dev, void *st
     PA_CUDA(cudaMemcpy(h.status, &clear, sizeof(int), cudaMemcpyHostToDevice));
     return fail(PA_ERR_INVALID_ARG, "non-finite sensor position");
   }
+  P->n_entries = size_t(nent);
   // entry lists: [sp_start | sp_m | sp_w | order keys]
   size_t eo = 0;
   auto place = [&](size_t bytes) {
@@ -1311,6 +1314,42 @@ int pa_position_grad(pa_plan *plan, const float *g_dev, const float *grad_f_dev,
   io.g_out = grad_g_dev;
   io.grad_xy = grad_xy_dev;
   return run_adjoint(plan, io, reinterpret_cast<cudaStream_t>(stream), true);
+}
+
+int pa_plan_set_weights_device(pa_plan *plan, const float *h_dev, void *stream) {
+  g_err.clear();
+  if (!plan || !h_dev) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  pa_plan *P = plan;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int M = int(P->M);
+  std::vector<float> hh(static_cast<size_t>(M));
+  PA_CUDA(cudaMemcpyAsync(hh.data(), h_dev, sizeof(float) * hh.size(), cudaMemcpyDeviceToHost, s));
+  PA_CUDA(cudaStreamSynchronize(s));
+  for (int m = 0; m < M; ++m)
+    if (!(hh[size_t(m)] > 0.f) || !std::isfinite(hh[size_t(m)]))
+      return fail(PA_ERR_INVALID_ARG, "weights must be finite and > 0");
+  float *ratio = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void **>(&ratio), sizeof(float) * size_t(M), s) != cudaSuccess)
+    return fail(PA_ERR_OOM, "pa_plan_set_weights_device: scratch allocation failed");
+  pa::WeightRescale r{};
+  r.M = M;
+  r.w = P->w;
+  r.h_new = h_dev;
+  r.inv_h = P->d_invh;
+  r.ratio = ratio;
+  r.perm = P->h.perm;
+  r.wy = const_cast<float *>(P->h.wy);
+  r.dwy = const_cast<float *>(P->h.dwy);
+  r.n_entries = P->n_entries;
+  r.sp_m = P->h.sp_m;
+  r.sp_w = const_cast<float4 *>(P->h.sp_w);
+  r.lat_amp = const_cast<float *>(P->lat_amp);
+  cudaError_t e = pa::rescale_weights(r, s);
+  if (e == cudaSuccess) e = pa::build_interp_pack(P->h, s);
+  cudaFreeAsync(ratio, s);
+  if (e != cudaSuccess) return fail(PA_ERR_CUDA, std::string("set weights: ") + cudaGetErrorString(e));
+  for (int m = 0; m < M; ++m) P->weights[size_t(m)] = double(hh[size_t(m)]);
+  return PA_OK;
 }
 
 int pa_weight_grad(pa_plan *plan, const float *g_dev, const float *grad_f_dev, float *grad_h_dev, void *stream) {

@@ -111,3 +111,59 @@ def test_gradient_through_voronoi_weights_end_to_end():
     err = rel(got[idx], ref)
     print(f"gradient through Voronoi weights: rel L2 vs FD = {err:.3e}")
     assert err <= 1e-3
+
+
+def test_set_weights_matches_a_fresh_plan():
+    rng = np.random.default_rng(10)
+    P = synth.c1()
+    plan = pa().Plan(P.xy, P.n_t, P.dt, P.c, P.grid.as_tuple(), weights=P.h)
+    h = plan.voronoi_weights()
+    plan.set_weights(h)
+    fresh = pa().Plan(P.xy, P.n_t, P.dt, P.c, P.grid.as_tuple(), weights=host(h))
+    gd = dev(P.g)
+    assert rel(host(plan.reconstruct(gd)), host(fresh.reconstruct(gd))) <= 1e-6
+    fb = dev(rng.normal(size=P.grid.shape))
+    assert rel(host(plan.adjoint(fb)), host(fresh.adjoint(fb))) <= 1e-6
+    # on the lattice path too (lattice amplitudes rescaled)
+    xy = synth.lattice_positions(P.grid.nx, P.grid.ny, P.grid.dx, P.grid.dy)
+    pl = pa().Plan(xy, P.n_t, P.dt, P.c, P.grid.as_tuple())
+    assert pl.is_lattice
+    hw = rng.uniform(0.5, 1.5, xy.shape[0]) * P.grid.dx * P.grid.dy
+    pl.set_weights(dev(hw))
+    fr = pa().Plan(xy, P.n_t, P.dt, P.c, P.grid.as_tuple(), weights=hw)
+    g = dev(rng.normal(size=(xy.shape[0], P.n_t)))
+    assert rel(host(pl.reconstruct(g)), host(fr.reconstruct(g))) <= 1e-6
+
+
+def test_autograd_with_voronoi_weights():
+    """reconstruct(..., voronoi=True): the loss gradient to the positions
+    includes the weights' dependence on them (FP64 central differences of the
+    direct sums with Voronoi weights)."""
+    rng = np.random.default_rng(11)
+    grid = synth.Grid(10, 12, 16, 1e-4, 1e-4, 1e-4)
+    X, Y = grid.nx * grid.dx, grid.ny * grid.dy
+    xy0 = synth.jittered_lattice(rng, 10, 12, grid.dx, grid.dy, 0.3)
+    nt, dt, c = 32, 20e-9, 1500.0
+    g = rng.normal(size=(xy0.shape[0], nt))
+    fb = rng.normal(size=grid.shape)
+    plan = pa().Plan(xy0, nt, dt, c, grid.as_tuple())
+    xy = torch.tensor(xy0, dtype=torch.float64, requires_grad=True)
+    f = pa().reconstruct(dev(g), xy, plan, voronoi=True)
+    (f * dev(fb)).sum().backward()
+    got = xy.grad.numpy()
+
+    def L(p):
+        return float(np.vdot(fb, ndft.reconstruct(p, voronoi.areas_2d(reduce(p, X, Y), X, Y), g, dt, c, grid)))
+
+    eps = 1e-9
+    idx = rng.choice(xy0.shape[0], size=10, replace=False)
+    ref = np.zeros((10, 2))
+    for r, m in enumerate(idx):
+        for k in range(2):
+            a, b = xy0.copy(), xy0.copy()
+            a[m, k] += eps
+            b[m, k] -= eps
+            ref[r, k] = (L(a) - L(b)) / (2 * eps)
+    err = rel(got[idx], ref)
+    print(f"autograd with Voronoi weights: rel L2 vs FD = {err:.3e}")
+    assert err <= 1e-3
