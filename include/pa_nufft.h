@@ -302,7 +302,7 @@ int pa_status(pa_plan *plan, int *device_status, void *stream);
  * (4 or 8), columns per block and block size of the NER kernels (2 or 4
  * columns, 128 or 256 threads, as the shared memory and the transform plans
  * allow; only for plans on the block NER kernels, see PA_FLAG_BLOCK_NER)
- * and the tile height of the interpolation (16 or 32 columns).  The
+ * and the tile height of the interpolation (8, 16 or 32 columns).  The
  * forward results do not change (every shape sums in the same order); the
  * adjoint's shared-memory accumulation order follows the NER block shape, so
  * the adjoint and the gradient may change in the last bits.  Allocates a

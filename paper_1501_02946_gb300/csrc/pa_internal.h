@@ -56,7 +56,7 @@ struct InstDesc {
   int ner_threads;      // block size of the NER kernels (128 or 256)
   int ner_lperm;        // adjoint NER depth order il = (i * ner_lperm) mod Nz
   int spread_spl;       // samples per lane of the spread (4 or 8)
-  int interp_ty;        // grid columns per interpolation tile (16 or 32)
+  int interp_ty;        // grid columns per interpolation tile (8, 16 or 32)
   int ner_warp;         // 1: the NER stage runs the warp-per-column kernels
   int wtw;              // offset of the warp-transform twiddle tables in tw
 

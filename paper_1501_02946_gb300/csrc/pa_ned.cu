@@ -1145,6 +1145,7 @@ cudaError_t launch_interp_width(const Launch &L, int width, bool grad, int ty) {
   case W:                                                                                               \
     if (ty == 32) return grad ? launch_interp_w<W, 32, true>(L) : launch_interp_w<W, 32, false>(L);     \
     if (ty == 16) return grad ? launch_interp_w<W, 16, true>(L) : launch_interp_w<W, 16, false>(L);     \
+    if (ty == 8) return grad ? launch_interp_w<W, 8, true>(L) : launch_interp_w<W, 8, false>(L);        \
     return cudaErrorInvalidValue;
   switch (width) {
     PA_INTERP_W(6)

@@ -1245,7 +1245,7 @@ int pa_plan_autotune(pa_plan *plan, void *stream, int *choice) {
     {
       float best = 1e30f;
       int pick = h.interp_ty;
-      for (int ty : {16, 32}) {
+      for (int ty : {8, 16, 32}) {
         h.interp_ty = ty;
         if (pa::smem_interp(h) > P->smem_limit) continue;
         if ((rc = upload()) != PA_OK) break;
