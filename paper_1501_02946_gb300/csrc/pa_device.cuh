@@ -68,7 +68,8 @@ __device__ __forceinline__ ff ff_sqrt(ff a) {
   if (!(a.hi > 0.f)) return {0.f, 0.f};
   float s = sqrtf(a.hi);
   ff s2 = two_prod(s, s);
-  float r = ((a.hi - s2.hi) - s2.lo + a.lo) / (2.f * s);
+  // the correction is ~1e-8 of s: a two-ulp quotient is exact enough
+  float r = __fdividef((a.hi - s2.hi) - s2.lo + a.lo, 2.f * s);
   return quick_two_sum(s, r);
 }
 

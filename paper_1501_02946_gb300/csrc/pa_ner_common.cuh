@@ -33,7 +33,7 @@ __device__ __forceinline__ ff tau_of(const InstDesc &d, int jx, int jy, int l) {
 // W(j, l) = 2 c |kz| / |K| with W(0, 0) = 2c and W(j != 0, 0) = 0.
 __device__ __forceinline__ float weight_of(const InstDesc &d, ff tau, int l) {
   if (l == 0) return tau.hi == 0.f ? d.two_c : 0.f;
-  return d.two_c * d.sqrt_az * fabsf(float(l)) / fabsf(tau.hi);
+  return __fdividef(d.two_c * d.sqrt_az * fabsf(float(l)), fabsf(tau.hi));
 }
 
 // exp(-2 pi i tau nc / Nt) with the argument reduced in double-float.

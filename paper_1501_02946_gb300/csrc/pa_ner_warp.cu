@@ -101,10 +101,10 @@ __device__ __forceinline__ void warp_fft(float2 *scr, const float2 *__restrict__
 #pragma unroll
     for (int c = 0; c < E; ++c) {
       float2 t = v[c];
-      if (c > 0) {
-        float sn, cs;
-        sincospif(float(a * c) * (1.f / 16.f), &sn, &cs);
-        t = cmul(t, make_float2(cs, DIR * sn));
+      if (c > 0) {  // exp(DIR 2 pi i a c / 32): a picks one of three constants
+        const float wc = a == 1 ? Tw32::c(c) : (a == 2 ? Tw32::c(2 * c) : Tw32::c(3 * c));
+        const float ws = a == 1 ? Tw32::s(c) : (a == 2 ? Tw32::s(2 * c) : Tw32::s(3 * c));
+        if (a != 0) t = cmul(t, make_float2(wc, DIR * ws));
       }
       const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, t.x, 16), __shfl_xor_sync(0xffffffffu, t.y, 16));
       const float2 lo = low ? t : other, hi = low ? other : t;
