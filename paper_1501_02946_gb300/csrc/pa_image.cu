@@ -281,10 +281,18 @@ __global__ void __launch_bounds__(kThreadsImg) k_imgy_pipe(const InstDesc *__res
       fft_fixed<LGL, +1>(B, ZP, LGZP, lgT, tw, tid);
       float *fo = io.f_out + (size_t)x * L * Nz + z0;
       const int nv4 = nz >> 2;
-      for (int idx = tid; idx < L * nv4; idx += nthr) {
-        const int y = idx / nv4, k2 = idx - y * nv4;
-        *reinterpret_cast<float4 *>(fo + (size_t)y * Nz + 4 * k2) =
-            reinterpret_cast<const float4 *>(B + ((y - hy) & (L - 1)) * ZP)[k2];
+      if (nv4 == ZP / 2) {  // full chunk: index splits by shifts
+        for (int idx = tid; idx < L * (ZP / 2); idx += nthr) {
+          const int y = idx >> (LGZP - 1), k2 = idx & (ZP / 2 - 1);
+          *reinterpret_cast<float4 *>(fo + (size_t)y * Nz + 4 * k2) =
+              reinterpret_cast<const float4 *>(B + ((y - hy) & (L - 1)) * ZP)[k2];
+        }
+      } else {
+        for (int idx = tid; idx < L * nv4; idx += nthr) {
+          const int y = idx / nv4, k2 = idx - y * nv4;
+          *reinterpret_cast<float4 *>(fo + (size_t)y * Nz + 4 * k2) =
+              reinterpret_cast<const float4 *>(B + ((y - hy) & (L - 1)) * ZP)[k2];
+        }
       }
     } else {
       fft_fixed<LGL, -1>(buf, ZP, LGZP, lgT, tw, tid);

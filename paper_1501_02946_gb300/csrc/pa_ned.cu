@@ -562,9 +562,16 @@ __global__ void __launch_bounds__(kThreadsCol) k_rowifft_pipe(const InstDesc *__
     fft_fixed<LGL, +1>(S, NCP, LGNCP, lgT, tw, tid);
     float *G0 = d.G0 + (size_t)p * L * Nt + n0;
     const int nv4 = (min(2 * NCP, Nt - n0)) >> 2;
-    for (int idx = tid; idx < L * nv4; idx += nthr) {
-      const int q = idx / nv4, k2 = idx - q * nv4;
-      *reinterpret_cast<float4 *>(G0 + (size_t)q * Nt + 4 * k2) = reinterpret_cast<const float4 *>(S + q * NCP)[k2];
+    if (nv4 == NCP / 2) {  // full chunk: index splits by shifts
+      for (int idx = tid; idx < L * (NCP / 2); idx += nthr) {
+        const int q = idx >> (LGNCP - 1), k2 = idx & (NCP / 2 - 1);
+        *reinterpret_cast<float4 *>(G0 + (size_t)q * Nt + 4 * k2) = reinterpret_cast<const float4 *>(S + q * NCP)[k2];
+      }
+    } else {
+      for (int idx = tid; idx < L * nv4; idx += nthr) {
+        const int q = idx / nv4, k2 = idx - q * nv4;
+        *reinterpret_cast<float4 *>(G0 + (size_t)q * Nt + 4 * k2) = reinterpret_cast<const float4 *>(S + q * NCP)[k2];
+      }
     }
   };
   tile_pipeline(nwork, st0, st1, bars, d.status, issue, compute);
