@@ -380,6 +380,31 @@ def run_ours(args):
     d2_ms = timed_calls(d2_step, k_parts)
     plan_2.close()
     del g_2, f_2
+    # the position gradient (data gradient A^T fbar included) alone, and the
+    # variational workload on the same plan: L = ||A(xy) g - target||^2 +
+    # 1e-3 TV_eps(A(xy) g), eps = 1e-8 (isotropic, forward differences),
+    # target = the phantom's balls sampled at the voxel centres, backpropagated
+    # to g and xy through the autograd function (loss terms in torch, FP64 sums)
+    fb_v = torch.randn(P.grid.shape, device=dev, dtype=torch.float32)
+    pg_ms = timed_calls(lambda: plan.position_grad(g, fb_v), k_parts)
+    target_d = torch.tensor(P.voxelised(), dtype=torch.float32, device=dev)
+    xy_v = torch.tensor(P.xy, dtype=torch.float64, requires_grad=True)
+    g_v = g.detach().clone().requires_grad_(True)
+
+    def var_loss(fv):
+        fv = fv.to(torch.float64)
+        d0 = torch.diff(fv, dim=0, append=fv[-1:])
+        d1 = torch.diff(fv, dim=1, append=fv[:, -1:])
+        d2 = torch.diff(fv, dim=2, append=fv[:, :, -1:])
+        r = fv - target_d
+        return (r * r).sum() + 1e-3 * torch.sqrt(d0 * d0 + d1 * d1 + d2 * d2 + 1e-8).sum()
+
+    def var_step():
+        g_v.grad = None
+        xy_v.grad = None
+        var_loss(pa.reconstruct(g_v, xy_v, plan)).backward()
+    var_ms = timed_calls(var_step, k_parts)
+    del fb_v, target_d, g_v
     parts = {"forward": {"ms": fwd_ms, "voxels_per_s": voxels / (fwd_ms / 1e3)},
              "adjoint": {"ms": adj_ms, "voxels_per_s": voxels / (adj_ms / 1e3)},
              "cubic_baseline_forward": {"ms": cub_ms, "voxels_per_s": voxels / (cub_ms / 1e3)},
@@ -390,6 +415,11 @@ def run_ours(args):
              "d2_fwd_adj": {"ms": d2_ms, "pixels_per_s": nx2 * nz2 / (d2_ms / 1e3),
                             "workload": f"d = 2: {m2} sensors on a {X2 * 1e3:.1f} mm line, {nt2} samples at 20 ns, "
                                         f"image {nx2}x{nz2} at 100 um"},
+             "position_grad": {"ms": pg_ms, "voxels_per_s": voxels / (pg_ms / 1e3),
+                               "what": "pa_position_grad: A^T fbar and dL/dxy of <fbar, A(xy) g>"},
+             "variational_fwd_bwd": {"ms": var_ms, "voxels_per_s": voxels / (var_ms / 1e3),
+                                     "what": "L = ||A(xy) g - target||^2 + 1e-3 TV_eps(A(xy) g); forward, loss and "
+                                             "backward to g and xy through the autograd function"},
              "own_row_col_transforms_ms": (prof["ned_rowfft"][0] / prof["ned_rowfft"][1]
                                            + prof["ned_colfft"][0] / prof["ned_colfft"][1])
              if "ned_rowfft" in prof and "ned_colfft" in prof else None,
