@@ -361,6 +361,13 @@ int pa_plan_buffer(const pa_plan *plan, int which, void *dst_dev, int64_t capaci
  */
 #define PA_PROFILE_STAGES 17
 int pa_profile_enable(pa_plan *plan, int enable);
+/*
+ * Events around the launches of the selected stages only (bit k = stage k;
+ * 0 switches profiling off, as pa_profile_enable(plan, 0) does).  Each event
+ * pair sits between two kernels of the stream, so a timing run that brackets
+ * one stage disturbs the others' back-to-back launches least.
+ */
+int pa_profile_select(pa_plan *plan, uint32_t stage_mask);
 int pa_profile_read(pa_plan *plan, double *ms_total, int64_t *launches);
 const char *pa_profile_stage_name(int stage);
 

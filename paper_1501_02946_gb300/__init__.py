@@ -255,9 +255,23 @@ class Plan:
                                  _stream_ptr(self.device)))
         return out
 
-    def profile(self, enable=True):
-        """Record CUDA events around every kernel launch of this plan."""
-        check(_lib.load().pa_profile_enable(self.handle, 1 if enable else 0))
+    def profile(self, enable=True, stages=None):
+        """Record CUDA events around every kernel launch of this plan, or
+        (stages: names from profile_read) around those stages' launches only."""
+        if stages is None:
+            check(_lib.load().pa_profile_enable(self.handle, 1 if enable else 0))
+            return
+        lib = _lib.load()
+        names, n = {}, 0
+        while lib.pa_profile_stage_name(n):
+            names[lib.pa_profile_stage_name(n).decode()] = n
+            n += 1
+        mask = 0
+        for st in stages:
+            if st not in names:
+                raise ValueError(f"unknown stage {st!r}")
+            mask |= 1 << names[st]
+        check(lib.pa_profile_select(self.handle, mask if enable else 0))
 
     def profile_read(self):
         """{stage name: (total ms, launches)} since the last read (waits for

@@ -63,6 +63,7 @@ SIGNATURES = {
     "pa_plan_info": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64)]),
     "pa_plan_buffer": (c_int, [c_void_p, c_int, c_void_p, c_int64, POINTER(c_int64), c_void_p]),
     "pa_profile_enable": (c_int, [c_void_p, c_int]),
+    "pa_profile_select": (c_int, [c_void_p, ctypes.c_uint32]),
     "pa_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64)]),
     "pa_profile_stage_name": (c_char_p, [c_int]),
     "pa_last_error": (c_char_p, []),

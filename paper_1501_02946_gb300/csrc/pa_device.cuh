@@ -4,11 +4,30 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
 
 #include <cuda.h>
 #include "pa_internal.h"
 
+// Programmatic dependent launch of the single-plan pipeline kernels (0: the
+// same kernels launched the ordinary way).
+#ifndef PA_PDL
+#define PA_PDL 1
+#endif
+
 namespace pa {
+
+// Programmatic dependent launch.  A kernel started by launch_pdl may be
+// scheduled while the previous kernel of its stream drains.  Its first
+// statement is griddep_enter(): griddepcontrol.wait returns once that kernel
+// has completed and its memory operations are visible (at once for a kernel
+// launched the ordinary way), and griddepcontrol.launch_dependents then lets
+// the next kernel of the stream be scheduled early in the same way.  The
+// previous kernel never waits for its dependents, so no wait can cycle.
+__device__ __forceinline__ void griddep_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // ---------------------------------------------------------------- complex
 // Complex sums as packed two-wide FP32 adds (sm_100+; each component rounds
@@ -661,6 +680,29 @@ static cudaError_t launch_persistent(K kernel, const Launch &L, int threads, siz
   return cudaGetLastError();
 }
 
+// Launch with the programmatic-stream-serialization attribute (the kernel
+// must begin with griddep_enter()); an ordinary launch while the stream is
+// being captured into a graph.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int threads, size_t smem, cudaStream_t s,
+                              Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(unsigned(threads));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 0;
+  if (PA_PDL) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusActive;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Opt-in shared memory per block of the current device (read once).
 static inline size_t smem_optin_limit() {
   static int v = -1;
@@ -682,8 +724,7 @@ static cudaError_t launch_persistent_map(K kernel, const Launch &L, int threads,
     if (e != cudaSuccess) return e;
   }
   const int grid = persistent_grid(kernel, threads, smem, nwork);
-  kernel<<<grid, threads, smem, L.stream>>>(L.descs, nwork, map, use_map);
-  return cudaGetLastError();
+  return launch_pdl(kernel, grid, threads, smem, L.stream, L.descs, nwork, map, use_map);
 }
 
 static inline int pow2_log(int n) {

@@ -159,6 +159,7 @@ __global__ void __launch_bounds__(kThreadsImg) k_imgy(const InstDesc *__restrict
 template <bool ADJ, int LGL>
 __global__ void __launch_bounds__(kThreadsImg) k_imgx_pipe(const InstDesc *__restrict__ descs, int nwork,
                                                            const __grid_constant__ CUtensorMap map, int use_map) {
+  griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
   __shared__ __align__(8) uint64_t bars[2];
   constexpr int L = 1 << LGL, ZC = kImgZC, LGZC = 4;
@@ -210,6 +211,7 @@ __global__ void __launch_bounds__(kThreadsImg) k_imgx_pipe(const InstDesc *__res
 template <bool ADJ, int LGL>
 __global__ void __launch_bounds__(kThreadsImg) k_imgy_pipe(const InstDesc *__restrict__ descs, int nwork, IoPtrs io,
                                                            const __grid_constant__ CUtensorMap map, int use_map) {
+  griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
   __shared__ __align__(8) uint64_t bars[2];
   constexpr int L = 1 << LGL, ZP = kImgZP, LGZP = 4;
@@ -367,8 +369,7 @@ static cudaError_t launch_persistent_io(K kernel, const Launch &L, size_t smem, 
     if (e != cudaSuccess) return e;
   }
   const int grid = persistent_grid(kernel, kThreadsImg, smem, nwork);
-  kernel<<<grid, kThreadsImg, smem, L.stream>>>(L.descs, nwork, L.io, map, use_map);
-  return cudaGetLastError();
+  return launch_pdl(kernel, grid, kThreadsImg, smem, L.stream, L.descs, nwork, L.io, map, use_map);
 }
 
 cudaError_t launch_imgy(const Launch &L, bool adjoint) {

@@ -89,6 +89,7 @@ template <int S>
 __global__ void __launch_bounds__(kThreadsSpread, 2) k_spread(const InstDesc *__restrict__ descs,
                                                               const int2 *__restrict__ work, IoPtrs io0,
                                                               const IoPtrs *__restrict__ io_table) {
+  griddep_enter();  // the previous kernel of the stream has completed
   constexpr int P = kSpreadP, QC = kThreadsSpread / 32, CH = 32 * S;
   static_assert(P == 4, "tap products hold four rows");
   static_assert(S % 4 == 0, "samples per lane load as float4");
@@ -327,6 +328,7 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft(const InstDesc *__restri
 template <bool ADJ, int LGL>
 __global__ void __launch_bounds__(kThreadsCol) k_colfft_pipe(const InstDesc *__restrict__ descs, int nwork,
                                                              const __grid_constant__ CUtensorMap map, int use_map) {
+  griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
   __shared__ __align__(8) uint64_t bars[2];
   constexpr int L = 1 << LGL, NC = kColNC, LGNC = 4, BOX = L < 256 ? L : 256;
@@ -400,6 +402,7 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft_pipe(const InstDesc *__r
 template <int LGL>
 __global__ void __launch_bounds__(kThreadsCol) k_rowfft_pipe(const InstDesc *__restrict__ descs, int nwork,
                                                              const __grid_constant__ CUtensorMap map, int use_map) {
+  griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
   __shared__ __align__(8) uint64_t bars[2];
   constexpr int L = 1 << LGL, NCP = 16, LGNCP = 4, BOX = L < 256 ? L : 256;
@@ -511,6 +514,7 @@ __global__ void __launch_bounds__(kThreadsCol) k_rowifft(const InstDesc *__restr
 template <int LGL>
 __global__ void __launch_bounds__(kThreadsCol) k_rowifft_pipe(const InstDesc *__restrict__ descs, int nwork,
                                                               const __grid_constant__ CUtensorMap map, int use_map) {
+  griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
   __shared__ __align__(8) uint64_t bars[2];
   constexpr int L = 1 << LGL, NCP = 16, LGNCP = 4;
@@ -749,6 +753,7 @@ template <int W, int TY, bool GRAD, int NS>
 __global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS) k_interp_pipe(const InstDesc *__restrict__ descs, IoPtrs io,
                                                                 int nwork, const __grid_constant__ CUtensorMap g0map,
                                                                 int use_map) {
+  griddep_enter();  // the previous kernel of the stream has completed
   using S = InterpPipe<W, TY, GRAD, NS>;
   constexpr int TX = S::TX, HX = S::HX, HY = S::HY, NC = S::NC, CELLS = S::CELLS, SMAX = S::SMAX;
   constexpr int PW = S::PW, PD = S::PD;
@@ -1012,14 +1017,9 @@ static cudaError_t set_smem(K kernel, size_t smem) {
 }
 
 cudaError_t launch_spread(const Launch &L, int spl) {
-  if (spl == 8) {
-    k_spread<8><<<L.nblocks, kThreadsSpread, 0, L.stream>>>(L.descs, L.work, L.io, L.io_table);
-  } else if (spl == 4) {
-    k_spread<4><<<L.nblocks, kThreadsSpread, 0, L.stream>>>(L.descs, L.work, L.io, L.io_table);
-  } else {
-    return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  if (spl == 8) return launch_pdl(k_spread<8>, L.nblocks, kThreadsSpread, 0, L.stream, L.descs, L.work, L.io, L.io_table);
+  if (spl == 4) return launch_pdl(k_spread<4>, L.nblocks, kThreadsSpread, 0, L.stream, L.descs, L.work, L.io, L.io_table);
+  return cudaErrorInvalidValue;
 }
 
 // The persistent kernels are instantiated for lengths 2^5 .. 2^9 (two tile
@@ -1124,8 +1124,7 @@ static bool launch_interp_pipe(const Launch &L, cudaError_t &err) {
   const int use_map = encode_g0_box(h, IP::HX, IP::HY, &map) ? 1 : 0;
   const int nwork = blocks_interp(h);
   const int grid = persistent_grid(kp, IP::THREADS, IP::smem, nwork);
-  kp<<<grid, IP::THREADS, IP::smem, L.stream>>>(L.descs, L.io, nwork, map, use_map);
-  err = cudaGetLastError();
+  err = launch_pdl(kp, grid, IP::THREADS, IP::smem, L.stream, L.descs, L.io, nwork, map, use_map);
   return true;
 }
 

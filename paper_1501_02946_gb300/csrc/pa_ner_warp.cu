@@ -198,6 +198,7 @@ __device__ __forceinline__ void flush_point(float2 *He, float2 *Ho, int pu, int 
 template <int LGT, int LGZ, int W>
 __global__ void __launch_bounds__(128, LGT <= 9 ? PA_NER_FWD_MINB : 1) k_ner_warp(const InstDesc *__restrict__ descs,
                                                   const __grid_constant__ HornerTable ht) {
+  griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ float4 smem_f4[];
   constexpr int Nt = 1 << LGT, Nz = 1 << LGZ;
   constexpr int HH = NerWarpShape<LGT, W>::HH, FS = NerWarpFs<LGZ>::FS;
@@ -268,6 +269,7 @@ __global__ void __launch_bounds__(128, LGT <= 9 ? PA_NER_FWD_MINB : 1) k_ner_war
 template <int LGT, int LGZ, int W>
 __global__ void __launch_bounds__(128, PA_NER_ADJ_MINB) k_ner_warp_adj(const InstDesc *__restrict__ descs,
                                                       const __grid_constant__ HornerTable ht) {
+  griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ float4 smem_f4[];
   constexpr int Nt = 1 << LGT, Nz = 1 << LGZ;
   constexpr int HH = NerWarpShape<LGT, W>::HH, FS = NerWarpFs<LGZ>::FS;
@@ -408,8 +410,7 @@ cudaError_t launch_warp_kernel(K kernel, const Launch &L, const InstDesc &h, int
     if (e != cudaSuccess) return e;
   }
   const int nblocks = (nslots + nw - 1) / nw;
-  kernel<<<nblocks, nw * 32, smem, L.stream>>>(L.descs, ht);
-  return cudaGetLastError();
+  return launch_pdl(kernel, nblocks, nw * 32, smem, L.stream, L.descs, ht);
 }
 
 template <int LGT, int LGZ>

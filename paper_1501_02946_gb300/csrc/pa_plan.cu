@@ -224,7 +224,7 @@ struct pa_plan {
   const int *lat_pq = nullptr;
   const float *lat_amp = nullptr;
   // optional per-stage event timing
-  bool profiling = false;
+  uint32_t profile_mask = 0;  // stages whose launches are bracketed by events
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
 };
@@ -454,17 +454,19 @@ cudaEvent_t take_event(pa_plan *P) {
   return e;
 }
 
-// Launch `fn` on stream s; with profiling on, bracket it with events.
+// Launch `fn` on stream s; with profiling on for the stage, bracket it with
+// events.
 template <typename Fn>
 int timed(pa_plan *P, int stage, cudaStream_t s, Fn fn, const char *what) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (P->profiling) {
+  const bool prof = (P->profile_mask >> stage) & 1u;
+  if (prof) {
     e0 = take_event(P);
     e1 = take_event(P);
     if (e0) cudaEventRecord(e0, s);
   }
   int rc = check_launch(fn(), what);
-  if (P->profiling && e0 && e1) {
+  if (prof && e0 && e1) {
     cudaEventRecord(e1, s);
     P->ev_used.push_back({stage, {e0, e1}});
   }
@@ -1414,7 +1416,14 @@ int pa_voronoi_grad(pa_plan *plan, const float *grad_h_dev, float *grad_xy_dev, 
 int pa_profile_enable(pa_plan *plan, int enable) {
   g_err.clear();
   if (!plan) return fail(PA_ERR_INVALID_ARG, "plan is NULL");
-  plan->profiling = enable != 0;
+  plan->profile_mask = enable ? (1u << PA_PROFILE_STAGES) - 1u : 0u;
+  return PA_OK;
+}
+
+int pa_profile_select(pa_plan *plan, uint32_t stage_mask) {
+  g_err.clear();
+  if (!plan) return fail(PA_ERR_INVALID_ARG, "plan is NULL");
+  plan->profile_mask = stage_mask & ((1u << PA_PROFILE_STAGES) - 1u);
   return PA_OK;
 }
 
