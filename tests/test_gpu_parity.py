@@ -288,6 +288,32 @@ def test_autotune_keeps_results(name):
     assert rel(after[2], before[2]) <= 1e-5
 
 
+def test_profile_selected_stages():
+    """Events around every launch, around the selected stages only, or none;
+    the results do not depend on it."""
+    P = synth.c1()
+    plan = plan_of(P)
+    g = dev(P.g)
+    f0 = host(plan.reconstruct(g))
+    plan.profile(True)
+    f1 = plan.reconstruct(g)
+    plan.adjoint(f1)
+    every = plan.profile_read()
+    assert {"ned_spread", "ner_fused", "ner_adj", "ned_interp"} <= set(every)
+    plan.profile(True, stages=["ned_interp"])
+    plan.reconstruct(g)
+    plan.adjoint(f1)
+    sel = plan.profile_read()
+    assert set(sel) == {"ned_interp"}
+    assert sel["ned_interp"][1] == 1 and sel["ned_interp"][0] > 0
+    plan.profile(False)
+    plan.reconstruct(g)
+    assert plan.profile_read() == {}
+    assert np.array_equal(f0, host(f1))
+    with pytest.raises(ValueError):
+        plan.profile(True, stages=["no_such_stage"])
+
+
 # ---------------------------------------------------------- edge cases
 def test_positions_wrap_by_period():
     P = synth.c1()

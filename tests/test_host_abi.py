@@ -91,3 +91,5 @@ def test_null_plan_calls_are_errors(lib):
     assert lib.pa_position_grad(None, None, None, None, None, None) == 1
     assert lib.pa_plan_destroy(None) == 0
     assert lib.pa_batch_destroy(None) == 0
+    assert lib.pa_profile_enable(None, 1) == 1
+    assert lib.pa_profile_select(None, 1) == 1
