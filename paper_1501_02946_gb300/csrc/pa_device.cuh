@@ -587,7 +587,13 @@ __device__ __forceinline__ bool tile_pipeline(int nwork, float2 *buf0, float2 *b
 
 // The same loop with NS buffers: the copies of the next NS - 1 items are in
 // flight while item i is computed in buffer i mod NS (buffer b at
-// buf + b * stride floats2; barrier b at bars[b]).
+// buf + b * stride floats2; barrier b at bars[b]).  One block barrier per
+// item: a warp computes as soon as its own wait on the item's mbarrier has
+// returned (the landed bytes are then visible to it), so the warps need not
+// wait for the thread that issues the next copies.  What issue() writes to
+// shared memory for item w is read by compute(w) only after the barrier that
+// ends the previous item (or the one after the first issues).  compute() may
+// not contain block barriers.
 template <int NS, typename Issue, typename Compute>
 __device__ __forceinline__ bool tile_pipeline_n(int nwork, float2 *buf, size_t stride, uint64_t *bars, int *status,
                                                 Issue issue, Compute compute) {
@@ -602,6 +608,7 @@ __device__ __forceinline__ bool tile_pipeline_n(int nwork, float2 *buf, size_t s
     const int w = blockIdx.x + k * gridDim.x;
     if (w < nwork) issue(w, buf + k * stride, &bars[k]);
   }
+  __syncthreads();  // what the first issues wrote to shared memory
 #pragma unroll 1
   for (int i = 0;; ++i) {
     const int w = blockIdx.x + i * gridDim.x;
@@ -614,7 +621,9 @@ __device__ __forceinline__ bool tile_pipeline_n(int nwork, float2 *buf, size_t s
       issue(wn, buf + sn * stride, &bars[sn]);
     }
     const uint32_t par = uint32_t(i / NS) & 1u;
-    const bool ok = mbar_wait(&bars[s], par);
+    // warp-uniform, so that compute() keeps its shuffles whole
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars[s], par));
+    if (ok) compute(w, buf + s * stride);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) atomicOr(status, kStatusWaitTimeout);
       // one more bounded wait for every copy still in flight
@@ -624,8 +633,6 @@ __device__ __forceinline__ bool tile_pipeline_n(int nwork, float2 *buf, size_t s
       }
       return false;
     }
-    compute(w, buf + s * stride);
-    __syncthreads();
   }
   return true;
 }

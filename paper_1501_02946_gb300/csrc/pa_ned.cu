@@ -15,6 +15,12 @@
 #include "pa_device.cuh"
 #include "pa_tmap.h"
 
+// Blocks per SM the pipelined interpolation's register budget is set for
+// (its two 54 KB stages allow two).
+#ifndef PA_INTERP_MINB
+#define PA_INTERP_MINB 2
+#endif
+
 namespace pa {
 
 namespace {
@@ -750,7 +756,7 @@ struct InterpPipe {
 };
 
 template <int W, int TY, bool GRAD, int NS>
-__global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS) k_interp_pipe(const InstDesc *__restrict__ descs, IoPtrs io,
+__global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS, PA_INTERP_MINB) k_interp_pipe(const InstDesc *__restrict__ descs, IoPtrs io,
                                                                 int nwork, const __grid_constant__ CUtensorMap g0map,
                                                                 int use_map) {
   griddep_enter();  // the previous kernel of the stream has completed
