@@ -26,6 +26,7 @@ constexpr int kD2Samples = 4;   // samples per lane in the spread
 constexpr int kD2Threads = 256;
 
 __global__ void __launch_bounds__(kD2Threads) k_spread_x(const InstDesc *__restrict__ descs, IoPtrs io) {
+  griddep_enter();  // the previous kernel of the stream has completed
   const InstDesc &d = descs[0];
   const int Mx = d.Mx, Nt = d.Nt, w = d.w;
   const int nstrips = (Mx + kD2Rows - 1) / kD2Rows;
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(kD2Threads) k_spread_x(const InstDesc *__restr
 // One warp per (sorted sensor i, 32 samples), lane = sample.
 template <bool GRAD>
 __global__ void __launch_bounds__(kD2Threads) k_interp_x(const InstDesc *__restrict__ descs, IoPtrs io) {
+  griddep_enter();  // the previous kernel of the stream has completed
   const InstDesc &d = descs[0];
   const int Mx = d.Mx, Nt = d.Nt, w = d.w, M = d.M;
   const int nch = (Nt + 31) / 32;
@@ -116,6 +118,7 @@ __global__ void __launch_bounds__(kD2Threads) k_interp_x(const InstDesc *__restr
 }
 
 __global__ void k_real_out(const InstDesc *__restrict__ descs, IoPtrs io) {
+  griddep_enter();  // the previous kernel of the stream has completed
   const InstDesc &d = descs[0];
   const size_t n = size_t(d.Nx) * d.Nz;
   for (size_t k = blockIdx.x * size_t(blockDim.x) + threadIdx.x; k < n; k += size_t(gridDim.x) * blockDim.x)
@@ -123,6 +126,7 @@ __global__ void k_real_out(const InstDesc *__restrict__ descs, IoPtrs io) {
 }
 
 __global__ void k_real_in(const InstDesc *__restrict__ descs, IoPtrs io) {
+  griddep_enter();  // the previous kernel of the stream has completed
   const InstDesc &d = descs[0];
   const size_t n = size_t(d.Nx) * d.Nz;
   for (size_t k = blockIdx.x * size_t(blockDim.x) + threadIdx.x; k < n; k += size_t(gridDim.x) * blockDim.x)
@@ -138,29 +142,22 @@ int grid_of(size_t threads) {
 
 cudaError_t launch_spread_x(const Launch &L, const InstDesc &h) {
   const size_t warps = size_t((h.Mx + kD2Rows - 1) / kD2Rows) * ((h.Nt + 32 * kD2Samples - 1) / (32 * kD2Samples));
-  k_spread_x<<<int((warps * 32 + kD2Threads - 1) / kD2Threads), kD2Threads, 0, L.stream>>>(L.descs, L.io);
-  return cudaGetLastError();
+  return launch_pdl(k_spread_x, int((warps * 32 + kD2Threads - 1) / kD2Threads), kD2Threads, 0, L.stream, L.descs, L.io);
 }
 
 cudaError_t launch_interp_x(const Launch &L, const InstDesc &h, bool grad) {
   const size_t warps = size_t(h.M) * ((h.Nt + 31) / 32);
   const int blocks = int((warps * 32 + kD2Threads - 1) / kD2Threads);
-  if (grad) {
-    k_interp_x<true><<<blocks, kD2Threads, 0, L.stream>>>(L.descs, L.io);
-  } else {
-    k_interp_x<false><<<blocks, kD2Threads, 0, L.stream>>>(L.descs, L.io);
-  }
-  return cudaGetLastError();
+  return grad ? launch_pdl(k_interp_x<true>, blocks, kD2Threads, 0, L.stream, L.descs, L.io)
+              : launch_pdl(k_interp_x<false>, blocks, kD2Threads, 0, L.stream, L.descs, L.io);
 }
 
 cudaError_t launch_real_out(const Launch &L, const InstDesc &h) {
-  k_real_out<<<grid_of(size_t(h.Nx) * h.Nz), kD2Threads, 0, L.stream>>>(L.descs, L.io);
-  return cudaGetLastError();
+  return launch_pdl(k_real_out, grid_of(size_t(h.Nx) * h.Nz), kD2Threads, 0, L.stream, L.descs, L.io);
 }
 
 cudaError_t launch_real_in(const Launch &L, const InstDesc &h) {
-  k_real_in<<<grid_of(size_t(h.Nx) * h.Nz), kD2Threads, 0, L.stream>>>(L.descs, L.io);
-  return cudaGetLastError();
+  return launch_pdl(k_real_in, grid_of(size_t(h.Nx) * h.Nz), kD2Threads, 0, L.stream, L.descs, L.io);
 }
 
 }  // namespace pa

@@ -705,7 +705,10 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int threads, s
   cfg.numAttrs = 0;
   if (PA_PDL) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusActive;
-    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) cfg.numAttrs = 1;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess)
+      (void)cudaGetLastError();  // the query's own error: launch the ordinary way
+    else if (cs == cudaStreamCaptureStatusNone)
+      cfg.numAttrs = 1;
   }
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }

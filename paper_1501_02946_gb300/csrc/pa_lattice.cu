@@ -22,6 +22,7 @@ constexpr int kThreadsLattice = 256;
 // G0[pq[m]][n] = a[m] g[m][n]
 __global__ void k_lattice_scatter(float *__restrict__ G0, const int *__restrict__ pq, const float *__restrict__ a,
                                   const float *__restrict__ g, int M, int Nt) {
+  griddep_enter();  // the previous kernel of the stream has completed
   const size_t total = size_t(M) * Nt;
   const bool vec = (Nt & 3) == 0 && ((reinterpret_cast<uintptr_t>(g) & 15u) == 0);
   if (vec) {
@@ -43,6 +44,7 @@ __global__ void k_lattice_scatter(float *__restrict__ G0, const int *__restrict_
 // g[m][n] = a[m] G0b[pq[m]][n]
 __global__ void k_lattice_gather(float *__restrict__ g, const float *__restrict__ G0, const int *__restrict__ pq,
                                  const float *__restrict__ a, int M, int Nt) {
+  griddep_enter();  // the previous kernel of the stream has completed
   const size_t total = size_t(M) * Nt;
   const bool vec = (Nt & 3) == 0 && ((reinterpret_cast<uintptr_t>(g) & 15u) == 0);
   if (vec) {
@@ -65,6 +67,7 @@ __global__ void k_lattice_gather(float *__restrict__ g, const float *__restrict_
 // G1[jx + hx][jy][n] are one bin at sigma = 1.  dir 0: copy 0 -> 2hx;
 // dir 1: add the cotangent of 2hx into 0.
 __global__ void k_lattice_alias(float2 *G1, int nY1, int Nt, int hx, int dir) {
+  griddep_enter();  // the previous kernel of the stream has completed
   const size_t row = size_t(nY1) * Nt;
   float2 *r0 = G1, *r1 = G1 + size_t(2 * hx) * row;
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < row; i += size_t(gridDim.x) * blockDim.x) {
@@ -85,19 +88,16 @@ int grid_for(size_t n) {
 
 cudaError_t launch_lattice_scatter(float *G0, const int *pq, const float *a, const float *g, int M, int Nt,
                                    cudaStream_t s) {
-  k_lattice_scatter<<<grid_for(size_t(M) * Nt / 4), kThreadsLattice, 0, s>>>(G0, pq, a, g, M, Nt);
-  return cudaGetLastError();
+  return launch_pdl(k_lattice_scatter, grid_for(size_t(M) * Nt / 4), kThreadsLattice, 0, s, G0, pq, a, g, M, Nt);
 }
 
 cudaError_t launch_lattice_gather(float *g, const float *G0, const int *pq, const float *a, int M, int Nt,
                                   cudaStream_t s) {
-  k_lattice_gather<<<grid_for(size_t(M) * Nt / 4), kThreadsLattice, 0, s>>>(g, G0, pq, a, M, Nt);
-  return cudaGetLastError();
+  return launch_pdl(k_lattice_gather, grid_for(size_t(M) * Nt / 4), kThreadsLattice, 0, s, g, G0, pq, a, M, Nt);
 }
 
 cudaError_t launch_lattice_alias(float2 *G1, int nY1, int Nt, int hx, int dir, cudaStream_t s) {
-  k_lattice_alias<<<grid_for(size_t(nY1) * Nt), kThreadsLattice, 0, s>>>(G1, nY1, Nt, hx, dir);
-  return cudaGetLastError();
+  return launch_pdl(k_lattice_alias, grid_for(size_t(nY1) * Nt), kThreadsLattice, 0, s, G1, nY1, Nt, hx, dir);
 }
 
 }  // namespace pa
