@@ -32,7 +32,11 @@
  *  - Device buffers ("*_dev") are owned by the caller, live on the device the
  *    plan was created on, are not aliased with each other, and are dense
  *    C-order FP32 arrays.  Calls are asynchronous and ordered on `stream`
- *    (a cudaStream_t; NULL means the legacy default stream).
+ *    (a cudaStream_t; NULL means the legacy default stream).  A call's
+ *    kernels may be scheduled while the previous kernel of the stream
+ *    drains (programmatic dependent launch), but none touches memory before
+ *    that kernel has completed, so work queued before a call, the caller's
+ *    own kernels included, is seen by it as with ordinary launches.
  *  - A plan owns its device workspace and tables; it is not safe to run one
  *    plan on two streams at the same time.
  */
