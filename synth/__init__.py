@@ -162,28 +162,33 @@ def ball_signal(xy, t, ball, c):
     return np.where(np.abs(s) < R, p0 * s / (2.0 * r), 0.0)
 
 
-def balls_data(xy, n_t, dt, balls, c):
+def balls_data(xy, n_t, dt, balls, c, chunk=1024):
     """Sum of closed-form ball signals (linear superposition), float64.
 
-    Only the samples with |r - c t_n| < R are touched, so many small balls are
-    cheap.
+    Only the samples with |r - c t_n| < R are touched: per ball, each sensor's
+    K candidate samples n_lo .. n_lo + K - 1 (n_lo = ceil((r - R) / (c dt)))
+    are evaluated at once as an array, for blocks of `chunk` sensors whose
+    rows of g stay in cache while every ball is added (in ball order).
     """
     M = xy.shape[0]
     g = np.zeros((M, n_t))
-    rows = np.arange(M)
-    for (bx, by, bz, R, p0) in balls:
-        r = np.sqrt((xy[:, 0] - bx) ** 2 + (xy[:, 1] - by) ** 2 + bz ** 2)
-        n_lo = np.ceil((r - R) / (c * dt)).astype(np.int64)
-        K = int(math.ceil(2 * R / (c * dt))) + 2
-        for k in range(K):
-            n = n_lo + k
-            t = n * dt
-            s = r - c * t
-            ok = (np.abs(s) < R) & (n >= 0) & (n < n_t)
-            if not ok.any():
+    for a in range(0, M, chunk):
+        b = min(M, a + chunk)
+        gc = g[a:b]
+        xs, ys = xy[a:b, 0], xy[a:b, 1]
+        for (bx, by, bz, R, p0) in balls:
+            r = np.sqrt((xs - bx) ** 2 + (ys - by) ** 2 + bz ** 2)
+            n_lo = np.ceil((r - R) / (c * dt)).astype(np.int64)
+            K = int(math.ceil(2 * R / (c * dt))) + 2
+            live = np.nonzero((n_lo < n_t) & (n_lo + K > 0))[0]
+            if live.size == 0:
                 continue
-            m = rows[ok]
-            g[m, n[ok]] += p0 * s[ok] / (2.0 * r[ok])
+            rl = r[live][:, None]
+            n = n_lo[live][:, None] + np.arange(K)[None, :]
+            s = rl - c * (n * dt)
+            ok = (np.abs(s) < R) & (n >= 0) & (n < n_t)
+            m = np.broadcast_to(live[:, None], n.shape)[ok]
+            gc[m, n[ok]] += p0 * s[ok] / (2.0 * np.broadcast_to(rl, n.shape)[ok])
     return g
 
 
