@@ -181,7 +181,14 @@ def position_grad(xy, h, g, fbar, dt, c, grid):
     G1bar the cotangent of G1 from the transposed chain."""
     nt = g.shape[1]
     _, aux = reconstruct_adjoint(xy, h, fbar, dt, c, grid, nt, full=True)
-    G1bar = aux["G1bar"]
+    return position_grad_from_cotangent(xy, h, g, aux["G1bar"], grid)
+
+
+def position_grad_from_cotangent(xy, h, g, G1bar, grid):
+    """The last step of position_grad: dL/dx_m and dL/dy_m from the cotangent
+    G1bar(j, n) of the spatial spectrum (on the index sets of Sec. 2), for the
+    sensors xy given (any subset: each row depends on its own sensor only)."""
+    nt = g.shape[1]
     a = h / (grid.dx * grid.dy)
     kx, ky, _ = wavenumbers(grid)
     Ex, Ey = spatial_factors(xy, grid)

@@ -145,6 +145,25 @@ def tau_of(grid, c, dt, nt):
     return omega * nt * dt / (2 * np.pi), W
 
 
+def spectrum_cotangent(fbar, dt, c, grid, nt, sigma=2, width=16, rows=None):
+    """G1bar(j, n): the cotangent of the spatial spectrum G1 in the transposed
+    chain of reconstruct -- the image adjoint, the weight (dt/dz) W and the NER
+    adjoint, i.e. reconstruct_adjoint without its last (NED) step -- on the
+    full index sets, shape (nx, ny, nt).  With `rows`, the NER adjoint takes
+    that many jx rows at a time (each column is independent, so the values
+    are the same; only the memory held at once is smaller)."""
+    tau, W = tau_of(grid, c, dt, nt)
+    Fbar = ndft.image_transform_adjoint(fbar, grid)
+    Ghatbar = (dt / grid.dz) * W * Fbar
+    del Fbar
+    if rows is None:
+        return ner_adjoint(Ghatbar, tau, nt, sigma, width)
+    out = np.empty(Ghatbar.shape[:2] + (nt,), dtype=np.complex128)
+    for a in range(0, Ghatbar.shape[0], rows):
+        out[a:a + rows] = ner_adjoint(Ghatbar[a:a + rows], tau[a:a + rows], nt, sigma, width)
+    return out
+
+
 def reconstruct(xy, h, g, dt, c, grid, sigma=2, width=16, full=False):
     nt = g.shape[1]
     G1 = ned(xy, h, g, grid, sigma, width)

@@ -197,6 +197,46 @@ def test_half_spectrum_voxels_round_trip(shape):
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("shape,nt", [((8, 8, 16), 32), ((7, 9, 11), 24)])
+def test_spectrum_cotangent_and_sampled_sensor_helpers(shape, nt):
+    """The helpers of the sampled full-size checks: the cotangent G1bar from
+    the image adjoint, the weight and O2's NER adjoint (width 16, any number
+    of jx rows at a time) equals O1's transposed chain; the O1 adjoint and
+    the analytic gradient evaluated for a subset of the sensors equal the
+    corresponding rows of the full evaluations; and the gradient of a subset
+    matches FP64 central differences of the loss for that subset alone."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(13)
+    grid = synth.Grid(nx, ny, nz, 1e-4, 1.1e-4, 0.9e-4)
+    X, Y = nx * grid.dx, ny * grid.dy
+    M = 40
+    xy = np.stack([rng.uniform(-X / 2, X / 2, M), rng.uniform(-Y / 2, Y / 2, M)], axis=1)
+    h = np.full(M, X * Y / M)
+    g = rng.normal(size=(M, nt))
+    fb = rng.normal(size=shape)
+    dt, c = 40e-9, 1500.0
+    gbar, aux = ndft.reconstruct_adjoint(xy, h, fb, dt, c, grid, nt, full=True)
+    G1bar = aux["G1bar"]
+    for rows in (None, 1, 3):
+        got = nufft.spectrum_cotangent(fb, dt, c, grid, nt, rows=rows)
+        assert np.abs(got - G1bar).max() <= 1e-11 * np.abs(G1bar).max()
+    S = np.array([0, 3, 17, 39])
+    sub = ndft.data_transform_adjoint(xy[S], h[S], G1bar, grid)
+    assert np.abs(sub - gbar[S]).max() <= 1e-13 * np.abs(gbar).max()
+    full = ndft.position_grad(xy, h, g, fb, dt, c, grid)
+    gs = ndft.position_grad_from_cotangent(xy[S], h[S], g[S], G1bar, grid)
+    assert np.abs(gs - full[S]).max() <= 1e-13 * np.abs(full).max()
+    # dL/dx_m for sensor 3 by central differences of <fb, A(xy) g>
+    eps = 1e-6 * grid.dx
+    for axis in (0, 1):
+        xp, xm = xy.copy(), xy.copy()
+        xp[3, axis] += eps
+        xm[3, axis] -= eps
+        fd = (np.vdot(fb, ndft.reconstruct(xp, h, g, dt, c, grid)) -
+              np.vdot(fb, ndft.reconstruct(xm, h, g, dt, c, grid))) / (2 * eps)
+        assert abs(fd - gs[1, axis]) <= 1e-6 * np.abs(gs).max()
+
+
 # ---------------------------------------------------------------- d = 2
 def test_plane_wave_profile_recovered_2d():
     assert pinlib.pin_plane_wave_2d() <= 1e-9
