@@ -8,7 +8,7 @@ import torch
 
 from oracle import ndft
 
-from test_gpu_parity import TOL, dev, host, pa, rel
+from test_gpu_parity import TOL, close, dev, host, pa, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -41,14 +41,10 @@ def test_2d_forward_adjoint_match_direct_sums(nx, nz, nt, ns):
     plan = pa().Plan2D(x, nt, dt, c, (nx, nz, grid.dx, grid.dz), weights=h)
     f = host(plan.reconstruct(dev(g)))
     assert f.shape == (nx, nz)
-    err = rel(f, ndft.reconstruct_2d(x, h, g, dt, c, grid))
-    print(f"2-D {nx}x{nz} nt={nt} M={ns} warp={plan.warp_ner}: forward rel L2 = {err:.3e}")
-    assert err <= TOL
+    close(f, ndft.reconstruct_2d(x, h, g, dt, c, grid), f"2-D {nx}x{nz} nt={nt} M={ns} warp={plan.warp_ner} forward")
     fb = np.random.default_rng(3).normal(size=(nx, nz))
     gb = host(plan.adjoint(dev(fb)))
-    errb = rel(gb, ndft.reconstruct_adjoint_2d(x, h, fb, dt, c, grid, nt))
-    print(f"2-D {nx}x{nz} nt={nt}: adjoint rel L2 = {errb:.3e}")
-    assert errb <= TOL
+    close(gb, ndft.reconstruct_adjoint_2d(x, h, fb, dt, c, grid, nt), f"2-D {nx}x{nz} nt={nt} adjoint")
     lhs = float(np.vdot(f, fb))
     rhs = float(np.vdot(g.astype(np.float32).astype(np.float64), gb))
     assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs))
@@ -64,11 +60,9 @@ def test_2d_position_grad_matches_oracle(nx, nz, nt, ns):
     gg, gxy = plan.position_grad(dev(g), dev(fb))
     gxy = host(gxy)
     ref = ndft.position_grad_2d(x, h, g, fb, dt, c, grid)
-    err = rel(gxy[:, 0], ref)
-    print(f"2-D {nx}x{nz}: position gradient rel L2 = {err:.3e}")
-    assert err <= TOL
+    close(gxy[:, 0], ref, f"2-D {nx}x{nz} position gradient")
     assert np.all(gxy[:, 1] == 0.0)
-    assert rel(host(gg), ndft.reconstruct_adjoint_2d(x, h, fb, dt, c, grid, nt)) <= TOL
+    close(host(gg), ndft.reconstruct_adjoint_2d(x, h, fb, dt, c, grid, nt), f"2-D {nx}x{nz} data gradient")
 
 
 def test_2d_warp_and_block_ner_agree():
@@ -85,7 +79,7 @@ def test_2d_default_weights_are_x_over_m():
     dt, c = 20e-9, 1500.0
     plan = pa().Plan2D(x, 64, dt, c, (16, 32, grid.dx, grid.dz))
     hdef = np.full(12, 16 * grid.dx / 12)
-    assert rel(host(plan.reconstruct(dev(g))), ndft.reconstruct_2d(x, hdef, g, dt, c, grid)) <= TOL
+    close(host(plan.reconstruct(dev(g))), ndft.reconstruct_2d(x, hdef, g, dt, c, grid), "2-D default weights forward")
 
 
 def test_2d_plans_refuse_unsupported_calls():
@@ -123,6 +117,4 @@ def test_2d_bench_size_dot_and_columns():
     for jx in (0, 37, -101):
         ref = ndft.column_depth_profile(np.stack([x, np.zeros_like(x)], 1), h, g, dt, c, grid, jx, 0)
         got = spec[jx + nx // 2, 0, :]
-        err = rel(got, ref)
-        print(f"2-D bench size column jx={jx}: rel L2 = {err:.3e}")
-        assert err <= TOL
+        close(got, ref, f"2-D bench size column jx={jx}")

@@ -1,9 +1,11 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
 Tolerance: relative L2 error <= 1e-4 against the FP64 oracle for every
-reconstruction, adjoint and position gradient; the FP32 NUFFT with a width-8
-Kaiser-Bessel window is expected near 1e-6.  Dot-product tests of the GPU
-operator and its adjoint: <= 1e-5.
+reconstruction, adjoint and position gradient, and element by element
+max |GPU - oracle| <= 1e-3 max |oracle| (so that an error confined to a few
+elements -- one wrong Nyquist column, one bad tile halo -- cannot hide in the
+norm); the FP32 NUFFT with a width-8 Kaiser-Bessel window is expected near
+1e-6.  Dot-product tests of the GPU operator and its adjoint: <= 1e-5.
 """
 import numpy as np
 import pytest
@@ -37,6 +39,41 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def close(got, ref, what, tol=TOL):
+    """GPU result against the oracle: relative L2 error <= tol and max
+    |got - ref| <= 10 tol max |ref| (1e-3 for the default 1e-4).  Returns
+    the relative L2 error."""
+    cplx = np.iscomplexobj(got) or np.iscomplexobj(ref)
+    got = np.asarray(got, dtype=np.complex128 if cplx else np.float64)
+    ref = np.asarray(ref, dtype=np.complex128 if cplx else np.float64)
+    err = rel(got, ref)
+    peak = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    print(f"{what}: rel L2 = {err:.3e}, max abs err / max |ref| = {peak:.3e}")
+    assert err <= tol, f"{what}: rel L2 {err:.3e}"
+    assert peak <= 10 * tol, f"{what}: max abs err / max |ref| {peak:.3e}"
+    return err
+
+
+def sample_sensors(P, n, seed=0):
+    """n sensor indices of a problem: sensors whose window footprint wraps
+    round the periodic grid (within 4 oversampled cells of an edge), the ones
+    nearest the centre, and a seeded random draw from each half of the sensor
+    list (for the 128x128 workload: the jittered lattice, then the
+    centre-dense half)."""
+    X, Y = P.grid.nx * P.grid.dx, P.grid.ny * P.grid.dy
+    ux = (P.xy[:, 0] / X + 0.5) % 1.0
+    uy = (P.xy[:, 1] / Y + 0.5) % 1.0
+    edge = np.minimum(np.minimum(ux, 1 - ux) * 2 * P.grid.nx, np.minimum(uy, 1 - uy) * 2 * P.grid.ny)
+    rng = np.random.default_rng(seed)
+    k = n // 4
+    picks = list(np.argsort(edge)[:k])
+    picks += list(np.argsort(np.hypot(P.xy[:, 0], P.xy[:, 1]))[:k])
+    M = P.n_sensors
+    picks += list(rng.choice(M // 2, k, replace=False))
+    picks += list(M // 2 + rng.choice(M - M // 2, n - 3 * k, replace=False))
+    return np.unique(np.array(picks))
+
+
 def dev(a):
     return torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
 
@@ -65,9 +102,7 @@ def test_forward_matches_direct_sum(name):
     ref = ndft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid)
     plan = plan_of(P)
     f = host(plan.reconstruct(dev(P.g)))
-    err = rel(f, ref)
-    print(f"{name}: rel L2 vs O1 = {err:.3e}")
-    assert err <= TOL
+    close(f, ref, f"{name} forward vs O1")
     assert plan.status() == 0
 
 
@@ -81,25 +116,21 @@ def test_forward_odd_and_ragged_sizes(grid, n_t, ns):
     P = custom_problem(ns[0], ns[1], grid, n_t)
     ref = ndft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid)
     f = host(plan_of(P).reconstruct(dev(P.g)))
-    err = rel(f, ref)
-    print(f"{grid.shape} nt={n_t}: rel L2 = {err:.3e}")
-    assert err <= TOL
+    close(f, ref, f"{grid.shape} nt={n_t} forward vs O1")
 
 
 @pytest.mark.parametrize("width", [6, 12, 16])
 def test_forward_other_widths(width):
     P = synth.c1()
     ref = ndft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid)
-    err = rel(host(plan_of(P, width=width).reconstruct(dev(P.g))), ref)
-    print(f"width {width}: rel L2 = {err:.3e}")
-    assert err <= (3e-4 if width == 6 else TOL)
+    close(host(plan_of(P, width=width).reconstruct(dev(P.g))), ref, f"width {width} forward vs O1",
+          tol=3e-4 if width == 6 else TOL)
 
 
 def test_sigma_three():
     P = synth.c1()
     ref = ndft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid)
-    err = rel(host(plan_of(P, sigma=3).reconstruct(dev(P.g))), ref)
-    assert err <= TOL
+    close(host(plan_of(P, sigma=3).reconstruct(dev(P.g))), ref, "sigma 3 forward vs O1")
 
 
 # ----------------------------------------------------------- stage parity
@@ -113,9 +144,7 @@ def test_spatial_spectrum_stage():
     hx, hy = nx // 2, ny // 2
     # the GPU keeps jx = -hx..hx and jy = 0..hy (the Hermitian half plus +N/2)
     exp = ndft.data_transform(P.xy, P.h, P.g, P.grid, np.arange(-hx, hx + 1), np.arange(0, hy + 1))
-    err = rel(G1, exp)
-    print(f"G1 rel L2 = {err:.3e}")
-    assert err <= TOL
+    close(G1, exp, "G1 vs eq:NUDFT2")
 
 
 def test_time_frequency_stage():
@@ -140,9 +169,7 @@ def test_time_frequency_stage():
     # jy = 0..hy: array indices hy..ny-1, then (even ny) the Nyquist slot at index 0
     half = Fsym[:, hy:, :] if ny % 2 else np.concatenate([Fsym[:, hy:, :], Fsym[:, :1, :]], axis=1)
     exp = np.einsum("abl,lz->abz", half, E) / (nx * ny * nz)
-    err = rel(Fz, exp)
-    print(f"Fz rel L2 = {err:.3e}")
-    assert err <= TOL
+    close(Fz, exp, "Fz vs direct sums")
 
 
 # ------------------------------------------------------------------ adjoint
@@ -153,9 +180,7 @@ def test_adjoint_matches_direct_transpose(name):
     fb = rng.normal(size=P.grid.shape)
     ref = ndft.reconstruct_adjoint(P.xy, P.h, fb, P.dt, P.c, P.grid, P.n_t)
     got = host(plan_of(P).adjoint(dev(fb)))
-    err = rel(got, ref)
-    print(f"{name}: adjoint rel L2 = {err:.3e}")
-    assert err <= TOL
+    close(got, ref, f"{name} adjoint vs O1 transpose")
 
 
 def _dot_test(P, plan, seed=4):
@@ -193,11 +218,9 @@ def test_position_gradient_matches_analytic(name):
     ref = ndft.position_grad(P.xy, P.h, P.g, fb, P.dt, P.c, P.grid)
     plan = plan_of(P)
     gg, gxy = plan.position_grad(dev(P.g), dev(fb))
-    err = rel(host(gxy), ref)
-    print(f"{name}: position gradient rel L2 = {err:.3e}")
-    assert err <= TOL
+    close(host(gxy), ref, f"{name} position gradient vs O1")
     ref_g = ndft.reconstruct_adjoint(P.xy, P.h, fb, P.dt, P.c, P.grid, P.n_t)
-    assert rel(host(gg), ref_g) <= TOL
+    close(host(gg), ref_g, f"{name} data gradient vs O1")
 
 
 def test_autograd_function():
@@ -213,7 +236,7 @@ def test_autograd_function():
     assert rel(host(g.grad), host(gg)) <= 1e-6
     assert rel(xy.grad.numpy(), host(gxy)) <= 1e-6
     ref = ndft.position_grad(P.xy, P.h, P.g, host(fb), P.dt, P.c, P.grid)
-    assert rel(xy.grad.numpy(), ref) <= TOL
+    close(xy.grad.numpy(), ref, "autograd position gradient vs O1")
 
 
 def test_update_positions_matches_new_plan():
@@ -332,7 +355,7 @@ def test_single_sensor_and_one_cell():
         h = np.full(xy.shape[0], 6.4e-7 / xy.shape[0])
         ref = ndft.reconstruct(xy, h, g, 40e-9, 1500.0, grid)
         got = host(pa().Plan(xy, 32, 40e-9, 1500.0, grid.as_tuple(), weights=h).reconstruct(dev(g)))
-        assert rel(got, ref) <= TOL
+        close(got, ref, f"{xy.shape[0]} sensor(s) in one cell, forward vs O1")
 
 
 def test_zero_data_gives_zero_image():
@@ -367,8 +390,9 @@ def test_batch_matches_single_plans(mode):
         B.run(gs, fs)
         for f, s in zip(fs, singles):
             assert np.array_equal(host(f), s)
-    ref = ndft.reconstruct(probs[1].xy, probs[1].h, probs[1].g, probs[1].dt, probs[1].c, probs[1].grid)
-    assert rel(singles[1], ref) <= TOL
+    for k, (P, f) in enumerate(zip(probs, fs)):
+        ref = ndft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid)
+        close(host(f), ref, f"batch mode {mode} instance {k} vs O1")
 
 
 def test_batch_with_fast_path_sizes():
@@ -380,6 +404,7 @@ def test_batch_with_fast_path_sizes():
     plans = [plan_of(P) for P in probs]
     gs = [dev(P.g) for P in probs]
     singles = [host(p.reconstruct(g)) for p, g in zip(plans, gs)]
+    refs = [nufft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid) for P in probs]   # O2, width 16
     for mode in (0, 1):
         B = pa().Batch(plans, mode=mode)
         fs = [torch.empty(p.image_shape, device="cuda") for p in plans]
@@ -390,6 +415,8 @@ def test_batch_with_fast_path_sizes():
                     assert np.array_equal(host(f), s)
                 else:
                     assert rel(host(f), s) <= 1e-5
+        for k, (f, ref) in enumerate(zip(fs, refs)):
+            close(host(f), ref, f"batch mode {mode} instance {k} {probs[k].grid.shape} vs O2")
         B.close()
 
 
@@ -403,9 +430,7 @@ def test_c2_forward_matches_nufft_oracle(c2):
     P = c2
     ref = nufft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid, 2, 12)
     f = host(plan_of(P).reconstruct(dev(P.g)))
-    err = rel(f, ref)
-    print(f"C2 forward rel L2 vs O2(w=12) = {err:.3e}")
-    assert err <= TOL
+    close(f, ref, "C2 forward vs O2(w=12)")
 
 
 def test_c2_adjoint_and_dot(c2):
@@ -414,10 +439,32 @@ def test_c2_adjoint_and_dot(c2):
     rng = np.random.default_rng(6)
     fb = rng.normal(size=P.grid.shape)
     ref = nufft.reconstruct_adjoint(P.xy, P.h, fb, P.dt, P.c, P.grid, P.n_t, 2, 12)
-    err = rel(host(plan.adjoint(dev(fb))), ref)
-    print(f"C2 adjoint rel L2 = {err:.3e}")
-    assert err <= TOL
+    close(host(plan.adjoint(dev(fb))), ref, "C2 adjoint vs O2(w=12)")
     assert _dot_test(P, plan) <= 1e-5
+
+
+def test_c2_position_gradient_sampled_sensors(c2):
+    """The position gradient (and the data gradient) of the autotuned plan the
+    benchmark times, at the full 128x128x256 size, on sampled sensors
+    (footprints that wrap round the grid, the centre-dense region, random
+    draws from both halves) against the oracle: the cotangent G1bar of the
+    spatial spectrum from the oracle's transposed chain (image adjoint,
+    weight, NER adjoint at width 16), then the analytic derivative of
+    eq:NUDFT2 at each sampled sensor."""
+    P = c2
+    plan = plan_of(P)
+    plan.autotune()
+    assert plan.warp_ner
+    fb = np.random.default_rng(9).normal(size=P.grid.shape).astype(np.float32).astype(np.float64)
+    gg, gxy = plan.position_grad(dev(P.g), dev(fb))
+    G1bar = nufft.spectrum_cotangent(fb, P.dt, P.c, P.grid, P.n_t, rows=32)
+    S = sample_sensors(P, 80)
+    g32 = P.g.astype(np.float32).astype(np.float64)
+    ref_xy = ndft.position_grad_from_cotangent(P.xy[S], P.h[S], g32[S], G1bar, P.grid)
+    close(host(gxy)[S], ref_xy, f"C2 position gradient, {len(S)} sensors")
+    ref_g = ndft.data_transform_adjoint(P.xy[S], P.h[S], G1bar, P.grid)
+    close(host(gg)[S], ref_g, f"C2 data gradient, {len(S)} sensors")
+    assert plan.status() == 0
 
 
 def test_c2_autotuned_plan_matches_default(c2):

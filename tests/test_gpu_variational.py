@@ -16,7 +16,7 @@ import synth
 from oracle import ndft
 
 import varloss
-from test_gpu_parity import TOL, dev, host, pa, plan_of, rel
+from test_gpu_parity import TOL, close, dev, host, pa, plan_of, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -43,14 +43,13 @@ def test_variational_gradients_match_oracle_c1():
     plan = plan_of(P)
     f, L, gg, gxy = _forward_backward(P, plan, dev(target))
     f_ref = ndft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid)
-    assert rel(host(f), f_ref) <= TOL
+    close(host(f), f_ref, "c1 variational forward")
     dLdf = varloss.grad_f_np(host(f), target)
     ref_g = ndft.reconstruct_adjoint(P.xy, P.h, dLdf, P.dt, P.c, P.grid, P.n_t)
     ref_xy = ndft.position_grad(P.xy, P.h, P.g, dLdf, P.dt, P.c, P.grid)
-    eg, exy = rel(host(gg), ref_g), rel(gxy.numpy(), ref_xy)
-    print(f"c1 variational: loss {L:.6e}, grad g rel L2 {eg:.3e}, grad xy rel L2 {exy:.3e}")
-    assert eg <= TOL
-    assert exy <= TOL
+    print(f"c1 variational: loss {L:.6e}")
+    close(host(gg), ref_g, "c1 variational grad g")
+    close(gxy.numpy(), ref_xy, "c1 variational grad xy")
     assert abs(L - varloss.loss_np(f_ref, target)) <= 1e-4 * L
 
 
