@@ -220,24 +220,29 @@ int pa_position_grad(pa_plan *plan, const float *g_dev, const float *grad_f_dev,
 /*
  * Position gradient without device allocation.  The paper has no counterpart;
  * this is a library convenience.  Same result as pa_position_grad (same
- * kernels), but the kernel's scratch -- the per-chunk partial sums of the
+ * kernels), but the kernels' scratch -- the per-chunk partial sums of the
  * gradient, ceil(n_t/32) * n_sensors float2 values -- lives in a static device
  * array of the library (16 MiB, at most 2^21 partials; larger problems get
- * PA_ERR_UNSUPPORTED_SIZE) instead of the plan's workspace.  For callers
- * that may not call cudaMalloc at the time they need gradients: code running
- * while a CUDA graph is being captured (cudaMalloc is not a stream operation
- * and is refused or breaks the capture), or code whose device memory is owned
- * by a fixed arena or an external allocator that forbids new allocations.
+ * PA_ERR_UNSUPPORTED_SIZE) instead of the plan's workspace.  It is meant for
+ * callers that cannot let a library allocate device memory while they run:
+ * applications whose device memory is handed out by their own arena or
+ * caching allocator (a cudaMalloc beside it can fail on a full device or
+ * fragment the pool the application sized), and loops that take a gradient
+ * step after step and must not stall on cudaMalloc/cudaFree, which may
+ * synchronise the device and so hold up the work on every other stream.
  *   - The call allocates nothing: no cudaMalloc/cudaFree, no allocating
- *     library routine.  It copies one plan descriptor (host to device) and
- *     launches the same kernels as pa_position_grad.
+ *     library routine.  It launches one single-thread kernel that stores the
+ *     plan's descriptor (passed as a kernel argument) into a static device
+ *     descriptor, then the kernels of pa_position_grad.
  *   - The first call on a device looks up the static array's device address
- *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture.  The plan's device must be current.
+ *     with that device current (cudaGetSymbolAddress), and again when the
+ *     device's context has changed (after cudaDeviceReset, which also
+ *     invalidates every plan of that device).  The plan's device must be
+ *     current.
  *   - All calls share the one array and descriptor, which keep the last
- *     call's contents; every partial is rewritten by each call, so nothing
- *     needs clearing.  Calls that overlap on the GPU (different streams, or
- *     host threads) race and must not be issued.
+ *     call's contents; every partial a call reads is rewritten by that call
+ *     first, so nothing needs clearing.  Calls that overlap on the GPU
+ *     (different streams, or host threads) race and must not be issued.
  * Arguments as in pa_position_grad.
  */
 int pa_position_grad_noalloc(pa_plan *plan, const float *g_dev, const float *grad_f_dev,
@@ -299,6 +304,23 @@ int pa_batch_destroy(pa_batch *batch);
  * *device_status = 0 when no kernel recorded an error.
  */
 int pa_status(pa_plan *plan, int *device_status, void *stream);
+
+/*
+ * Test hook for the bounded waits (off by default; not for production use).
+ * With item >= 0, the plan's pipelined interpolation kernel (the last stage
+ * of pa_reconstruct_adjoint and pa_position_grad on plans whose n_t is a
+ * multiple of 4 and width <= 8) posts the byte count of its work item `item`
+ * on that item's mbarrier but issues none of the item's copies, and every
+ * wait of that kernel gives up after `polls` polls (polls <= 0: the default
+ * limit of 2^20).  The block that owns the item then finds its wait run out,
+ * waits (bounded) for the copies it did issue, records PA_STATUS_WAIT_TIMEOUT
+ * in the plan's status word and returns; nothing is left in flight and no
+ * fault is raised, but the call's output is incomplete.  pa_status reports
+ * the bit.  item < 0 switches the hook off again.  Synchronises `stream`
+ * (the plan's device descriptor is rewritten on it).  3-D plans only.
+ */
+#define PA_STATUS_WAIT_TIMEOUT 1
+int pa_plan_test_wait_fault(pa_plan *plan, int item, int polls, void *stream);
 
 /*
  * Measure the alternative launch shapes of the plan's three heaviest stages

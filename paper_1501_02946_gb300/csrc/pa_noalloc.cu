@@ -6,10 +6,15 @@
 // The array below is part of the library image: every GPU that loads the
 // library holds it (16 MiB plus one descriptor) until the process exits.
 // In host code its name is only a host-side stand-in for the device symbol,
-// so its device address is looked up once per device with that device
-// current (cudaGetSymbolAddress) and passed to the kernels.
+// so its device address is looked up with that device current
+// (cudaGetSymbolAddress) and passed to the kernels.  The lookup is made once
+// per device and context: a new primary context (after cudaDeviceReset, say)
+// may load the library's module at another address, so it is looked up again.
 #include <mutex>
 #include <string>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "pa_internal.h"
 #include "pa_nufft.h"
@@ -22,16 +27,41 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) float2 pa_noalloc_partials[kPartials];
 __device__ __align__(256) pa::InstDesc pa_noalloc_desc;
 
+// The call's descriptor reaches the device as a kernel argument (copied at
+// launch) and is stored into the static descriptor by one thread; no host
+// buffer is read after the launch returns.
+__global__ void k_store_desc(const __grid_constant__ pa::InstDesc d) { pa_noalloc_desc = d; }
+
 std::mutex g_mu;
+CUcontext g_ctx[kMaxDevices] = {};
 bool g_ready[kMaxDevices] = {};
 float2 *g_partials[kMaxDevices] = {};
 pa::InstDesc *g_desc[kMaxDevices] = {};
 
+// The current context through the runtime's driver entry-point query (null
+// if unavailable; the lookup is then made on every call).
+CUcontext current_context() {
+  static PFN_cuCtxGetCurrent_v4000 get = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
+  }
+  CUcontext c = nullptr;
+  if (get && get(&c) != CUDA_SUCCESS) c = nullptr;
+  return c;
+}
+
 // Device addresses of the static arrays on the current device (looked up on
-// the first call made on that device).
+// the first call made on that device, and again when its context changed).
 int static_addresses(int dev, float2 **partials, pa::InstDesc **desc) {
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_ready[dev]) {
+  const CUcontext ctx = current_context();
+  if (!g_ready[dev] || !ctx || ctx != g_ctx[dev]) {
     void *p = nullptr, *q = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, pa_noalloc_partials);
     if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, pa_noalloc_desc);
@@ -39,6 +69,7 @@ int static_addresses(int dev, float2 **partials, pa::InstDesc **desc) {
       return pa::set_error(PA_ERR_CUDA, (std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)).c_str());
     g_partials[dev] = static_cast<float2 *>(p);
     g_desc[dev] = static_cast<pa::InstDesc *>(q);
+    g_ctx[dev] = ctx;
     g_ready[dev] = true;
   }
   *partials = g_partials[dev];
@@ -83,8 +114,8 @@ extern "C" int pa_position_grad_noalloc(pa_plan *plan, const float *g_dev, const
   // the plan's descriptor with the partial sums redirected to the static array
   pa::InstDesc d = h;
   d.grad_part = partials;
-  e = cudaMemcpyAsync(ddesc, &d, sizeof(d), cudaMemcpyHostToDevice, s);  // pageable: consumed on return
-  if (e != cudaSuccess) return launched(e, "descriptor upload");
+  k_store_desc<<<1, 1, 0, s>>>(d);
+  if ((rc = launched(cudaGetLastError(), "descriptor store")) != PA_OK) return rc;
 
   pa::Launch L{};
   L.descs = ddesc;
