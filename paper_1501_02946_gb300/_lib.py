@@ -60,6 +60,7 @@ SIGNATURES = {
     "pa_batch_destroy": (c_int, [c_void_p]),
     "pa_batch_set_mode": (c_int, [c_void_p, c_int]),
     "pa_status": (c_int, [c_void_p, POINTER(c_int), c_void_p]),
+    "pa_plan_test_wait_fault": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "pa_plan_info": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64)]),
     "pa_plan_buffer": (c_int, [c_void_p, c_int, c_void_p, c_int64, POINTER(c_int64), c_void_p]),
     "pa_profile_enable": (c_int, [c_void_p, c_int]),

@@ -524,8 +524,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 constexpr int kMbarPolls = 1 << 20;  // each poll suspends for a hardware-defined interval
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  for (int i = 0; i < kMbarPolls; ++i)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int polls = kMbarPolls) {
+  for (int i = 0; i < polls; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -593,10 +593,10 @@ __device__ __forceinline__ bool tile_pipeline(int nwork, float2 *buf0, float2 *b
 // wait for the thread that issues the next copies.  What issue() writes to
 // shared memory for item w is read by compute(w) only after the barrier that
 // ends the previous item (or the one after the first issues).  compute() may
-// not contain block barriers.
+// not contain block barriers.  Each wait gives up after `polls` polls.
 template <int NS, typename Issue, typename Compute>
 __device__ __forceinline__ bool tile_pipeline_n(int nwork, float2 *buf, size_t stride, uint64_t *bars, int *status,
-                                                Issue issue, Compute compute) {
+                                                Issue issue, Compute compute, int polls = kMbarPolls) {
   const int tid = threadIdx.x;
   if (tid == 0) {
     for (int b = 0; b < NS; ++b) mbar_init(&bars[b], 1);
@@ -622,14 +622,14 @@ __device__ __forceinline__ bool tile_pipeline_n(int nwork, float2 *buf, size_t s
     }
     const uint32_t par = uint32_t(i / NS) & 1u;
     // warp-uniform, so that compute() keeps its shuffles whole
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars[s], par));
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars[s], par, polls));
     if (ok) compute(w, buf + s * stride);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) atomicOr(status, kStatusWaitTimeout);
       // one more bounded wait for every copy still in flight
       for (int k = 0; k < NS; ++k) {
         const int wk = w + k * gridDim.x;
-        if (wk < nwork) mbar_wait(&bars[(i + k) % NS], uint32_t((i + k) / NS) & 1u);
+        if (wk < nwork) mbar_wait(&bars[(i + k) % NS], uint32_t((i + k) / NS) & 1u, polls);
       }
       return false;
     }

@@ -106,6 +106,11 @@ struct InstDesc {
   float2 *grad_part;    // [nchunk_adj][M] per-chunk position-gradient partials
   float *G0;            // [Mx][My][Nt] real oversampled grid (forward) or its cotangent (adjoint)
   int *status;
+  // test hook of the pipelined interpolation (zero: off): work item
+  // test_fault - 1 has its byte count posted but none of its copies issued,
+  // and its waits give up after wait_polls polls (zero: kMbarPolls)
+  int test_fault;
+  int wait_polls;
 };
 
 // Twiddle tables of the warp-per-column NER kernels, appended to the plan's

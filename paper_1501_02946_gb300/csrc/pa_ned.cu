@@ -806,6 +806,9 @@ __global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS, PA_INTER
     float *packs = Gs + CELLS * NC, *packd = packs + SMAX * PW;
     const int ps = p0 - W / 2 + 1, qs = q0 - W / 2 + 1;
     const bool box = use_map && ps >= 0 && ps + HX <= Mx && qs >= 0 && qs + HY <= My;
+    // test hook: this item's byte count is posted and none of its copies is
+    // issued, so its waits run out (nothing is left in flight)
+    const bool drop = d.test_fault == w + 1;
     uint32_t pack_bytes = 0;
     if (tid < 32) {
       // rows r < TX of the tile: sorted ranges, their prefix, and the packs
@@ -830,13 +833,17 @@ __global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS, PA_INTER
         rlo[par][lane] = lo;
         rpre[par][lane] = pre;
         const int k = min(cnt, SMAX - pre);
-        if (k > 0) {
+        if (k > 0 && !drop) {
           bulk_g2s(packs + pre * PW, d.ipack + (size_t)lo * (PW / 4), uint32_t(k * PW * 4), bar);
           if (GRAD) bulk_g2s(packd + pre * PD, d.ipack_d + (size_t)lo * (PD / 4), uint32_t(k * PD * 4), bar);
         }
       }
       if (lane == 0) rpre[par][TX] = total;
       pack_bytes = uint32_t(min(total, SMAX) * (PW + PD) * 4);
+    }
+    if (drop) {
+      if (tid == 0) mbar_arrive_expect_tx(bar, uint32_t(CELLS * NC * sizeof(float)));
+      return;
     }
     if (box) {
       if (tid == 0) {
@@ -944,7 +951,8 @@ __global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS, PA_INTER
       }
     }
   };
-  tile_pipeline_n<S::NS>(nwork, buf0, S::BUF / 2, bars, d.status, issue, compute);
+  tile_pipeline_n<S::NS>(nwork, buf0, S::BUF / 2, bars, d.status, issue, compute,
+                         d.wait_polls > 0 ? d.wait_polls : kMbarPolls);
 }
 
 // ipack[i] = (wx[i][0..w), wy[i][0..w), sby[i], perm[i]); ipack_d[i] = (dwx, dwy)

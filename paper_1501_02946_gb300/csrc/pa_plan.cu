@@ -1472,6 +1472,18 @@ int pa_status(pa_plan *plan, int *device_status, void *stream) {
   return v ? fail(PA_ERR_DEVICE, "a kernel recorded an error") : PA_OK;
 }
 
+int pa_plan_test_wait_fault(pa_plan *plan, int item, int polls, void *stream) {
+  g_err.clear();
+  if (!plan) return fail(PA_ERR_INVALID_ARG, "plan is NULL");
+  if (plan->d2) return fail(PA_ERR_INVALID_ARG, "not supported for 2-D plans");
+  plan->h.test_fault = item >= 0 ? item + 1 : 0;
+  plan->h.wait_polls = item >= 0 && polls > 0 ? polls : 0;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  PA_CUDA(cudaMemcpyAsync(plan->d_desc, &plan->h, sizeof(InstDesc), cudaMemcpyHostToDevice, s));
+  PA_CUDA(cudaStreamSynchronize(s));
+  return PA_OK;
+}
+
 int pa_plan_is_lattice(const pa_plan *plan, int *is_lattice) {
   g_err.clear();
   if (!plan || !is_lattice) return fail(PA_ERR_INVALID_ARG, "NULL argument");
