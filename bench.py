@@ -1,7 +1,8 @@
 #!/usr/bin/env python3
 """Throughput of the GB300 NEDNER-NUFFT: one step = one forward
-reconstruction and one adjoint (f = A g, then A^T f) of the 128x128 sensor
-workload (16384 non-equispaced sensors, 512 samples, 128x128x256 voxels).
+reconstruction and one adjoint (f = A g, then A^T f) of the large single
+reconstruction (65536 dart-thrown sensors over 25.6 mm, 1024 samples at
+10 ns, 256x256x512 voxels).
 
 Prints ONE JSON line (rank 0).  Multi-GPU (torchrun): each rank runs its own
 replica of the workload ("replicas only": a single reconstruction does not
@@ -11,7 +12,8 @@ the voxels of all ranks.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle (the NUFFT algorithm in numpy) on
-the host cores instead, on a bounded sample of the same workload.
+the host cores instead, on a bounded sample of the same workload (tiles of
+the aperture, one oracle process per core).
 """
 from __future__ import annotations
 
@@ -32,8 +34,11 @@ if ROOT not in sys.path:
 
 METRIC = "voxels/s (NEDNER-NUFFT fwd+adjoint, FP32, ≤1e-4 rel L2 vs FP64) and HBM roofline %"
 UNIT = "voxels/s"
-WORKLOAD = ("128x128 non-equispaced sensors over 12.8 mm (8192 jittered lattice + 8192 centre-dense), "
-            "512 samples at 20 ns, 20 balls + 1% noise, output 128x128x256 at 100 um, sigma 2, width 8")
+WORKLOAD = ("256x256 non-equispaced sensors: 65536 random-uniform over 25.6 mm (dart throwing, minimum "
+            "spacing 40 um), 1024 samples at 10 ns, 20 balls + 6 vessels (chains of balls, 638 sources), "
+            "output 256x256x512 at 100 um, sigma 2, width 8")
+WORKLOAD_C2 = ("128x128 non-equispaced sensors over 12.8 mm (8192 jittered lattice + 8192 centre-dense), "
+               "512 samples at 20 ns, 20 balls + 1% noise, output 128x128x256 at 100 um, sigma 2, width 8")
 STAGES = ["ned_spread", "ned_rowfft", "ned_colfft", "ner_fused", "image_x", "image_y_c2r", "image_y_adj",
           "image_x_adj", "ner_adj", "ned_colfft_adj", "ned_rowifft", "ned_interp"]
 
@@ -148,45 +153,65 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_step(P, fb_seed=0):
-    """One forward + adjoint of the FP64 NUFFT oracle (as it stands)."""
-    import numpy as np
-    from oracle import nufft
-    t0 = time.perf_counter()
-    f = nufft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid)
-    nufft.reconstruct_adjoint(P.xy, P.h, f, P.dt, P.c, P.grid, P.n_t)
-    return time.perf_counter() - t0
-
-
-def cropped(P, s):
-    """Sub-aperture sample of a workload: the sensors within the central
-    (X/s) x (Y/s) square and the matching (nx/s) x (ny/s) x nz output grid."""
+def tile_problem(P, s, i, j):
+    """Tile (i, j) of an s x s tiling of a workload's aperture: the sensors in
+    that (X/s) x (Y/s) square, moved so the tile is centred on (0, 0), with
+    the matching (nx/s) x (ny/s) x nz output grid and uniform weights."""
     import numpy as np
     import synth
     if s == 1:
         return P
     gr = P.grid
-    hx, hy = gr.nx * gr.dx / (2 * s), gr.ny * gr.dy / (2 * s)
-    keep = (P.xy[:, 0] >= -hx) & (P.xy[:, 0] < hx) & (P.xy[:, 1] >= -hy) & (P.xy[:, 1] < hy)
+    X, Y = gr.nx * gr.dx, gr.ny * gr.dy
+    x0, y0 = -X / 2 + i * X / s, -Y / 2 + j * Y / s
+    keep = (P.xy[:, 0] >= x0) & (P.xy[:, 0] < x0 + X / s) & (P.xy[:, 1] >= y0) & (P.xy[:, 1] < y0 + Y / s)
     grid = synth.Grid(gr.nx // s, gr.ny // s, gr.nz, gr.dx, gr.dy, gr.dz)
     M = int(keep.sum())
-    h = np.full(M, (2 * hx) * (2 * hy) / M)
-    return synth.Problem(P.name + f"_crop{s}", P.xy[keep], h, P.g[keep], P.dt, P.c, grid)
+    xy = P.xy[keep] - np.array([x0 + X / (2 * s), y0 + Y / (2 * s)])
+    h = np.full(M, (X / s) * (Y / s) / M)
+    return synth.Problem(P.name + f"_tile{s}_{i}_{j}", xy, h, P.g[keep], P.dt, P.c, grid)
 
 
-def cpu_baseline_subprocess(s=1):
-    """Time the oracle single-threaded in a fresh interpreter (BLAS/FFT threads
-    pinned to 1 so `cores` is exact)."""
-    code = ("import sys, json; sys.path.insert(0, %r); import bench, synth; "
-            "P = bench.cropped(synth.c2(), %d); t = bench.cpu_oracle_step(P); "
-            "print(json.dumps({'t': t, 'voxels': P.grid.nx * P.grid.ny * P.grid.nz, 'M': P.n_sensors}))"
-            % (ROOT, s))
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
-    if r.returncode != 0:
-        raise RuntimeError("cpu baseline failed: " + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+def _oracle_worker(args):
+    """One FP64 forward + adjoint of the NUFFT oracle (as it stands) on one
+    tile, in a worker process with one BLAS/FFT thread.  Returns the seconds
+    it took, its voxels, and (if asked) the forward image."""
+    xy, h, g, dt, c, grid_t, want_f = args
+    import synth
+    from oracle import nufft
+    grid = synth.Grid(*grid_t)
+    t0 = time.perf_counter()
+    f = nufft.reconstruct(xy, h, g, dt, c, grid)
+    nufft.reconstruct_adjoint(xy, h, f, dt, c, grid, g.shape[1])
+    return time.perf_counter() - t0, grid.nx * grid.ny * grid.nz, (f if want_f else None)
+
+
+def oracle_pool(n):
+    """A pool of n spawned oracle workers, each with one BLAS/FFT thread (the
+    environment is set before the workers start; spawn, so that no worker is
+    forked from a process that holds a CUDA context)."""
+    import multiprocessing as mp
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    return mp.get_context("spawn").Pool(n)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_tiles(P, s, k0, n, want_first=False):
+    """Arguments of n oracle tasks: tiles k0, k0 + 1, .. (mod s*s) of an s x s
+    tiling of P."""
+    out = []
+    for k in range(k0, k0 + n):
+        i, j = divmod(k % (s * s), s)
+        T = tile_problem(P, s, i, j)
+        out.append((T.xy, T.h, T.g, T.dt, T.c, T.grid.as_tuple(), want_first and k == k0))
+    return out
 
 
 def dist_env():
@@ -197,41 +222,150 @@ def dist_env():
 
 
 def run_reference(args):
+    """The FP64 oracle on the host cores: every step runs one tile of the
+    workload's aperture per core at once (tiles cycle through the tiling);
+    value = the tiles' voxels / the step's wall time."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    # the oracle runs on one host thread (numpy's FFT is single-threaded;
-    # pin BLAS pools before numpy loads so that `cores` is exact)
-    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[var] = "1"
     import synth
-    # sample per step: a central sub-aperture crop sized so that the whole
-    # (steps + warmup) run stays within about three minutes
-    t_full_est = 25.0
+    P = synth.c3()
+    cores = min(host_cores(), 32)
     n = args.steps + args.warmup
-    s = 1
-    while s < 8 and n * t_full_est / (s * s) > 180.0:
-        s *= 2
-    P = cropped(synth.c2(), s)
-    times = []
-    for i in range(n):
-        t = cpu_oracle_step(P)
-        if i >= args.warmup:
-            times.append(t)
-    voxels = P.grid.nx * P.grid.ny * P.grid.nz
+    # tile size: 64x64x512 tiles take about 20 s each on one core, 32x32x512
+    # about a fifth of that; keep the whole run within about three minutes
+    s = 4 if n * 20.0 <= 180.0 else 8
+    pool = oracle_pool(cores)
+    times, vox = [], 0
+    try:
+        for k in range(n):
+            tasks = oracle_tiles(P, s, k * cores, cores)
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_worker, tasks)
+            t = time.perf_counter() - t0
+            if k >= args.warmup:
+                times.append(t)
+                vox = sum(r[1] for r in res)
+    finally:
+        pool.close()
+        pool.join()
     ms = 1e3 * sum(times) / len(times)
-    value = voxels / (ms / 1e3)
-    sample = (f"central {P.grid.nx}x{P.grid.ny} of 128x128 sub-aperture ({P.n_sensors} sensors), "
-              f"512 samples, depth 256; one FP64 forward+adjoint per step")
+    value = vox / (ms / 1e3)
+    sample = (f"{cores} tiles of {256 // s}x{256 // s}x512 per step (a {s}x{s} tiling of the 256x256 aperture, "
+              f"each tile's sensors re-centred, 1024 samples), one tile per core at once, one FP64 "
+              f"forward+adjoint per tile")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "sample": sample, "oracle": "FP64 NUFFT (numpy), width 16"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
+
+
+def cpu_baseline(P, pa, dev):
+    """The oracle on all host cores: one 64x64x512 tile of the workload per
+    core, run at once (one step's worth of a 4x4 tiling, cycling); plus the
+    accuracy of the GPU forward and of the cubic baseline on the first tile
+    against the oracle's FP64 forward image."""
+    import numpy as np
+    import torch
+    cores = min(host_cores(), 32)
+    s = 4
+    tasks = oracle_tiles(P, s, 0, cores, want_first=True)
+    pool = oracle_pool(cores)
+    try:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, tasks)
+        wall = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    vox = sum(r[1] for r in res)
+    xy, h, g, dt, c, grid_t, _ = tasks[0]
+    ref = res[0][2]
+    tile = pa.Plan(xy, g.shape[1], dt, c, grid_t, weights=h)
+    gd = torch.tensor(g, dtype=torch.float32, device=dev)
+    f_n = tile.reconstruct(gd).double().cpu().numpy()
+    f_c = tile.reconstruct_cubic(gd).double().cpu().numpy()
+    tile.close()
+    nrm = np.linalg.norm(ref)
+    acc = {"tile": f"{grid_t[0]}x{grid_t[1]}x{grid_t[2]}, {g.shape[0]} sensors, 1024 samples",
+           "nedner_rel_l2_vs_fp64_oracle": float(np.linalg.norm(f_n - ref) / nrm),
+           "cubic_rel_l2_vs_fp64_oracle": float(np.linalg.norm(f_c - ref) / nrm)}
+    sample = (f"{cores} tiles of 64x64x512 (a 4x4 tiling of the 256x256 aperture, each tile's sensors "
+              f"re-centred, 1024 samples), one FP64 forward+adjoint per tile, one tile per core at once")
+    return {"value": vox / wall, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "seconds": wall, "per_tile_seconds": [r[0] for r in res]}, acc
+
+
+def batch_timings(pa, synth, dev, steps, warmup, tune=True):
+    """The uneven batch (64 instances, N uniform over the 7-smooth integers in
+    [64, 256], T in {256, 512, 1024}, output N x N x 2T), seeded random data:
+    pa_batch_run in its two modes against 64 sequential single-plan calls."""
+    import numpy as np
+    import torch
+    shapes = synth.batch_shapes()
+    rng = np.random.default_rng(1505)
+    plans, gs, fs = [], [], []
+    voxels = 0
+    for n_side, n_t in shapes:
+        xy = synth.jittered_lattice(rng, n_side, n_side, 1e-4, 1e-4)
+        grid = (n_side, n_side, 2 * n_t, 1e-4, 1e-4, 1e-4)
+        p = pa.Plan(xy, n_t, 20e-9, synth.C_WATER, grid)
+        if tune:
+            p.autotune()
+        plans.append(p)
+        gs.append(torch.randn(n_side * n_side, n_t, device=dev, dtype=torch.float32))
+        fs.append(torch.empty(n_side, n_side, 2 * n_t, device=dev, dtype=torch.float32))
+        voxels += n_side * n_side * 2 * n_t
+    batch = pa.Batch(plans)
+    batch_st = pa.Batch(plans, mode=1)
+    stream = torch.cuda.current_stream(dev)
+
+    def seq():
+        for p, g, f in zip(plans, gs, fs):
+            p.reconstruct(g, out=f)
+
+    res = {}
+    for name, fn in (("batch_graph", lambda: batch.run(gs, fs)),
+                     ("batch_graph_stage_launches", lambda: batch_st.run(gs, fs)),
+                     ("sequential_64", seq)):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in evs:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = statistics.median(a.elapsed_time(b) for a, b in evs)
+        res[name] = {"ms": ms, "voxels_per_s": voxels / (ms / 1e3)}
+    batch.close()
+    batch_st.close()
+    for p in plans:
+        p.close()
+    best = min(res["batch_graph"]["ms"], res["batch_graph_stage_launches"]["ms"])
+    return {"workload": "64 instances, N in 7-smooth [64, 256], T in {256, 512, 1024}, output N x N x 2T, "
+                        "forward; plans autotuned" if tune else "64 instances (untuned plans)",
+            "total_voxels": voxels, "median_of": steps, **res,
+            "speedup_vs_sequential": res["sequential_64"]["ms"] / best}
+def timed_median(fn, k, flush, stream, dev):
+    """Median of k CUDA-event timings of fn() (L2 flushed before each, outside
+    the events), after two untimed calls."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    for _ in range(2):
+        fn()
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    return statistics.median(a.elapsed_time(b) for a, b in evs)
 
 
 def run_ours(args):
@@ -251,7 +385,7 @@ def run_ours(args):
     import paper_1501_02946_gb300 as pa
     import synth
 
-    P = synth.c2()
+    P = synth.c3()
     Nx, Ny, Nz = P.grid.shape
     voxels = Nx * Ny * Nz
     plan = pa.Plan(P.xy, P.n_t, P.dt, P.c, P.grid.as_tuple(), weights=P.h)
@@ -335,49 +469,69 @@ def run_ours(args):
                 "launch_timing": "CUDA events around this kernel's launches inside the timed region"}
     stages = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
                   "gbs": sb[k] / (v[0] / v[1] / 1e3) / 1e9 if k in sb else None,
+                  "frac_of_hbm": sb[k] / (v[0] / v[1] / 1e3) / 1e9 / hbm if k in sb else None,
                   "share": v[0] / sum(x[0] for x in prof.values())} for k, v in prof.items()}
     pipe = 2 * pipeline_min_bytes(P.n_sensors, P.n_t, Nx, Ny, Nz)
     pipeline = {"min_bytes_per_step": pipe, "achieved_gbs": pipe / (ms_per_step / 1e3) / 1e9,
                 "frac": pipe / (ms_per_step / 1e3) / 1e9 / hbm}
 
-    # forward alone, adjoint alone and the cubic-in-omega baseline forward
-    # (same plan, same L2 flush, CUDA events around each call)
-    def timed_calls(fn, k):
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
-        for _ in range(2):
-            fn()
-        for a, b in evs:
-            flush.zero_()
-            a.record(stream)
-            fn()
-            b.record(stream)
-        torch.cuda.synchronize(dev)
-        return statistics.median(a.elapsed_time(b) for a, b in evs)
     k_parts = max(3, min(args.steps, 10))
-    fwd_ms = timed_calls(lambda: plan.reconstruct(g, out=f), k_parts)
-    adj_ms = timed_calls(lambda: plan.adjoint(f, out=g2), k_parts)
-    cub_ms = timed_calls(lambda: plan.reconstruct_cubic(g, out=f), k_parts)
-    plan.reconstruct(g, out=f)
+
+    def timed(fn):
+        return timed_median(fn, k_parts, flush, stream, dev)
+
+    # forward alone, adjoint alone, the cubic-in-omega baseline forward and
+    # the position gradient of the same plan
+    fwd_ms = timed(lambda: plan.reconstruct(g, out=f))
+    adj_ms = timed(lambda: plan.adjoint(f, out=g2))
+    cub_ms = timed(lambda: plan.reconstruct_cubic(g, out=f))
+    f_cub = plan.reconstruct_cubic(g).double()
+    f_ned = plan.reconstruct(g, out=f).double()
+    cub_vs_ned = float(torch.linalg.norm(f_cub - f_ned) / torch.linalg.norm(f_ned))
+    del f_cub, f_ned
+    fb3 = torch.randn(P.grid.shape, device=dev, dtype=torch.float32)
+    pg3_ms = timed(lambda: plan.position_grad(g, fb3))
+    del fb3
     # library comparison (bench only): cuFFT (through torch.fft) doing the
     # row and column transforms of the same oversampled grid, without the
     # deconvolution, truncation and pair packing that the kernels fuse
     Mx, My = 2 * Nx, 2 * Ny
     g0 = torch.randn(Mx, My, P.n_t, device=dev, dtype=torch.float32)
+
     def cufft_rows_cols():
         t = torch.fft.rfft(g0, dim=1)[:, : Ny // 2 + 1, :]
         return torch.fft.fft(t, dim=0)
-    cufft_ms = timed_calls(cufft_rows_cols, k_parts)
+    cufft_ms = timed(cufft_rows_cols)
     del g0
+    own_rc = (prof["ned_rowfft"][0] / prof["ned_rowfft"][1] + prof["ned_colfft"][0] / prof["ned_colfft"][1]
+              if "ned_rowfft" in prof and "ned_colfft" in prof else None)
+
+    # the 128x128 sensor workload (the single reconstruction at 128x128x256)
+    Q = synth.c2()
+    voxels2 = int(np.prod(Q.grid.shape))
+    plan2 = pa.Plan(Q.xy, Q.n_t, Q.dt, Q.c, Q.grid.as_tuple(), weights=Q.h)
+    plan2.autotune()
+    q_g = torch.tensor(Q.g, dtype=torch.float32, device=dev)
+    q_f = torch.empty(Q.grid.shape, dtype=torch.float32, device=dev)
+    q_g2 = torch.empty_like(q_g)
+
+    def step2():
+        plan2.reconstruct(q_g, out=q_f)
+        plan2.adjoint(q_f, out=q_g2)
+    c2_ms = timed(step2)
+    c2_fwd_ms = timed(lambda: plan2.reconstruct(q_g, out=q_f))
+    c2_adj_ms = timed(lambda: plan2.adjoint(q_f, out=q_g2))
+    c2_cub_ms = timed(lambda: plan2.reconstruct_cubic(q_g, out=q_f))
     # the same output grid and samples with the sensors on the output lattice
     # (the lattice spatial step: no window spreading)
-    import numpy as np
-    xy_l = synth.lattice_positions(Nx, Ny, P.grid.dx, P.grid.dy)
-    plan_l = pa.Plan(xy_l, P.n_t, P.dt, P.c, P.grid.as_tuple())
-    g_l = torch.randn(Nx * Ny, P.n_t, device=dev, dtype=torch.float32)
+    xy_l = synth.lattice_positions(128, 128, Q.grid.dx, Q.grid.dy)
+    plan_l = pa.Plan(xy_l, Q.n_t, Q.dt, Q.c, Q.grid.as_tuple())
+    g_l = torch.randn(128 * 128, Q.n_t, device=dev, dtype=torch.float32)
+
     def lattice_step():
-        plan_l.reconstruct(g_l, out=f)
-        plan_l.adjoint(f, out=g_l)
-    lat_ms = timed_calls(lattice_step, k_parts) if plan_l.is_lattice else None
+        plan_l.reconstruct(g_l, out=q_f)
+        plan_l.adjoint(q_f, out=g_l)
+    lat_ms = timed(lattice_step) if plan_l.is_lattice else None
     plan_l.close()
     del g_l
     # the d = 2 operator: 256 sensors on a 51.2 mm line (jittered, centre-dense),
@@ -387,25 +541,27 @@ def run_ours(args):
     X2 = nx2 * 1e-4
     x2 = np.sort(np.concatenate([rng2.uniform(-X2 / 2, X2 / 2, m2 // 2),
                                  rng2.normal(0.0, X2 / 8, m2 // 2).clip(-X2 / 2, X2 / 2 - 1e-7)]))
-    plan_2 = pa.Plan2D(x2, nt2, 20e-9, P.c, (nx2, nz2, 1e-4, 1e-4))
+    plan_2 = pa.Plan2D(x2, nt2, 20e-9, Q.c, (nx2, nz2, 1e-4, 1e-4))
     g_2 = torch.randn(m2, nt2, device=dev, dtype=torch.float32)
     f_2 = torch.empty(nx2, nz2, device=dev, dtype=torch.float32)
+
     def d2_step():
         plan_2.reconstruct(g_2, out=f_2)
         plan_2.adjoint(f_2, out=g_2)
-    d2_ms = timed_calls(d2_step, k_parts)
+    d2_ms = timed(d2_step)
     plan_2.close()
     del g_2, f_2
     # the position gradient (data gradient A^T fbar included) alone, and the
-    # variational workload on the same plan: L = ||A(xy) g - target||^2 +
+    # variational workload at 128x128x256: L = ||A(xy) g - target||^2 +
     # 1e-3 TV_eps(A(xy) g), eps = 1e-8 (isotropic, forward differences),
     # target = the phantom's balls sampled at the voxel centres, backpropagated
-    # to g and xy through the autograd function (loss terms in torch, FP64 sums)
-    fb_v = torch.randn(P.grid.shape, device=dev, dtype=torch.float32)
-    pg_ms = timed_calls(lambda: plan.position_grad(g, fb_v), k_parts)
-    target_d = torch.tensor(P.voxelised(), dtype=torch.float32, device=dev)
-    xy_v = torch.tensor(P.xy, dtype=torch.float64, requires_grad=True)
-    g_v = g.detach().clone().requires_grad_(True)
+    # to g and xy through the autograd function (loss terms in torch, FP64 sums;
+    # positions as a CUDA tensor, re-binned on the device when they change)
+    fb_v = torch.randn(Q.grid.shape, device=dev, dtype=torch.float32)
+    pg_ms = timed(lambda: plan2.position_grad(q_g, fb_v))
+    target_d = torch.tensor(Q.voxelised(), dtype=torch.float32, device=dev)
+    xy_v = torch.tensor(Q.xy, dtype=torch.float32, device=dev, requires_grad=True)
+    g_v = q_g.detach().clone().requires_grad_(True)
 
     def var_loss(fv):
         fv = fv.to(torch.float64)
@@ -418,27 +574,31 @@ def run_ours(args):
     def var_step():
         g_v.grad = None
         xy_v.grad = None
-        var_loss(pa.reconstruct(g_v, xy_v, plan)).backward()
-    var_ms = timed_calls(var_step, k_parts)
+        var_loss(pa.reconstruct(g_v, xy_v, plan2)).backward()
+    var_ms = timed(var_step)
     del fb_v, target_d, g_v
+    plan2.close()
+    del q_g, q_f, q_g2
+    torch.cuda.empty_cache()
+    batch = batch_timings(pa, synth, dev, steps=5, warmup=3) if not args.no_batch else None
     parts = {"forward": {"ms": fwd_ms, "voxels_per_s": voxels / (fwd_ms / 1e3)},
              "adjoint": {"ms": adj_ms, "voxels_per_s": voxels / (adj_ms / 1e3)},
-             "cubic_baseline_forward": {"ms": cub_ms, "voxels_per_s": voxels / (cub_ms / 1e3)},
-             "cufft_row_col_transforms_ms": cufft_ms,
-             "lattice_sensors_fwd_adj": None if lat_ms is None else
-             {"ms": lat_ms, "voxels_per_s": voxels / (lat_ms / 1e3),
-              "workload": f"{Nx}x{Ny} sensors on the output lattice, same samples and output"},
+             "cubic_baseline_forward": {"ms": cub_ms, "voxels_per_s": voxels / (cub_ms / 1e3),
+                                        "rel_l2_vs_nedner_forward": cub_vs_ned},
+             "position_grad": {"ms": pg3_ms, "voxels_per_s": voxels / (pg3_ms / 1e3),
+                               "what": "pa_position_grad: A^T fbar and dL/dxy of <fbar, A(xy) g>"},
+             "cufft_row_col_transforms_ms": cufft_ms, "own_row_col_transforms_ms": own_rc,
+             "c2_fwd_adj": {"workload": WORKLOAD_C2, "ms": c2_ms, "voxels_per_s": voxels2 / (c2_ms / 1e3),
+                            "forward_ms": c2_fwd_ms, "adjoint_ms": c2_adj_ms, "cubic_forward_ms": c2_cub_ms,
+                            "position_grad_ms": pg_ms,
+                            "variational_fwd_bwd_ms": var_ms,
+                            "variational_what": "L = ||A(xy) g - target||^2 + 1e-3 TV_eps(A(xy) g); forward, "
+                                                "loss and backward to g and xy through the autograd function",
+                            "lattice_sensors_fwd_adj_ms": lat_ms},
              "d2_fwd_adj": {"ms": d2_ms, "pixels_per_s": nx2 * nz2 / (d2_ms / 1e3),
                             "workload": f"d = 2: {m2} sensors on a {X2 * 1e3:.1f} mm line, {nt2} samples at 20 ns, "
                                         f"image {nx2}x{nz2} at 100 um"},
-             "position_grad": {"ms": pg_ms, "voxels_per_s": voxels / (pg_ms / 1e3),
-                               "what": "pa_position_grad: A^T fbar and dL/dxy of <fbar, A(xy) g>"},
-             "variational_fwd_bwd": {"ms": var_ms, "voxels_per_s": voxels / (var_ms / 1e3),
-                                     "what": "L = ||A(xy) g - target||^2 + 1e-3 TV_eps(A(xy) g); forward, loss and "
-                                             "backward to g and xy through the autograd function"},
-             "own_row_col_transforms_ms": (prof["ned_rowfft"][0] / prof["ned_rowfft"][1]
-                                           + prof["ned_colfft"][0] / prof["ned_colfft"][1])
-             if "ned_rowfft" in prof and "ned_colfft" in prof else None,
+             "batch": batch,
              "median_of": k_parts}
 
     # end to end through the public API with host buffers: every step copies
@@ -506,15 +666,15 @@ def run_ours(args):
         e2e_ms, e2e_serial_ms = float(t[0].item()), float(t[1].item())
     e2e = {"value": world * voxels / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": g_h.numel() * 4,
            "d2h_bytes_per_step": (f_h.numel() + g2_h.numel()) * 4, "ms_per_step": e2e_ms,
-           "overlap": "H2D of step k+1 and D2H of step k overlap the compute (two buffer sets, three streams)",
-           "serial_ms_per_step": e2e_serial_ms}
+           "overlap": "pipelined: H2D of step k+1 and D2H of step k overlap the compute (two buffer sets, "
+                      "three streams); serial_* is copy, compute, copy on one stream",
+           "serial_ms_per_step": e2e_serial_ms, "serial_value": world * voxels / (e2e_serial_ms / 1e3)}
+    del bufs
 
-    cpu = None
+    cpu, acc = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = cpu_baseline_subprocess(1)
-        cpu = {"value": r["voxels"] / r["t"], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "one FP64 forward+adjoint of the full workload (NUFFT oracle, width 16), "
-                         "single thread", "seconds": r["t"]}
+        cpu, acc = cpu_baseline(P, pa, dev)
+        parts["cubic_baseline_forward"]["accuracy_on_a_tile"] = acc
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -537,68 +697,20 @@ def run_ours(args):
 
 
 def run_batch(args):
-    """The uneven batch (64 instances, N uniform over the 7-smooth integers in
-    [64, 256], T in {256, 512, 1024}, output N x N x 2T): pa_batch_run
-    (the instances' launches as concurrent branches of a CUDA graph; and the
-    mode with one launch per stage over all instances) against 64 sequential
-    single-plan reconstructions.  Seeded random data (timing only)."""
-    import numpy as np
+    """The uneven batch alone (see batch_timings)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     import paper_1501_02946_gb300 as pa
     import synth
-
     dev = torch.device("cuda", 0)
-    shapes = synth.batch_shapes()
-    rng = np.random.default_rng(1505)
-    plans, gs, fs = [], [], []
-    voxels = 0
-    for k, (n_side, n_t) in enumerate(shapes):
-        xy = synth.jittered_lattice(rng, n_side, n_side, 1e-4, 1e-4)
-        grid = (n_side, n_side, 2 * n_t, 1e-4, 1e-4, 1e-4)
-        plans.append(pa.Plan(xy, n_t, 20e-9, synth.C_WATER, grid))
-        gs.append(torch.randn(n_side * n_side, n_t, device=dev, dtype=torch.float32))
-        fs.append(torch.empty(n_side, n_side, 2 * n_t, device=dev, dtype=torch.float32))
-        voxels += n_side * n_side * 2 * n_t
-    batch = pa.Batch(plans)               # concurrent per-instance branches
-    batch_st = pa.Batch(plans, mode=1)    # one launch per stage over all instances
-    stream = torch.cuda.current_stream(dev)
-
-    def seq():
-        for p, g, f in zip(plans, gs, fs):
-            p.reconstruct(g, out=f)
-
-    def bat():
-        batch.run(gs, fs)
-
-    def bat_st():
-        batch_st.run(gs, fs)
-
-    res = {}
-    for name, fn in (("batch_graph", bat), ("batch_graph_stage_launches", bat_st), ("sequential_64", seq)):
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize(dev)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        for a, b in evs:
-            a.record(stream)
-            fn()
-            b.record(stream)
-        torch.cuda.synchronize(dev)
-        ms = statistics.median(a.elapsed_time(b) for a, b in evs)
-        res[name] = {"ms": ms, "voxels_per_s": voxels / (ms / 1e3)}
-    out = {"metric": "voxels/s (uneven batch of 64 forward reconstructions)", "value": res["batch_graph"]["voxels_per_s"],
-           "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": res["batch_graph"]["ms"], "higher_is_better": True, "dtype": "f32", "data": "synthetic (seeded random)",
-           "config": {"workload": "64 instances, N in 7-smooth [64, 256], T in {256, 512, 1024}, output N x N x 2T",
-                      "total_voxels": voxels, "shapes": shapes},
-           "comparison": res, "speedup_vs_sequential": res["sequential_64"]["ms"] / res["batch_graph"]["ms"]}
+    res = batch_timings(pa, synth, dev, args.steps, args.warmup)
+    out = {"metric": "voxels/s (uneven batch of 64 forward reconstructions)",
+           "value": res["batch_graph"]["voxels_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": res["batch_graph"]["ms"], "higher_is_better": True,
+           "dtype": "f32", "data": "synthetic (seeded random)", "config": {"workload": res["workload"]},
+           "comparison": res}
     print(json.dumps(out))
-    batch.close()
-    batch_st.close()
-    for p in plans:
-        p.close()
     return 0
 
 
@@ -609,7 +721,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batch", action="store_true", help="time the uneven 64-instance batch instead")
+    ap.add_argument("--no-batch", action="store_true", help="leave the uneven batch out of the parts")
+    ap.add_argument("--batch", action="store_true", help="time the uneven 64-instance batch alone")
     ap.add_argument("--profile-step", action="store_true",
                     help="run one step between cudaProfilerStart/Stop (for ncu --profile-from-start off) and exit")
     args = ap.parse_args()
