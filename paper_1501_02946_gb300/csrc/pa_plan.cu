@@ -385,9 +385,6 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
     if (P->d_entries) {
       PA_CUDA(cudaStreamSynchronize(stream));
       cudaFree(P->d_entries);
-  cudaFree(P->d_rebin);
-  cudaFree(P->d_lattice);
-  cudaFree(P->d_desc_lat);
       P->d_entries = nullptr;
       P->entries_bytes = 0;
     }
@@ -420,6 +417,9 @@ void free_plan(pa_plan *P) {
   cudaFree(P->d_static);
   cudaFree(P->d_work);
   cudaFree(P->d_entries);
+  cudaFree(P->d_rebin);
+  cudaFree(P->d_lattice);
+  cudaFree(P->d_desc_lat);
   delete P;
 }
 

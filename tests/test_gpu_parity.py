@@ -278,6 +278,46 @@ def test_update_positions_on_device_matches_host(name):
     assert rel(gd, gh) <= 1e-5
 
 
+def test_position_updates_that_grow_the_entry_lists():
+    """Host and device position updates in turn, where a host update makes
+    the spread entry lists grow (sensors whose base cells all sit at the
+    last row of a strip meet two strips, lattice sensors three): every step
+    gives the image of a fresh plan with those positions, and the device
+    re-binning scratch and the lattice tables stay valid across the growth."""
+    grid = synth.Grid(32, 32, 64, 1e-4, 1e-4, 1e-4)
+    X = grid.nx * grid.dx
+    rng = np.random.default_rng(25)
+    n = 32
+    # oversampled cell coordinate U = 64 x / X + 32 with floor(U) = 3 mod 4
+    k = np.arange(n)
+    U = (4 * (k % 16) + 3.25)[:, None] + np.zeros((1, n))
+    V = (4 * (k % 16) + 3.5)[None, :] + np.zeros((n, 1))
+    xy_few = np.stack([(U.ravel() - 32) * X / 64, (V.ravel() - 32) * X / 64], axis=1)
+    xy_lat = synth.lattice_positions(32, 32, grid.dx, grid.dy)
+    h = np.full(n * n, X * X / (n * n))
+    g = rng.normal(size=(n * n, 64))
+    gd = dev(g)
+
+    def fresh(xy):
+        return host(pa().Plan(xy, 64, 20e-9, 1500.0, grid.as_tuple(), weights=h).reconstruct(gd))
+
+    plan = pa().Plan(xy_few, 64, 20e-9, 1500.0, grid.as_tuple(), weights=h)
+    n0 = plan.info()
+    xy_j = (xy_few + rng.uniform(-1e-6, 1e-6, xy_few.shape)).astype(np.float32)
+    plan.update_positions(torch.tensor(xy_j, device="cuda"))          # device: re-binning scratch
+    assert rel(host(plan.reconstruct(gd)), fresh(xy_j.astype(np.float64))) <= 1e-6
+    plan.update_positions(xy_lat)                                       # host: the entry lists grow
+    assert plan.is_lattice
+    assert np.array_equal(host(plan.reconstruct(gd)), fresh(xy_lat))
+    plan.update_positions(torch.tensor(xy_j, device="cuda"))          # device again, after the growth
+    assert rel(host(plan.reconstruct(gd)), fresh(xy_j.astype(np.float64))) <= 1e-6
+    plan.update_positions(xy_lat)
+    assert np.array_equal(host(plan.reconstruct(gd)), fresh(xy_lat))
+    assert plan.status() == 0
+    assert n0["n_sensors"] == n * n
+    plan.close()
+
+
 def test_update_positions_on_device_rejects_nonfinite():
     P = synth.c1()
     plan = plan_of(P)
