@@ -85,7 +85,7 @@ class Plan:
                                     _stream_ptr(self.device))
         check(rc)
         self._ptr = ptr
-        self._xy = xy.copy()
+        self._xy, self._xy_dev, self._dev_key = xy.copy(), None, None
 
     # -- properties
     @property
@@ -220,22 +220,28 @@ class Plan:
         the host in FP64) or a CUDA tensor (float32, re-binned on the device)."""
         torch = _torch()
         if isinstance(xy, torch.Tensor) and xy.is_cuda:
-            t = xy.detach().to(torch.float32).contiguous().reshape(-1, 2)
+            t = xy.detach().to(torch.float32).reshape(-1, 2).clone()
             if t.shape[0] != self.M:
                 raise ValueError("update_positions needs one position per sensor")
             check(_lib.load().pa_plan_update_positions_device(self.handle, c_void_p(t.data_ptr()),
                                                               _stream_ptr(self.device)))
-            self._xy = t.cpu().numpy().astype(np.float64)
+            # the host copy is made only if `positions` is asked for
+            self._xy, self._xy_dev = None, t
+            self._dev_key = None
             return
         xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(-1, 2))
         if xy.shape[0] != self.M:
             raise ValueError("update_positions needs one position per sensor")
         check(_lib.load().pa_plan_update_positions(self.handle, xy.ctypes.data_as(c_void_p),
                                                    _stream_ptr(self.device)))
-        self._xy = xy.copy()
+        self._xy, self._xy_dev = xy.copy(), None
+        self._dev_key = None
 
     @property
     def positions(self):
+        """The plan's current sensor positions (M, 2) as a host float64 array."""
+        if self._xy is None:
+            self._xy = self._xy_dev.cpu().numpy().astype(np.float64)
         return self._xy.copy()
 
     def buffer(self, which):
@@ -351,6 +357,7 @@ class Plan2D(Plan):
         check(rc)
         self._ptr = ptr
         self._xy = np.stack([x, np.zeros_like(x)], axis=1)
+        self._xy_dev, self._dev_key = None, None
 
     @property
     def image_shape(self):
@@ -419,9 +426,19 @@ def _autograd():
 
         @staticmethod
         def forward(ctx, g, xy, plan, voronoi=False):
-            xy_np = xy.detach().to("cpu", torch.float64).numpy()
-            if not np.array_equal(xy_np, plan.positions):
-                plan.update_positions(xy_np)
+            if xy.is_cuda:
+                # positions on the device are re-binned on the device, without
+                # a copy to the host, unless they are the very tensor (same
+                # object, no in-place change since: same version counter) the
+                # plan was last given
+                key = getattr(plan, "_dev_key", None)
+                if key is None or key[0] is not xy or key[1] != xy._version:
+                    plan.update_positions(xy)
+                    plan._dev_key = (xy, xy._version)
+            else:
+                xy_np = xy.detach().to("cpu", torch.float64).numpy()
+                if not np.array_equal(xy_np, plan.positions):
+                    plan.update_positions(xy_np)
             if voronoi:
                 plan.set_weights(plan.voronoi_weights())
             ctx.plan = plan
@@ -463,7 +480,14 @@ def ReconstructFunction():
 def reconstruct(g, xy, plan, voronoi=False):
     """Differentiable reconstruction: f = A(xy) g.  With voronoi=True the
     detector weights are the Voronoi cells of xy (set on every call) and the
-    position gradient includes their dependence on xy."""
+    position gradient includes their dependence on xy.
+
+    xy on the host is compared with the plan's positions and re-binned on the
+    host when it differs; xy on the GPU (float32 is enough: the cell
+    coordinates are formed in FP64 on the device) is re-binned on the device
+    unless it is the same tensor as on the last call with no in-place change
+    since (its version counter; a change through .data bypasses the counter
+    and is not seen)."""
     return ReconstructFunction().apply(g, xy, plan, voronoi)
 
 

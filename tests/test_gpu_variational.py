@@ -90,3 +90,32 @@ def test_variational_c2_gradients_and_descent(c2):
     print(f"c2 variational: L0 {L0:.6e}; decrease / first-order prediction: data {r_g:.4f}, positions {r_xy:.4f}")
     assert 0.8 <= r_g <= 1.2
     assert 0.8 <= r_xy <= 1.2
+
+
+def test_autograd_positions_on_the_device():
+    """Positions given as a CUDA tensor are re-binned on the device (no copy
+    to the host): the gradients equal those of the same positions given on
+    the host to float rounding (the device path takes float32 positions), a
+    second call with the same tensor keeps the binning, and an in-place step
+    of the tensor is seen (its version counter)."""
+    P = synth.c1()
+    target_d = dev(P.voxelised())
+    xy32 = P.xy.astype(np.float32).astype(np.float64)
+    plan_h, plan_d = plan_of(P), plan_of(P)
+    _, L_h, gg_h, gxy_h = _forward_backward(P, plan_h, target_d, xy0=xy32)
+    xy_d = torch.tensor(xy32, dtype=torch.float32, device="cuda", requires_grad=True)
+    for call in range(2):
+        g = dev(P.g).requires_grad_(True)
+        L = varloss.loss(pa().reconstruct(g, xy_d, plan_d), target_d)
+        xy_d.grad = None
+        L.backward()
+        assert abs(float(L) - L_h) <= 1e-6 * abs(L_h)
+        assert rel(host(g.grad), host(gg_h)) <= 1e-5
+        assert rel(host(xy_d.grad), gxy_h.numpy()) <= 1e-4
+        assert plan_d._xy is None            # no host copy of the positions was made
+    with torch.no_grad():
+        xy_d -= 3e-6 * xy_d.grad.sign()
+    f2 = pa().reconstruct(dev(P.g), xy_d, plan_d)
+    ref = plan_of(P)
+    ref.update_positions(xy_d.detach().double().cpu().numpy())
+    assert rel(host(f2), host(ref.reconstruct(dev(P.g)))) <= 1e-5
