@@ -340,7 +340,7 @@ template <int R, int DIR, int PADSH>
 __device__ __forceinline__ void fft_stage_p2(float2 *buf, int estride, int lgnb, int lgL, int lgNs,
                                              const float2 *__restrict__ tw, int tid, int lgT, int bar_id) {
   constexpr int IPT = Ipt<R>::v;
-  constexpr int LGR = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
+  constexpr int LGR = R == 32 ? 5 : (R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1)));
   constexpr int LGIPT = IPT == 1 ? 0 : (IPT == 2 ? 1 : 2);
   const int lgnj = lgL - LGR;
   const int nj = 1 << lgnj;
@@ -395,6 +395,11 @@ __device__ __forceinline__ void fft_stage_p2(float2 *buf, int estride, int lgnb,
 template <int LGL, int DIR, int PADSH = 0>
 __device__ __forceinline__ void fft_fixed(float2 *buf, int estride, int lgnb, int lgT, const float2 *__restrict__ tw,
                                           int tid, int bar_id = 0) {
+  if constexpr (LGL == 9) {  // 16 x 32: two passes through shared memory instead of three
+    fft_stage_p2<16, DIR, PADSH>(buf, estride, lgnb, LGL, 0, tw, tid, lgT, bar_id);
+    fft_stage_p2<32, DIR, PADSH>(buf, estride, lgnb, LGL, 4, tw, tid, lgT, bar_id);
+    return;
+  }
   constexpr int n16 = LGL / 4, rem = LGL % 4;
 #pragma unroll
   for (int st = 0; st < n16; ++st) fft_stage_p2<16, DIR, PADSH>(buf, estride, lgnb, LGL, 4 * st, tw, tid, lgT, bar_id);

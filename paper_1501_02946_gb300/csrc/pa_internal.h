@@ -83,6 +83,17 @@ struct InstDesc {
   const int *sp_start;
   const int *sp_m;
   const float4 *sp_w;
+  // the same entries for the staged spread: block b = strip * ceil(My / 8)
+  // + (q / 8) stages the g rows of its union of sensors (caller indices
+  // sp_um[sp_ustart[b] ..  sp_ustart[b + 1]), in sorted order) in shared
+  // memory, and entry e names its sensor by the position sp_slot[e] in that
+  // union; sp_urows is the number of rows the staging buffer holds (rows past
+  // it are read from global memory).  Null when not built (then the spread
+  // reads g through sp_m).
+  const int *sp_slot;
+  const int *sp_ustart;
+  const int *sp_um;
+  int sp_urows;
   // deconvolution factors 1/phihat (window normalised to phi(0) = 1)
   const float *invphx;  // [nX1], jx = ix - hx, at jx / Mx
   const float *invphy;  // [nY1], jy, at jy / My
@@ -138,6 +149,8 @@ struct IoPtrs {
 
 // Tile shapes (chosen on the host; kernels are templated on them).
 constexpr int kSpreadP = 4;      // oversampled rows per forward spread strip
+constexpr int kSpreadQC = 8;     // columns per spread block (one warp each)
+constexpr int kSpreadUrowsMax = 128;  // g rows the staged spread holds in shared memory
 constexpr int kColNC = 16;       // samples per column-FFT tile
 constexpr int kInterpNC = 32;    // samples per adjoint interpolation tile
 constexpr int kImgZC = 16;       // depth samples per inverse-x tile

@@ -20,12 +20,31 @@
 #ifndef PA_INTERP_MINB
 #define PA_INTERP_MINB 2
 #endif
+// Spread: entries whose g rows load together, and the blocks per SM its
+// register budget is set for.
+#ifndef PA_SPREAD_B
+#define PA_SPREAD_B 4
+#endif
+#ifndef PA_SPREAD_MINB
+#define PA_SPREAD_MINB 2
+#endif
+// 1: single-plan spreads stage their g rows in shared memory (k_spread_tile)
+#ifndef PA_SPREAD_TILE
+#define PA_SPREAD_TILE 1
+#endif
 
 namespace pa {
 
 namespace {
 
 constexpr int kThreadsCol = 256;
+// Block size of the persistent transform pipelines of length 2^LGL: 512
+// threads from length 512 on, where the two tile buffers leave room for one
+// block per SM only.
+template <int LGL>
+struct PipeThreads {
+  static constexpr int v = LGL >= 9 ? 512 : 256;
+};
 constexpr int kThreadsSpread = 256;  // 8 warps = 8 grid columns of one strip
 constexpr int kThreadsInterp = 256;
 
@@ -92,7 +111,7 @@ __device__ __forceinline__ void fma_entry(float (&acc)[kSpreadP][S], const float
 }
 
 template <int S>
-__global__ void __launch_bounds__(kThreadsSpread, 2) k_spread(const InstDesc *__restrict__ descs,
+__global__ void __launch_bounds__(kThreadsSpread, PA_SPREAD_MINB) k_spread(const InstDesc *__restrict__ descs,
                                                               const int2 *__restrict__ work, IoPtrs io0,
                                                               const IoPtrs *__restrict__ io_table) {
   griddep_enter();  // the previous kernel of the stream has completed
@@ -131,7 +150,7 @@ __global__ void __launch_bounds__(kThreadsSpread, 2) k_spread(const InstDesc *__
   // products (one coalesced load each), entry b reaches every lane by a
   // shuffle.  Within a window the g rows of batch k + 1 (B entries) load
   // while batch k is summed, so only the g loads remain on the path.
-  constexpr int B = 4;
+  constexpr int B = PA_SPREAD_B;
   for (int e = e0; e < e1; e += 32) {
     const int cnt = min(32, e1 - e);
     int mj = 0;
@@ -191,6 +210,111 @@ __global__ void __launch_bounds__(kThreadsSpread, 2) k_spread(const InstDesc *__
       for (int u = 0; u < S; ++u)
         if (n + u < Nt) dst[u] = acc[r][u];
     }
+  }
+}
+
+// The spread with the block's g rows staged in shared memory.  A block
+// (8 warps = the 8 columns q0 .. q0 + 7 of one strip, one chunk of CH = 32 S
+// samples) first copies the chunk of every g row its entries use -- its
+// union of sensors, in sorted order -- into shared memory with one bulk copy
+// (TMA engine) per row, then sums exactly as k_spread does (same entries,
+// same order, so the same results), reading the samples from shared memory
+// instead of through L1.  Lane l holds the samples n0 + 4 l + 128 k
+// (k < S / 4): 16-byte shared loads that are bank-conflict free.  Union rows
+// past the buffer's sp_urows rows are read from global memory.
+template <int S>
+__global__ void __launch_bounds__(kThreadsSpread, 2) k_spread_tile(const InstDesc *__restrict__ descs, IoPtrs io) {
+  griddep_enter();  // the previous kernel of the stream has completed
+  constexpr int P = kSpreadP, QC = kSpreadQC, CH = 32 * S, K4 = S / 4;
+  static_assert(P == 4 && QC * 32 == kThreadsSpread, "tile shape");
+  static_assert(S % 4 == 0, "samples per lane load as float4");
+  extern __shared__ __align__(128) float4 smem_a128[];
+  float *Gs = reinterpret_cast<float *>(smem_a128);  // [sp_urows][CH]
+  __shared__ __align__(8) uint64_t bar;
+  const InstDesc &d = descs[0];
+  const int Mx = d.Mx, My = d.My, Nt = d.Nt;
+  const int nstrips = (Mx + P - 1) / P, ncb = (My + QC - 1) / QC, nch = (Nt + CH - 1) / CH;
+  const int tile = blockIdx.x;
+  if (tile >= nstrips * ncb * nch) return;
+  const int st = tile % nstrips;
+  const int cb = (tile / nstrips) % ncb;
+  const int c = tile / (nstrips * ncb);
+  const int n0 = c * CH;
+  const int nv = min(CH, Nt - n0);  // samples of the chunk (a multiple of 4)
+  const float *__restrict__ g = io.g_in;
+  const int blk = st * ncb + cb;
+  const int u0 = __ldg(d.sp_ustart + blk), nu = __ldg(d.sp_ustart + blk + 1) - u0;
+  const int ur = min(nu, d.sp_urows);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0) mbar_arrive_expect_tx(&bar, uint32_t(ur) * uint32_t(nv) * 4u);
+  for (int u = tid; u < ur; u += kThreadsSpread)
+    bulk_g2s(Gs + (size_t)u * CH, g + (size_t)__ldg(d.sp_um + u0 + u) * Nt + n0, uint32_t(nv) * 4u, &bar);
+  if (__syncthreads_or(!mbar_wait(&bar, 0))) {
+    if (tid == 0) atomicOr(d.status, kStatusWaitTimeout);
+    mbar_wait(&bar, 0);  // one more bounded wait for the copies in flight
+    return;
+  }
+  const int q = cb * QC + (tid >> 5);
+  if (q >= My) return;  // whole warps leave; no block barrier follows
+  const int lane = tid & 31;
+  const int p0 = st * P;
+  const int *__restrict__ es = d.sp_slot;
+  const float4 *__restrict__ ew = d.sp_w;
+  const int e0 = __ldg(d.sp_start + (size_t)st * My + q), e1 = __ldg(d.sp_start + (size_t)st * My + q + 1);
+  float4 acc[P][K4];
+#pragma unroll
+  for (int r = 0; r < P; ++r)
+#pragma unroll
+    for (int k = 0; k < K4; ++k) acc[r][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  // entries in windows of 32: lane j loads entry j's slot and tap products,
+  // entry b reaches every lane by shuffles
+  for (int e = e0; e < e1; e += 32) {
+    const int cnt = min(32, e1 - e);
+    int sj = 0;
+    float4 wj = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane < cnt) {
+      sj = __ldg(es + e + lane);
+      wj = __ldg(ew + e + lane);
+    }
+#pragma unroll 4
+    for (int b = 0; b < cnt; ++b) {
+      const int slot = __shfl_sync(0xffffffffu, sj, b);
+      const float4 w = make_float4(__shfl_sync(0xffffffffu, wj.x, b), __shfl_sync(0xffffffffu, wj.y, b),
+                                   __shfl_sync(0xffffffffu, wj.z, b), __shfl_sync(0xffffffffu, wj.w, b));
+      float4 v[K4];
+      if (slot < ur) {
+        const float4 *row = reinterpret_cast<const float4 *>(Gs + (size_t)slot * CH) + lane;
+#pragma unroll
+        for (int k = 0; k < K4; ++k) v[k] = row[32 * k];
+      } else {
+        const float *row = g + (size_t)__ldg(d.sp_um + u0 + slot) * Nt + n0 + 4 * lane;
+#pragma unroll
+        for (int k = 0; k < K4; ++k)
+          v[k] = 4 * lane + 128 * k < nv ? __ldg(reinterpret_cast<const float4 *>(row + 128 * k))
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < K4; ++k) {
+        fma4(w.x, v[k], acc[0][k]);
+        fma4(w.y, v[k], acc[1][k]);
+        fma4(w.z, v[k], acc[2][k]);
+        fma4(w.w, v[k], acc[3][k]);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < P; ++r) {
+    const int p = p0 + r;
+    if (p >= Mx) break;
+    float *dst = d.G0 + ((size_t)p * My + q) * Nt + n0 + 4 * lane;
+#pragma unroll
+    for (int k = 0; k < K4; ++k)
+      if (4 * lane + 128 * k < nv) *reinterpret_cast<float4 *>(dst + 128 * k) = acc[r][k];
   }
 }
 
@@ -332,7 +456,7 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft(const InstDesc *__restri
 // start at rows hx and -1 (the row before 0 reads as zeros and lands on a
 // bin that is cleared anyway).
 template <bool ADJ, int LGL>
-__global__ void __launch_bounds__(kThreadsCol) k_colfft_pipe(const InstDesc *__restrict__ descs, int nwork,
+__global__ void __launch_bounds__(PipeThreads<LGL>::v) k_colfft_pipe(const InstDesc *__restrict__ descs, int nwork,
                                                              const __grid_constant__ CUtensorMap map, int use_map) {
   griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
@@ -406,7 +530,7 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft_pipe(const InstDesc *__r
 // With use_map, a tile arrives as boxes of the 2-D tensor map over G0
 // (dims Nt, Mx My; box 32 x min(My, 256)) instead of one copy per row q.
 template <int LGL>
-__global__ void __launch_bounds__(kThreadsCol) k_rowfft_pipe(const InstDesc *__restrict__ descs, int nwork,
+__global__ void __launch_bounds__(PipeThreads<LGL>::v) k_rowfft_pipe(const InstDesc *__restrict__ descs, int nwork,
                                                              const __grid_constant__ CUtensorMap map, int use_map) {
   griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
@@ -518,7 +642,7 @@ __global__ void __launch_bounds__(kThreadsCol) k_rowifft(const InstDesc *__restr
 // With use_map (nY1 <= 256), the staged rows arrive as one box of the 2-D
 // tensor map over T (floats; dims 2 Nt, Mx nY1; box 64 x nY1).
 template <int LGL>
-__global__ void __launch_bounds__(kThreadsCol) k_rowifft_pipe(const InstDesc *__restrict__ descs, int nwork,
+__global__ void __launch_bounds__(PipeThreads<LGL>::v) k_rowifft_pipe(const InstDesc *__restrict__ descs, int nwork,
                                                               const __grid_constant__ CUtensorMap map, int use_map) {
   griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
@@ -1030,7 +1154,24 @@ static cudaError_t set_smem(K kernel, size_t smem) {
   return cudaSuccess;
 }
 
+// The staged spread for single-plan launches with 16-byte sample rows (g
+// 16-byte aligned, Nt % 4 == 0) whose union lists were built.
+template <int S>
+static cudaError_t launch_spread_tile(const Launch &L) {
+  const InstDesc &h = *L.host;
+  const size_t smem = size_t(h.sp_urows > 0 ? h.sp_urows : 1) * 32 * S * sizeof(float);
+  auto kern = k_spread_tile<S>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(kern, blocks_spread(h, S), kThreadsSpread, smem, L.stream, L.descs, L.io);
+}
+
 cudaError_t launch_spread(const Launch &L, int spl) {
+  if (L.host && !L.work && L.host->sp_slot && (L.host->Nt % 4) == 0 &&
+      (reinterpret_cast<uintptr_t>(L.io.g_in) & 15u) == 0 && PA_SPREAD_TILE) {
+    if (spl == 8) return launch_spread_tile<8>(L);
+    if (spl == 4) return launch_spread_tile<4>(L);
+  }
   if (spl == 8) return launch_pdl(k_spread<8>, L.nblocks, kThreadsSpread, 0, L.stream, L.descs, L.work, L.io, L.io_table);
   if (spl == 4) return launch_pdl(k_spread<4>, L.nblocks, kThreadsSpread, 0, L.stream, L.descs, L.work, L.io, L.io_table);
   return cudaErrorInvalidValue;
@@ -1072,7 +1213,7 @@ cudaError_t launch_rowfft(const Launch &L) {
                                   uint32_t(h.My < 256 ? h.My : 256), &map) ? 1 : 0;
     switch (lg) {
 #define PA_ROWFFT_CASE(G) \
-  case G: return launch_persistent_map(k_rowfft_pipe<G>, L, kThreadsCol, smem, nwork, map, use_map);
+  case G: return launch_persistent_map(k_rowfft_pipe<G>, L, PipeThreads<G>::v, smem, nwork, map, use_map);
       PA_ROWFFT_CASE(5) PA_ROWFFT_CASE(6) PA_ROWFFT_CASE(7) PA_ROWFFT_CASE(8) PA_ROWFFT_CASE(9)
 #undef PA_ROWFFT_CASE
       default: break;
@@ -1105,8 +1246,8 @@ cudaError_t launch_colfft(const Launch &L, bool adjoint) {
     switch (lg) {
 #define PA_COLFFT_CASE(G)                                                                                      \
   case G:                                                                                                      \
-    return adjoint ? launch_persistent_map(k_colfft_pipe<true, G>, L, kThreadsCol, smem, nwork, map, use_map)  \
-                   : launch_persistent_map(k_colfft_pipe<false, G>, L, kThreadsCol, smem, nwork, map, use_map);
+    return adjoint ? launch_persistent_map(k_colfft_pipe<true, G>, L, PipeThreads<G>::v, smem, nwork, map, use_map) \
+                   : launch_persistent_map(k_colfft_pipe<false, G>, L, PipeThreads<G>::v, smem, nwork, map, use_map);
       PA_COLFFT_CASE(5) PA_COLFFT_CASE(6) PA_COLFFT_CASE(7) PA_COLFFT_CASE(8) PA_COLFFT_CASE(9)
 #undef PA_COLFFT_CASE
       default: break;
@@ -1190,7 +1331,7 @@ cudaError_t launch_rowifft(const Launch &L) {
                                                   uint64_t(h.Nt) * sizeof(float2), 64u, uint32_t(h.nY1), &map) ? 1 : 0;
     switch (lg) {
 #define PA_ROWIFFT_CASE(G) \
-  case G: return launch_persistent_map(k_rowifft_pipe<G>, L, kThreadsCol, smem, nwork, map, use_map);
+  case G: return launch_persistent_map(k_rowifft_pipe<G>, L, PipeThreads<G>::v, smem, nwork, map, use_map);
       PA_ROWIFFT_CASE(5) PA_ROWIFFT_CASE(6) PA_ROWIFFT_CASE(7) PA_ROWIFFT_CASE(8) PA_ROWIFFT_CASE(9)
 #undef PA_ROWIFFT_CASE
       default: break;

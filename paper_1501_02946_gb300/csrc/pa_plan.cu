@@ -361,16 +361,44 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
   for (size_t k = 0; k + 1 < sp_start.size(); ++k) sp_start[k + 1] += sp_start[k];
   const size_t nent = size_t(sp_start.back());
   P->n_entries = nent;
-  std::vector<int> sp_m(nent);
+  std::vector<int> sp_m(nent), sp_i(nent);
   std::vector<float4> sp_w(nent);
   {
     std::vector<int> fill(sp_start.begin(), sp_start.end() - 1);
     for_each_entry([&](int st, int q, int i, float wyq, const float *wxr) {
       const size_t e = size_t(fill[size_t(st) * My + q]++);
       sp_m[e] = perm[i];
+      sp_i[e] = i;
       sp_w[e] = make_float4(wyq * wxr[0], wyq * wxr[1], wyq * wxr[2], wyq * wxr[3]);
     });
   }
+  // Union lists of the staged spread: per block of kSpreadQC columns of a
+  // strip, the sensors of its entries in sorted order, and each entry's
+  // position in its block's union.
+  const int QC = pa::kSpreadQC, ncb = (My + QC - 1) / QC;
+  std::vector<int> sp_slot(nent), sp_ustart(size_t(nstrips) * ncb + 1, 0), sp_um;
+  sp_um.reserve(nent / 4 + 16);
+  int umax = 0;
+  {
+    std::vector<int> uni;
+    for (int st = 0; st < nstrips; ++st) {
+      for (int cb = 0; cb < ncb; ++cb) {
+        const size_t blk = size_t(st) * ncb + cb;
+        const int qa = cb * QC, qb = std::min(My, qa + QC);
+        const size_t ea = size_t(sp_start[size_t(st) * My + qa]), eb = size_t(sp_start[size_t(st) * My + qb]);
+        uni.assign(sp_i.begin() + ea, sp_i.begin() + eb);
+        std::sort(uni.begin(), uni.end());
+        uni.erase(std::unique(uni.begin(), uni.end()), uni.end());
+        for (size_t e = ea; e < eb; ++e)
+          sp_slot[e] = int(std::lower_bound(uni.begin(), uni.end(), sp_i[e]) - uni.begin());
+        sp_ustart[blk] = int(sp_um.size());
+        for (int i : uni) sp_um.push_back(perm[i]);
+        umax = std::max(umax, int(uni.size()));
+      }
+    }
+    sp_ustart.back() = int(sp_um.size());
+  }
+  P->h.sp_urows = std::min(umax, pa::kSpreadUrowsMax);
   size_t off = 0;
   auto place = [&](size_t bytes) {
     const size_t o = off;
@@ -380,6 +408,9 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
   const size_t o_ss = place(sizeof(int) * sp_start.size());
   const size_t o_sm = place(sizeof(int) * nent);
   const size_t o_sw = place(sizeof(float4) * nent);
+  const size_t o_sl = place(sizeof(int) * sp_slot.size());
+  const size_t o_us = place(sizeof(int) * sp_ustart.size());
+  const size_t o_um = place(sizeof(int) * sp_um.size());
   const size_t need = off;
   if (need > P->entries_bytes) {
     if (P->d_entries) {
@@ -395,6 +426,9 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
   P->h.sp_start = reinterpret_cast<const int *>(V + o_ss);
   P->h.sp_m = reinterpret_cast<const int *>(V + o_sm);
   P->h.sp_w = reinterpret_cast<const float4 *>(V + o_sw);
+  P->h.sp_slot = reinterpret_cast<const int *>(V + o_sl);
+  P->h.sp_ustart = reinterpret_cast<const int *>(V + o_us);
+  P->h.sp_um = reinterpret_cast<const int *>(V + o_um);
   auto upv = [&](const void *dst, const void *src, size_t bytes) {
     return bytes ? cudaMemcpyAsync(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice, stream)
                  : cudaSuccess;
@@ -402,6 +436,9 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
   PA_CUDA(upv(P->h.sp_start, sp_start.data(), sizeof(int) * sp_start.size()));
   PA_CUDA(upv(P->h.sp_m, sp_m.data(), sizeof(int) * nent));
   PA_CUDA(upv(P->h.sp_w, sp_w.data(), sizeof(float4) * nent));
+  PA_CUDA(upv(P->h.sp_slot, sp_slot.data(), sizeof(int) * sp_slot.size()));
+  PA_CUDA(upv(P->h.sp_ustart, sp_ustart.data(), sizeof(int) * sp_ustart.size()));
+  PA_CUDA(upv(P->h.sp_um, sp_um.data(), sizeof(int) * sp_um.size()));
   // pageable sources: the copies above are complete when they return
   return PA_OK;
 }
@@ -1150,6 +1187,9 @@ int pa_plan_update_positions_device(pa_plan *plan, const float *xy_dev, void *st
   h.sp_start = reinterpret_cast<const int *>(V + o_ss);
   h.sp_m = a.sp_m;
   h.sp_w = a.sp_w;
+  // the staged spread's union lists are built on the host only
+  h.sp_slot = h.sp_ustart = h.sp_um = nullptr;
+  h.sp_urows = 0;
   // pageable source: the copy has consumed the descriptor when it returns
   PA_CUDA(cudaMemcpyAsync(P->d_desc, &h, sizeof(InstDesc), cudaMemcpyHostToDevice, s));
   return PA_OK;
