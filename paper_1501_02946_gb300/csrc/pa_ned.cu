@@ -20,6 +20,9 @@
 #ifndef PA_INTERP_MINB
 #define PA_INTERP_MINB 2
 #endif
+#ifndef PA_INTERP_THREADS
+#define PA_INTERP_THREADS 256
+#endif
 // Spread: entries whose g rows load together, and the blocks per SM its
 // register budget is set for.
 #ifndef PA_SPREAD_B
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(kThreadsSpread, 2) k_spread_tile(const InstDes
   const int blk = st * ncb + cb;
   const int u0 = __ldg(d.sp_ustart + blk), nu = __ldg(d.sp_ustart + blk + 1) - u0;
   const int ur = min(nu, d.sp_urows);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   if (tid == 0) {
     mbar_init(&bar, 1);
     mbar_fence_init();
@@ -254,18 +257,28 @@ __global__ void __launch_bounds__(kThreadsSpread, 2) k_spread_tile(const InstDes
   if (tid == 0) mbar_arrive_expect_tx(&bar, uint32_t(ur) * uint32_t(nv) * 4u);
   for (int u = tid; u < ur; u += kThreadsSpread)
     bulk_g2s(Gs + (size_t)u * CH, g + (size_t)__ldg(d.sp_um + u0 + u) * Nt + n0, uint32_t(nv) * 4u, &bar);
+  // the warp's list bounds and its first window of entries load while the
+  // rows are in flight
+  const int q = cb * QC + (tid >> 5);
+  const int *__restrict__ es = d.sp_slot;
+  const float4 *__restrict__ ew = d.sp_w;
+  int e0 = 0, e1 = 0, sj = 0;
+  float4 wj = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (q < My) {
+    e0 = __ldg(d.sp_start + (size_t)st * My + q);
+    e1 = __ldg(d.sp_start + (size_t)st * My + q + 1);
+    if (lane < e1 - e0) {
+      sj = __ldg(es + e0 + lane);
+      wj = __ldg(ew + e0 + lane);
+    }
+  }
   if (__syncthreads_or(!mbar_wait(&bar, 0))) {
     if (tid == 0) atomicOr(d.status, kStatusWaitTimeout);
     mbar_wait(&bar, 0);  // one more bounded wait for the copies in flight
     return;
   }
-  const int q = cb * QC + (tid >> 5);
   if (q >= My) return;  // whole warps leave; no block barrier follows
-  const int lane = tid & 31;
   const int p0 = st * P;
-  const int *__restrict__ es = d.sp_slot;
-  const float4 *__restrict__ ew = d.sp_w;
-  const int e0 = __ldg(d.sp_start + (size_t)st * My + q), e1 = __ldg(d.sp_start + (size_t)st * My + q + 1);
   float4 acc[P][K4];
 #pragma unroll
   for (int r = 0; r < P; ++r)
@@ -275,11 +288,13 @@ __global__ void __launch_bounds__(kThreadsSpread, 2) k_spread_tile(const InstDes
   // entry b reaches every lane by shuffles
   for (int e = e0; e < e1; e += 32) {
     const int cnt = min(32, e1 - e);
-    int sj = 0;
-    float4 wj = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (lane < cnt) {
-      sj = __ldg(es + e + lane);
-      wj = __ldg(ew + e + lane);
+    if (e > e0) {
+      sj = 0;
+      wj = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (lane < cnt) {
+        sj = __ldg(es + e + lane);
+        wj = __ldg(ew + e + lane);
+      }
     }
 #pragma unroll 4
     for (int b = 0; b < cnt; ++b) {
@@ -639,8 +654,10 @@ __global__ void __launch_bounds__(kThreadsCol) k_rowifft(const InstDesc *__restr
 // Persistent, double-buffered k_rowifft for My = 2^LGL and Nt % 4 == 0 (one
 // plan): the T rows of the next tile land in a staging buffer by bulk copies
 // while the current spectrum is built, transformed and written.
-// With use_map (nY1 <= 256), the staged rows arrive as one box of the 2-D
-// tensor map over T (floats; dims 2 Nt, Mx nY1; box 64 x nY1).
+// With use_map = hb > 0, the staged rows arrive as boxes of the 2-D tensor
+// map over T (floats; dims 2 Nt, Mx nY1; box 64 x hb): one box when
+// hb = nY1 (<= 256), else two (rows [0, hb) and [nY1 - hb, nY1), the row
+// they share written twice with the same values).
 template <int LGL>
 __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_rowifft_pipe(const InstDesc *__restrict__ descs, int nwork,
                                                               const __grid_constant__ CUtensorMap map, int use_map) {
@@ -662,8 +679,10 @@ __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_rowifft_pipe(const Inst
     const int p = w / nchunks, n0 = (w - p * nchunks) * 2 * NCP;
     if (use_map) {
       if (tid == 0) {
-        mbar_arrive_expect_tx(bar, uint32_t(nY1 * 2 * NCP * sizeof(float2)));
+        const int hb = use_map, nb = hb < nY1 ? 2 : 1;
+        mbar_arrive_expect_tx(bar, uint32_t(nb * hb * 2 * NCP * sizeof(float2)));
         tma_load_2d(stg, &map, 2 * n0, p * nY1, bar);
+        if (nb == 2) tma_load_2d(stg + (nY1 - hb) * 2 * NCP, &map, 2 * n0, p * nY1 + nY1 - hb, bar);
       }
       return;
     }
@@ -875,7 +894,7 @@ struct InterpPipe {
   // floats per buffer, rounded to 128 bytes
   static constexpr int BUF = ((CELLS * NC + SMAX * (PW + PD)) + 31) / 32 * 32;
   static constexpr int NS = NSTAGE;      // pipeline stages (buffers)
-  static constexpr int THREADS = 256;
+  static constexpr int THREADS = PA_INTERP_THREADS;
   static constexpr size_t smem = size_t(NS * BUF) * sizeof(float);
 };
 
@@ -1326,9 +1345,11 @@ cudaError_t launch_rowifft(const Launch &L) {
     const size_t stage = size_t((h.nY1 * 32 + 15) & ~15);
     const size_t smem = (size_t(h.My) * 16 + 2 * stage) * sizeof(float2);
     CUtensorMap map;
-    // one box per tile: the staging rows hold exactly nY1 rows
-    const int use_map = h.nY1 <= 256 && encode_2d(h.T, 2 * uint64_t(h.Nt), uint64_t(h.Mx) * h.nY1,
-                                                  uint64_t(h.Nt) * sizeof(float2), 64u, uint32_t(h.nY1), &map) ? 1 : 0;
+    // the staging rows hold exactly nY1 rows: one box of nY1 rows, or two
+    // boxes of ceil(nY1 / 2) rows (boxes are at most 256 high)
+    const int hb = h.nY1 <= 256 ? h.nY1 : (h.nY1 + 1) / 2;
+    const int use_map = hb <= 256 && encode_2d(h.T, 2 * uint64_t(h.Nt), uint64_t(h.Mx) * h.nY1,
+                                               uint64_t(h.Nt) * sizeof(float2), 64u, uint32_t(hb), &map) ? hb : 0;
     switch (lg) {
 #define PA_ROWIFFT_CASE(G) \
   case G: return launch_persistent_map(k_rowifft_pipe<G>, L, PipeThreads<G>::v, smem, nwork, map, use_map);
