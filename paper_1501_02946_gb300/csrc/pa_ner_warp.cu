@@ -164,6 +164,40 @@ __device__ __forceinline__ float2 interp_split(float2 *He, float2 *Ho, ff tau, c
   return cmul(acc, centring_phase(d, tau));
 }
 
+// The window sum over the W grid points p0 .. p0 + W - 1 with taps wt[t],
+// or (REV) with taps wt[W - 1 - t].
+template <int W, bool REV>
+__device__ __forceinline__ float2 window_sum(float2 *He, float2 *Ho, int p0, const float (&wt)[W]) {
+  float2 *ba, *bb;
+  tap_bases(He, Ho, p0, ba, bb);
+  float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int t = 0; t < W; ++t) {
+    const float2 h = (t & 1) ? bb[t >> 1] : ba[t >> 1];
+    const float w = REV ? wt[W - 1 - t] : wt[t];
+    acc = __ffma2_rn(make_float2(w, w), h, acc);
+  }
+  return acc;
+}
+
+// The points u = 2 tau and -u share their window taps: with u's footprint
+// starting at the (unwrapped) point pu and taps wt[t] = phi(fr + W/2 - 1 - t),
+// the footprint of -u starts at -pu - (W - 1) with taps wt[W - 1 - t] (the
+// window is even), and the centring phase of -tau is the conjugate of that
+// of tau.  pm_interp returns the interpolated values at tau and at -tau.
+template <int W>
+__device__ __forceinline__ void pm_interp(float2 *He, float2 *Ho, ff tau, const InstDesc &d, const HornerTable &ht,
+                                          float2 &vp, float2 &vn) {
+  int pu;
+  float fr;
+  footprint_unwrapped(tau, 2, W / 2, pu, fr);
+  float wt[W];
+  window_taps<W>(fr, ht, wt);
+  const float2 ph = centring_phase(d, tau);
+  vp = cmul(window_sum<W, false>(He, Ho, wrap(pu, d.Mt), wt), ph);
+  vn = cmul(window_sum<W, true>(He, Ho, wrap(-pu - (W - 1), d.Mt), wt), cconj(ph));
+}
+
 template <int W>
 __device__ __forceinline__ void spread_split(float2 *He, float2 *Ho, ff tau, float2 v, const InstDesc &d,
                                              const HornerTable &ht) {
@@ -239,22 +273,39 @@ __global__ void __launch_bounds__(128, LGT <= 9 ? PA_NER_FWD_MINB : 1) k_ner_war
     __syncwarp();
     const bool nyq = sl.kind >= 2;
     const ff tb = tau_base(d, ci.jx, ci.jy);
+    // depths l and -l (l = 1 .. hz - 1) share tau, the weight, the window
+    // taps and the centring phase; l = 0 and the unpaired l = -hz (Nz is even)
+    // are taken alone
+    auto put = [&](int z, float2 F) { Fs[z] = s == 0 ? F : cadd(Fs[z], F); };
 #pragma unroll 1
-    for (int il = lane; il < Nz; il += 32) {
-      const int l = il - hz;
+    for (int l = 1 + lane; l < hz; l += 32) {
+      const ff tau = tau_at(d, tb, l);
+      const float wgt = weight_of(d, tau, l) * d.scale * (nyq ? 0.5f : 1.f);
+      float2 vp, vn;
+      pm_interp<W>(He, Ho, tau, d, ht, vp, vn);
+      put(l, cscale(vp, wgt));
+      put(Nz - l, cscale(vn, wgt));
+    }
+    if (lane == 0) {
       float2 F = make_float2(0.f, 0.f);
-      if (!(l == 0 && (ci.jx != 0 || ci.jy != 0))) {
-        const ff tau = tau_at(d, tb, l);
-        const float wgt = weight_of(d, tau, l) * d.scale;
-        const bool lnyq = l == -hz;  // Nz is even
-        const bool two = !nyq && lnyq;
-        const ff tp = (nyq && sl.src == 1 && lnyq) ? ff_neg(tau) : tau;
-        float2 val = interp_split<W>(He, Ho, tp, d, ht);
-        if (two) val = cadd(val, interp_split<W>(He, Ho, ff_neg(tau), d, ht));
-        F = cscale(val, (nyq || two) ? 0.5f * wgt : wgt);
+      if (ci.jx == 0 && ci.jy == 0) {
+        const ff tau = tau_at(d, tb, 0);
+        F = cscale(interp_split<W>(He, Ho, tau, d, ht), weight_of(d, tau, 0) * d.scale * (nyq ? 0.5f : 1.f));
       }
-      const int z = l < 0 ? l + Nz : l;
-      Fs[z] = s == 0 ? F : cadd(Fs[z], F);
+      put(0, F);
+    } else if (lane == 1) {
+      const int l = -hz;
+      const ff tau = tau_at(d, tb, l);
+      const float wgt = weight_of(d, tau, l) * d.scale;
+      float2 val;
+      if (nyq) {
+        val = interp_split<W>(He, Ho, sl.src == 1 ? ff_neg(tau) : tau, d, ht);
+      } else {
+        float2 vp, vn;
+        pm_interp<W>(He, Ho, tau, d, ht, vp, vn);
+        val = cadd(vp, vn);
+      }
+      put(hz, cscale(val, 0.5f * wgt));
     }
     __syncwarp();
   }
@@ -273,8 +324,6 @@ __global__ void __launch_bounds__(128, PA_NER_ADJ_MINB) k_ner_warp_adj(const Ins
   extern __shared__ float4 smem_f4[];
   constexpr int Nt = 1 << LGT, Nz = 1 << LGZ;
   constexpr int HH = NerWarpShape<LGT, W>::HH, FS = NerWarpFs<LGZ>::FS;
-  // each lane spreads C consecutive depth samples, in increasing l
-  constexpr int C = Nz / 32;
   const InstDesc &d = descs[0];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int v = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -299,39 +348,35 @@ __global__ void __launch_bounds__(128, PA_NER_ADJ_MINB) k_ner_warp_adj(const Ins
     __syncwarp();
     const bool nyq = ci.xnyq || ci.ynyq;
     const ff tb = tau_base(d, ci.jx, ci.jy);
-    // The points u(l) = 2 tau(j, l) increase with l, so the taps of a lane's
-    // consecutive samples overlap: they accumulate in a register window
-    // acc[t] of the grid points base + t, which slides forward (adding the
-    // point it leaves into shared memory) as the first tap advances.  Only
-    // the points a window leaves, and its last W, reach shared memory.
-    float2 acc[W];
+    const float half = nyq ? 0.5f : 1.f;
+    // Depths l and -l (l = 1 .. hz - 1) share tau, the weight, the window
+    // taps and the centring phase (see pm_interp).  The points u(l) = 2 tau(j, l)
+    // increase with l, so the taps of a lane's consecutive l overlap: they
+    // accumulate in register windows acc[t] (grid points base + t, for +tau)
+    // and accn[t] (points -(base + t), for -tau), which slide forward
+    // together (adding the points they leave into shared memory) as the first
+    // tap advances.  Only the points a window leaves, and its last W, reach
+    // shared memory.  l = 0 and the unpaired l = -hz are spread on their own.
+    constexpr int C2 = Nz / 64;  // pairs per lane: l = 1 + lane C2 .. (l < hz)
+    float2 acc[W], accn[W];
 #pragma unroll
-    for (int t = 0; t < W; ++t) acc[t] = make_float2(0.f, 0.f);
+    for (int t = 0; t < W; ++t) acc[t] = accn[t] = make_float2(0.f, 0.f);
     int base = 0;
     bool open = false;
 #pragma unroll 1
-    for (int j = 0; j < C; ++j) {
-      const int l = lane * C + j - hz;
-      if (l == 0 && (ci.jx != 0 || ci.jy != 0)) continue;
+    for (int j = 0; j < C2; ++j) {
+      const int l = 1 + lane * C2 + j;
+      if (l >= hz) break;
       const ff tau = tau_at(d, tb, l);
-      const float wgt = weight_of(d, tau, l) * d.scale;
-      const float2 val = cscale(Fs[l < 0 ? l + Nz : l], wgt);
-      if (l == -hz) {  // the depth Nyquist sample also reaches -tau: outside the window's order
-        const float2 hv = cscale(val, 0.5f);
-        if (!nyq) {
-          spread_split<W>(He, Ho, tau, hv, d, ht);
-          spread_split<W>(He, Ho, ff_neg(tau), hv, d, ht);
-        } else {
-          spread_split<W>(He, Ho, sl.src == 1 ? ff_neg(tau) : tau, hv, d, ht);
-        }
-        continue;
-      }
+      const float wgt = weight_of(d, tau, l) * d.scale * half;
       int pu;
       float fr;
       footprint_unwrapped(tau, 2, W / 2, pu, fr);
       float wt[W];
       window_taps<W>(fr, ht, wt);
-      const float2 vv = cmul(nyq ? cscale(val, 0.5f) : val, cconj(centring_phase(d, tau)));
+      const float2 ph = centring_phase(d, tau);
+      const float2 vp = cmul(cscale(Fs[l], wgt), cconj(ph));
+      const float2 vn = cmul(cscale(Fs[Nz - l], wgt), ph);
       if (!open) {
         base = pu;
         open = true;
@@ -341,27 +386,49 @@ __global__ void __launch_bounds__(128, PA_NER_ADJ_MINB) k_ner_warp_adj(const Ins
 #pragma unroll
         for (int t = 0; t < W; ++t) {
           flush_point(He, Ho, base + t, 2 * Nt, acc[t]);
-          acc[t] = make_float2(0.f, 0.f);
+          flush_point(He, Ho, -(base + t), 2 * Nt, accn[t]);
+          acc[t] = accn[t] = make_float2(0.f, 0.f);
         }
         base = pu;
       } else {
         for (; adv > 0; --adv) {
           flush_point(He, Ho, base, 2 * Nt, acc[0]);
+          flush_point(He, Ho, -base, 2 * Nt, accn[0]);
 #pragma unroll
-          for (int t = 0; t + 1 < W; ++t) acc[t] = acc[t + 1];
-          acc[W - 1] = make_float2(0.f, 0.f);
+          for (int t = 0; t + 1 < W; ++t) {
+            acc[t] = acc[t + 1];
+            accn[t] = accn[t + 1];
+          }
+          acc[W - 1] = accn[W - 1] = make_float2(0.f, 0.f);
           ++base;
         }
       }
 #pragma unroll
       for (int t = 0; t < W; ++t) {
-        acc[t].x = fmaf(wt[t], vv.x, acc[t].x);
-        acc[t].y = fmaf(wt[t], vv.y, acc[t].y);
+        acc[t] = __ffma2_rn(make_float2(wt[t], wt[t]), vp, acc[t]);
+        accn[t] = __ffma2_rn(make_float2(wt[t], wt[t]), vn, accn[t]);
       }
     }
     if (open) {
 #pragma unroll
-      for (int t = 0; t < W; ++t) flush_point(He, Ho, base + t, 2 * Nt, acc[t]);
+      for (int t = 0; t < W; ++t) {
+        flush_point(He, Ho, base + t, 2 * Nt, acc[t]);
+        flush_point(He, Ho, -(base + t), 2 * Nt, accn[t]);
+      }
+    }
+    if (lane == 0 && ci.jx == 0 && ci.jy == 0) {  // l = 0 (W(j != 0, 0) = 0)
+      const ff tau = tau_at(d, tb, 0);
+      spread_split<W>(He, Ho, tau, cscale(Fs[0], weight_of(d, tau, 0) * d.scale * half), d, ht);
+    } else if (lane == 1) {  // the depth Nyquist l = -hz also reaches -tau
+      const int l = -hz;
+      const ff tau = tau_at(d, tb, l);
+      const float2 hv = cscale(Fs[hz], 0.5f * weight_of(d, tau, l) * d.scale);
+      if (!nyq) {
+        spread_split<W>(He, Ho, tau, hv, d, ht);
+        spread_split<W>(He, Ho, ff_neg(tau), hv, d, ht);
+      } else {
+        spread_split<W>(He, Ho, sl.src == 1 ? ff_neg(tau) : tau, hv, d, ht);
+      }
     }
     __syncwarp();
     if (lane < W / 2) {
