@@ -26,18 +26,20 @@ struct FftPlan {
 
 // Horner coefficients of the window taps used by the NER interpolation:
 // tap t (0..w-1) at fraction fr in [0,1) of the oversampled time-frequency
-// grid is phi(fr + w/2 - 1 - t) = sum_d c[t][d] s^d with s = 2 fr - 1, where
-// phi is the Kaiser-Bessel window normalised to phi(0) = 1.
+// grid is phi(fr + w/2 - 1 - t) = P_t(s) = sum_d c[t][d] s^d with
+// s = 2 fr - 1, where phi is the Kaiser-Bessel window normalised to
+// phi(0) = 1.  The window is even, so P_{w-1-t}(s) = P_t(-s): with
+// P_t(s) = E_t(s^2) + s O_t(s^2) (the even and odd powers), taps t and
+// w - 1 - t are E_t(u) +- s O_t(u), u = s^2.  The table holds the first w/2
+// taps' coefficient pairs (c[t][2k], c[t][2k + 1]), so that E and O
+// evaluate together as packed two-wide Horner steps in u.
 struct HornerTable {
-  // coefficient d of taps 2i (x) and 2i + 1 (y) side by side, so that a pair
-  // of taps evaluates as packed two-wide FMAs
-  float2 c2[kMaxWidth / 2][kMaxDeg + 1];
-  __host__ __device__ float coef(int t, int d) const { return (t & 1) ? c2[t >> 1][d].y : c2[t >> 1][d].x; }
+  float2 eo[kMaxWidth / 2][kMaxDeg / 2 + 1];
   __host__ void set(int t, int d, float v) {
-    if (t & 1) {
-      c2[t >> 1][d].y = v;
+    if (d & 1) {
+      eo[t][d >> 1].y = v;
     } else {
-      c2[t >> 1][d].x = v;
+      eo[t][d >> 1].x = v;
     }
   }
 };

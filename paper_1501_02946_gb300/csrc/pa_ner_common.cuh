@@ -69,16 +69,17 @@ __device__ __forceinline__ void footprint(ff tau, int scale, int L, int half, in
 
 template <int W>
 __device__ __forceinline__ void window_taps(float fr, const HornerTable &ht, float *wt) {
-  constexpr int D = HornerDeg<W>::v;
-  const float s = 2.f * fr - 1.f;
-  const float2 ss = make_float2(s, s);
+  constexpr int D = HornerDeg<W>::v, KE = D / 2 + 1;
+  const float s = 2.f * fr - 1.f, u = s * s;
+  const float2 uu = make_float2(u, u), sm = make_float2(s, -s);
 #pragma unroll
-  for (int i = 0; i < W / 2; ++i) {  // taps 2i and 2i + 1 as packed two-wide Horner steps
-    float2 a = ht.c2[i][D];
+  for (int i = 0; i < W / 2; ++i) {  // taps i and W - 1 - i: E(u) +- s O(u)
+    float2 a = ht.eo[i][KE - 1];
 #pragma unroll
-    for (int k = D - 1; k >= 0; --k) a = __ffma2_rn(a, ss, ht.c2[i][k]);
-    wt[2 * i] = a.x;
-    wt[2 * i + 1] = a.y;
+    for (int k = KE - 2; k >= 0; --k) a = __ffma2_rn(a, uu, ht.eo[i][k]);
+    const float2 t = __ffma2_rn(sm, make_float2(a.y, a.y), make_float2(a.x, a.x));
+    wt[i] = t.x;
+    wt[W - 1 - i] = t.y;
   }
 }
 

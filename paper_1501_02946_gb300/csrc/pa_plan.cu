@@ -147,12 +147,13 @@ void split_ff(double v, float &hi, float &lo) {
 int horner_degree(int w) { return w <= 6 ? 7 : (w <= 8 ? 8 : (w <= 12 ? 10 : 14)); }
 
 // Monomial coefficients in s = 2 fr - 1 of the Chebyshev interpolant of
-// degree D of phi(fr + w/2 - 1 - t), fr in [0, 1].
+// degree D of phi(fr + w/2 - 1 - t), fr in [0, 1], for the taps t < w/2
+// (the others follow from the window's symmetry, see HornerTable).
 void fit_horner(const Kb &kb, int D, HornerTable &ht) {
   std::memset(&ht, 0, sizeof(ht));
   const int w = kb.w;
   std::vector<double> nodes(D + 1), vals(D + 1);
-  for (int t = 0; t < w; ++t) {
+  for (int t = 0; t < w / 2; ++t) {
     for (int k = 0; k <= D; ++k) {
       nodes[k] = std::cos(kPi * (k + 0.5) / (D + 1));
       const double fr = 0.5 * (nodes[k] + 1.0);
