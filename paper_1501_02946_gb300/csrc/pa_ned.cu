@@ -31,6 +31,10 @@
 #ifndef PA_SPREAD_MINB
 #define PA_SPREAD_MINB 2
 #endif
+// 1: the inverse row FFT's tiles leave shared memory by TMA stores
+#ifndef PA_ROWIFFT_TMA_STORE
+#define PA_ROWIFFT_TMA_STORE 1
+#endif
 // 1: single-plan spreads stage their g rows in shared memory (k_spread_tile)
 #ifndef PA_SPREAD_TILE
 #define PA_SPREAD_TILE 1
@@ -658,9 +662,14 @@ __global__ void __launch_bounds__(kThreadsCol) k_rowifft(const InstDesc *__restr
 // map over T (floats; dims 2 Nt, Mx nY1; box 64 x hb): one box when
 // hb = nY1 (<= 256), else two (rows [0, hb) and [nY1 - hb, nY1), the row
 // they share written twice with the same values).
+// With use_omap, the transformed tile leaves shared memory as boxes of the
+// 2-D tensor map omap over G0 (floats; dims Nt, Mx My; box 32 x min(My, 256))
+// stored by the TMA engine; the next tile's spectrum is built in the same
+// buffer only after the stores have read it.
 template <int LGL>
 __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_rowifft_pipe(const InstDesc *__restrict__ descs, int nwork,
-                                                              const __grid_constant__ CUtensorMap map, int use_map) {
+                                                              const __grid_constant__ CUtensorMap map, int use_map,
+                                                              const __grid_constant__ CUtensorMap omap, int use_omap) {
   griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
   __shared__ __align__(8) uint64_t bars[2];
@@ -693,6 +702,10 @@ __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_rowifft_pipe(const Inst
   };
   auto compute = [&](int w, float2 *stg) {
     const int p = w / nchunks, n0 = (w - p * nchunks) * 2 * NCP;
+    if (use_omap) {  // the previous tile's stores have read S
+      if (tid == 0) bulk_wait_read<0>();
+      __syncthreads();
+    }
     // bins jy and My - jy from the staged rows (one item reads a sample pair
     // and fills both); the bins nY1 .. My - nY1, which no jy reaches, are zero
     for (int idx = tid; idx < nY1 * NCP; idx += nthr) {
@@ -713,6 +726,16 @@ __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_rowifft_pipe(const Inst
       reinterpret_cast<float4 *>(S + nY1 * NCP)[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     fft_fixed<LGL, +1>(S, NCP, LGNCP, lgT, tw, tid);
+    if (use_omap) {
+      fence_proxy_async_smem();  // the transform's writes precede the stores' reads
+      __syncthreads();
+      if (tid == 0) {
+        constexpr int OB = L < 256 ? L : 256;
+        for (int b = 0; b < L; b += OB) tma_store_2d(&omap, n0, p * L + b, S + b * NCP);
+        bulk_commit();
+      }
+      return;
+    }
     float *G0 = d.G0 + (size_t)p * L * Nt + n0;
     const int nv4 = (min(2 * NCP, Nt - n0)) >> 2;
     if (nv4 == NCP / 2) {  // full chunk: index splits by shifts
@@ -728,6 +751,7 @@ __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_rowifft_pipe(const Inst
     }
   };
   tile_pipeline(nwork, st0, st1, bars, d.status, issue, compute);
+  if (use_omap && tid == 0) bulk_wait<0>();  // every store complete before the block exits
 }
 
 // ---------------------------------------------------- adjoint interpolation
@@ -1350,9 +1374,20 @@ cudaError_t launch_rowifft(const Launch &L) {
     const int hb = h.nY1 <= 256 ? h.nY1 : (h.nY1 + 1) / 2;
     const int use_map = hb <= 256 && encode_2d(h.T, 2 * uint64_t(h.Nt), uint64_t(h.Mx) * h.nY1,
                                                uint64_t(h.Nt) * sizeof(float2), 64u, uint32_t(hb), &map) ? hb : 0;
+    CUtensorMap omap;
+    const int use_omap = PA_ROWIFFT_TMA_STORE &&
+                         encode_2d(h.G0, uint64_t(h.Nt), uint64_t(h.Mx) * h.My, uint64_t(h.Nt) * sizeof(float), 32u,
+                                   uint32_t(h.My < 256 ? h.My : 256), &omap) ? 1 : 0;
     switch (lg) {
-#define PA_ROWIFFT_CASE(G) \
-  case G: return launch_persistent_map(k_rowifft_pipe<G>, L, PipeThreads<G>::v, smem, nwork, map, use_map);
+#define PA_ROWIFFT_CASE(G)                                                                               \
+  case G: {                                                                                              \
+    auto kern = k_rowifft_pipe<G>;                                                                       \
+    const cudaError_t e = set_smem(kern, smem);                                                          \
+    if (e != cudaSuccess) return e;                                                                      \
+    const int grid = persistent_grid(kern, PipeThreads<G>::v, smem, nwork);                              \
+    return launch_pdl(kern, grid, PipeThreads<G>::v, smem, L.stream, L.descs, nwork, map, use_map, omap, \
+                      use_omap);                                                                         \
+  }
       PA_ROWIFFT_CASE(5) PA_ROWIFFT_CASE(6) PA_ROWIFFT_CASE(7) PA_ROWIFFT_CASE(8) PA_ROWIFFT_CASE(9)
 #undef PA_ROWIFFT_CASE
       default: break;
