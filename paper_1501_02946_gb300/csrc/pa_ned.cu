@@ -31,6 +31,10 @@
 #ifndef PA_SPREAD_MINB
 #define PA_SPREAD_MINB 2
 #endif
+// 1: the adjoint column FFT's tiles leave shared memory by TMA stores
+#ifndef PA_COLFFT_TMA_STORE
+#define PA_COLFFT_TMA_STORE 1
+#endif
 // 1: the inverse row FFT's tiles leave shared memory by TMA stores
 #ifndef PA_ROWIFFT_TMA_STORE
 #define PA_ROWIFFT_TMA_STORE 1
@@ -474,9 +478,13 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft(const InstDesc *__restri
 // 2 Nt, nY1, nX1; box 32 x 1 x (hx + 1)) for the adjoint, whose two boxes
 // start at rows hx and -1 (the row before 0 reads as zeros and lands on a
 // bin that is cleared anyway).
+// With use_omap (adjoint), the transformed tile leaves shared memory as boxes
+// of the 3-D tensor map omap over T (the forward's input map) stored by the
+// TMA engine; the buffer is refilled only after the stores have read it.
 template <bool ADJ, int LGL>
 __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_colfft_pipe(const InstDesc *__restrict__ descs, int nwork,
-                                                             const __grid_constant__ CUtensorMap map, int use_map) {
+                                                             const __grid_constant__ CUtensorMap map, int use_map,
+                                                             const __grid_constant__ CUtensorMap omap, int use_omap) {
   griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
   __shared__ __align__(8) uint64_t bars[2];
@@ -498,6 +506,7 @@ __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_colfft_pipe(const InstD
           mbar_arrive_expect_tx(bar, uint32_t(L * NC * sizeof(float2)));
           for (int b = 0; b < L; b += BOX) tma_load_3d(buf + b * NC, &map, 2 * n0, jy, b, bar);
         } else {
+          if (use_omap) bulk_wait_read<0>();  // this buffer's last tile has been stored
           mbar_arrive_expect_tx(bar, uint32_t(2 * (hx + 1) * NC * sizeof(float2)));
           tma_load_3d(buf, &map, 2 * n0, jy, hx, bar);                       // ix = hx .. 2 hx
           tma_load_3d(buf + (L - hx - 1) * NC, &map, 2 * n0, jy, -1, bar);  // ix = -1 .. hx - 1
@@ -534,6 +543,15 @@ __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_colfft_pipe(const InstD
       }
       __syncthreads();
       fft_fixed<LGL, +1>(buf, NC, LGNC, lgT, tw, tid);
+      if (use_omap) {
+        fence_proxy_async_smem();  // the transform's writes precede the stores' reads
+        __syncthreads();
+        if (tid == 0) {
+          for (int b = 0; b < L; b += BOX) tma_store_3d(&omap, 2 * n0, jy, b, buf + b * NC);
+          bulk_commit();
+        }
+        return;
+      }
       for (int idx = tid; idx < L * NC; idx += nthr) {
         const int kk = idx & (NC - 1), p = idx >> LGNC;
         const int n = n0 + kk;
@@ -542,6 +560,7 @@ __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_colfft_pipe(const InstD
     }
   };
   tile_pipeline(nwork, buf0, buf1, bars, d.status, issue, compute);
+  if (use_omap && tid == 0) bulk_wait<0>();  // every store complete before the block exits
 }
 
 // Persistent, double-buffered row FFT (k_rowfft) for My = 2^LGL and
@@ -1269,6 +1288,15 @@ cudaError_t launch_rowfft(const Launch &L) {
   return cudaGetLastError();
 }
 
+template <typename K>
+static cudaError_t launch_colfft_pipe(K kernel, const Launch &L, int threads, size_t smem, int nwork,
+                                      const CUtensorMap &map, int use_map, const CUtensorMap &omap, int use_omap) {
+  const cudaError_t e = set_smem(kernel, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = persistent_grid(kernel, threads, smem, nwork);
+  return launch_pdl(kernel, grid, threads, smem, L.stream, L.descs, nwork, map, use_map, omap, use_omap);
+}
+
 cudaError_t launch_colfft(const Launch &L, bool adjoint) {
   if (L.host && !L.work && (L.host->Nt % 2) == 0) {
     const InstDesc &h = *L.host;
@@ -1286,11 +1314,20 @@ cudaError_t launch_colfft(const Launch &L, bool adjoint) {
     } else {
       std::memset(&map, 0, sizeof(map));
     }
+    // the adjoint's output T through the forward's input map (stores need the load map's issuing thread)
+    CUtensorMap omap;
+    const int use_omap = adjoint && use_map && PA_COLFFT_TMA_STORE &&
+                         encode_3d(h.T, 2 * uint64_t(h.Nt), uint64_t(h.nY1), uint64_t(h.Mx),
+                                   uint64_t(h.Nt) * sizeof(float2), uint64_t(h.nY1) * h.Nt * sizeof(float2), 32u, 1u,
+                                   uint32_t(h.Mx < 256 ? h.Mx : 256), &omap) ? 1 : 0;
+    if (!use_omap) std::memset(&omap, 0, sizeof(omap));
     switch (lg) {
-#define PA_COLFFT_CASE(G)                                                                                      \
-  case G:                                                                                                      \
-    return adjoint ? launch_persistent_map(k_colfft_pipe<true, G>, L, PipeThreads<G>::v, smem, nwork, map, use_map) \
-                   : launch_persistent_map(k_colfft_pipe<false, G>, L, PipeThreads<G>::v, smem, nwork, map, use_map);
+#define PA_COLFFT_CASE(G)                                                                                        \
+  case G:                                                                                                        \
+    return adjoint ? launch_colfft_pipe(k_colfft_pipe<true, G>, L, PipeThreads<G>::v, smem, nwork, map, use_map, \
+                                        omap, use_omap)                                                          \
+                   : launch_colfft_pipe(k_colfft_pipe<false, G>, L, PipeThreads<G>::v, smem, nwork, map, use_map, \
+                                        omap, 0);
       PA_COLFFT_CASE(5) PA_COLFFT_CASE(6) PA_COLFFT_CASE(7) PA_COLFFT_CASE(8) PA_COLFFT_CASE(9)
 #undef PA_COLFFT_CASE
       default: break;
