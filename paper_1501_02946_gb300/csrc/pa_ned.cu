@@ -31,7 +31,11 @@
 #ifndef PA_SPREAD_MINB
 #define PA_SPREAD_MINB 2
 #endif
-// 1: the adjoint column FFT's tiles leave shared memory by TMA stores
+// 1: the row FFT's unpacked rows leave shared memory by TMA stores (My >= 512)
+#ifndef PA_ROWFFT_TMA_STORE
+#define PA_ROWFFT_TMA_STORE 1
+#endif
+// 1: the column FFT's tiles leave shared memory by TMA stores
 #ifndef PA_COLFFT_TMA_STORE
 #define PA_COLFFT_TMA_STORE 1
 #endif
@@ -481,10 +485,15 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft(const InstDesc *__restri
 // With use_omap (adjoint), the transformed tile leaves shared memory as boxes
 // of the 3-D tensor map omap over T (the forward's input map) stored by the
 // TMA engine; the buffer is refilled only after the stores have read it.
+// In the forward, with use_omap the scaled bins leave as two boxes of the
+// 3-D maps over G1 (box heights hx + 1 for rows hx .. 2 hx, from bins
+// 0 .. hx, in omap; hx for rows 0 .. hx - 1, from bins L - hx .. L - 1, in
+// omap2).
 template <bool ADJ, int LGL>
 __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_colfft_pipe(const InstDesc *__restrict__ descs, int nwork,
                                                              const __grid_constant__ CUtensorMap map, int use_map,
-                                                             const __grid_constant__ CUtensorMap omap, int use_omap) {
+                                                             const __grid_constant__ CUtensorMap omap, int use_omap,
+                                                             const __grid_constant__ CUtensorMap omap2) {
   griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
   __shared__ __align__(8) uint64_t bars[2];
@@ -503,6 +512,7 @@ __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_colfft_pipe(const InstD
     if (use_map) {
       if (tid == 0) {
         if (!ADJ) {
+          if (use_omap) bulk_wait_read<0>();  // this buffer's last tile has been stored
           mbar_arrive_expect_tx(bar, uint32_t(L * NC * sizeof(float2)));
           for (int b = 0; b < L; b += BOX) tma_load_3d(buf + b * NC, &map, 2 * n0, jy, b, bar);
         } else {
@@ -528,6 +538,22 @@ __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_colfft_pipe(const InstD
     const int jy = w / nchunks, n0 = (w - jy * nchunks) * NC;
     if (!ADJ) {
       fft_fixed<LGL, -1>(buf, NC, LGNC, lgT, tw, tid);
+      if (use_omap) {
+        // scale the kept bins in place (bin (ix - hx) mod L holds row ix)
+        for (int idx = tid; idx < nX1 * NC; idx += nthr) {
+          const int kk = idx & (NC - 1), ix = idx >> LGNC;
+          float2 *q = buf + ((ix - hx) & (L - 1)) * NC + kk;
+          *q = cscale(*q, __ldg(d.invphx + ix));
+        }
+        fence_proxy_async_smem();  // the writes precede the stores' reads
+        __syncthreads();
+        if (tid == 0) {
+          tma_store_3d(&omap, 2 * n0, jy, hx, buf);
+          if (hx > 0) tma_store_3d(&omap2, 2 * n0, jy, 0, buf + (L - hx) * NC);
+          bulk_commit();
+        }
+        return;
+      }
       for (int idx = tid; idx < nX1 * NC; idx += nthr) {
         const int kk = idx & (NC - 1), ix = idx >> LGNC;
         const int n = n0 + kk;
@@ -567,9 +593,14 @@ __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_colfft_pipe(const InstD
 // Nt % 4 == 0 (one plan).
 // With use_map, a tile arrives as boxes of the 2-D tensor map over G0
 // (dims Nt, Mx My; box 32 x min(My, 256)) instead of one copy per row q.
+// With use_omap = hb > 0 (and use_map), the unpacked rows are staged in a
+// third buffer [nY1][32 complex] and leave as boxes of the 2-D map omap over
+// T (floats; dims 2 Nt, Mx nY1; box 64 x hb): one box when hb = nY1, else
+// two (rows [0, hb) and [nY1 - hb, nY1)).
 template <int LGL>
 __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_rowfft_pipe(const InstDesc *__restrict__ descs, int nwork,
-                                                             const __grid_constant__ CUtensorMap map, int use_map) {
+                                                             const __grid_constant__ CUtensorMap map, int use_map,
+                                                             const __grid_constant__ CUtensorMap omap, int use_omap) {
   griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
   __shared__ __align__(8) uint64_t bars[2];
@@ -596,9 +627,30 @@ __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_rowfft_pipe(const InstD
     const float *G0 = d.G0 + (size_t)p * L * Nt + n0;
     for (int q = tid; q < L; q += nthr) bulk_g2s(buf + q * NCP, G0 + (size_t)q * Nt, rb, bar);
   };
+  float4 *O = reinterpret_cast<float4 *>(buf1 + L * NCP);  // [nY1][NCP] staged (a, b) pairs
   auto compute = [&](int w, float2 *buf) {
     const int p = w / nchunks, n0 = (w - p * nchunks) * 2 * NCP;
     fft_fixed<LGL, -1>(buf, NCP, LGNCP, lgT, tw, tid);
+    if (use_omap) {
+      if (tid == 0) bulk_wait_read<0>();  // the previous tile's stores have read O
+      __syncthreads();
+      for (int idx = tid; idx < nY1 * NCP; idx += nthr) {
+        const int k = idx & (NCP - 1), jy = idx >> LGNCP;
+        const float2 Z = buf[jy * NCP + k];
+        const float2 Zm = buf[((L - jy) & (L - 1)) * NCP + k];
+        const float sc = 0.5f * __ldg(d.invphy + jy);
+        O[idx] = make_float4(sc * (Z.x + Zm.x), sc * (Z.y - Zm.y), sc * (Z.y + Zm.y), -sc * (Z.x - Zm.x));
+      }
+      fence_proxy_async_smem();  // the writes precede the stores' reads
+      __syncthreads();
+      if (tid == 0) {
+        const int hb = use_omap;
+        tma_store_2d(&omap, 2 * n0, p * nY1, O);
+        if (hb < nY1) tma_store_2d(&omap, 2 * n0, p * nY1 + nY1 - hb, O + (nY1 - hb) * NCP);
+        bulk_commit();
+      }
+      return;
+    }
     float2 *Trow = d.T + (size_t)p * nY1 * Nt;
     for (int idx = tid; idx < nY1 * NCP; idx += nthr) {
       const int k = idx & (NCP - 1), jy = idx >> LGNCP;
@@ -613,6 +665,7 @@ __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_rowfft_pipe(const InstD
     }
   };
   tile_pipeline(nwork, buf0, buf1, bars, d.status, issue, compute);
+  if (use_omap && tid == 0) bulk_wait<0>();  // every store complete before the block exits
 }
 
 // ------------------------------------------------------- adjoint row FFT
@@ -1269,13 +1322,30 @@ cudaError_t launch_rowfft(const Launch &L) {
     const InstDesc &h = *L.host;
     const int lg = pow2_log(h.My);
     const int nwork = h.Mx * ((h.Nt + 31) / 32);
-    const size_t smem = 2 * size_t(h.My) * 16 * sizeof(float2);
-    CUtensorMap map;
+    size_t smem = 2 * size_t(h.My) * 16 * sizeof(float2);
+    CUtensorMap map, omap;
     const int use_map = encode_2d(h.G0, uint64_t(h.Nt), uint64_t(h.Mx) * h.My, uint64_t(h.Nt) * sizeof(float), 32u,
                                   uint32_t(h.My < 256 ? h.My : 256), &map) ? 1 : 0;
+    // TMA stores of the output (a third buffer of nY1 rows) where a block
+    // per SM is all the two input buffers allow anyway (My >= 512)
+    const int hb = h.nY1 <= 256 ? h.nY1 : (h.nY1 + 1) / 2;
+    const size_t osmem = size_t(h.nY1) * 16 * sizeof(float4);
+    int use_omap = 0;
+    if (use_map && PA_ROWFFT_TMA_STORE && h.My >= 512 && hb <= 256 && smem + osmem <= smem_optin_limit())
+      use_omap = encode_2d(h.T, 2 * uint64_t(h.Nt), uint64_t(h.Mx) * h.nY1, uint64_t(h.Nt) * sizeof(float2), 64u,
+                           uint32_t(hb), &omap) ? hb : 0;
+    if (use_omap) smem += osmem;
+    else std::memset(&omap, 0, sizeof(omap));
     switch (lg) {
-#define PA_ROWFFT_CASE(G) \
-  case G: return launch_persistent_map(k_rowfft_pipe<G>, L, PipeThreads<G>::v, smem, nwork, map, use_map);
+#define PA_ROWFFT_CASE(G)                                                                                 \
+  case G: {                                                                                               \
+    auto kern = k_rowfft_pipe<G>;                                                                         \
+    const cudaError_t e = set_smem(kern, smem);                                                           \
+    if (e != cudaSuccess) return e;                                                                       \
+    const int grid = persistent_grid(kern, PipeThreads<G>::v, smem, nwork);                               \
+    return launch_pdl(kern, grid, PipeThreads<G>::v, smem, L.stream, L.descs, nwork, map, use_map, omap,  \
+                      use_omap);                                                                          \
+  }
       PA_ROWFFT_CASE(5) PA_ROWFFT_CASE(6) PA_ROWFFT_CASE(7) PA_ROWFFT_CASE(8) PA_ROWFFT_CASE(9)
 #undef PA_ROWFFT_CASE
       default: break;
@@ -1290,11 +1360,12 @@ cudaError_t launch_rowfft(const Launch &L) {
 
 template <typename K>
 static cudaError_t launch_colfft_pipe(K kernel, const Launch &L, int threads, size_t smem, int nwork,
-                                      const CUtensorMap &map, int use_map, const CUtensorMap &omap, int use_omap) {
+                                      const CUtensorMap &map, int use_map, const CUtensorMap &omap, int use_omap,
+                                      const CUtensorMap &omap2) {
   const cudaError_t e = set_smem(kernel, smem);
   if (e != cudaSuccess) return e;
   const int grid = persistent_grid(kernel, threads, smem, nwork);
-  return launch_pdl(kernel, grid, threads, smem, L.stream, L.descs, nwork, map, use_map, omap, use_omap);
+  return launch_pdl(kernel, grid, threads, smem, L.stream, L.descs, nwork, map, use_map, omap, use_omap, omap2);
 }
 
 cudaError_t launch_colfft(const Launch &L, bool adjoint) {
@@ -1314,20 +1385,34 @@ cudaError_t launch_colfft(const Launch &L, bool adjoint) {
     } else {
       std::memset(&map, 0, sizeof(map));
     }
-    // the adjoint's output T through the forward's input map (stores need the load map's issuing thread)
-    CUtensorMap omap;
-    const int use_omap = adjoint && use_map && PA_COLFFT_TMA_STORE &&
-                         encode_3d(h.T, 2 * uint64_t(h.Nt), uint64_t(h.nY1), uint64_t(h.Mx),
-                                   uint64_t(h.Nt) * sizeof(float2), uint64_t(h.nY1) * h.Nt * sizeof(float2), 32u, 1u,
-                                   uint32_t(h.Mx < 256 ? h.Mx : 256), &omap) ? 1 : 0;
+    // outputs by TMA stores (issued by the thread that issues the loads, so
+    // only with the load map): the adjoint's T through the forward's input
+    // map, the forward's G1 through two maps of box heights hx + 1 and hx
+    CUtensorMap omap, omap2;
+    std::memset(&omap2, 0, sizeof(omap2));
+    int use_omap = 0;
+    if (use_map && PA_COLFFT_TMA_STORE) {
+      if (adjoint) {
+        use_omap = encode_3d(h.T, 2 * uint64_t(h.Nt), uint64_t(h.nY1), uint64_t(h.Mx), uint64_t(h.Nt) * sizeof(float2),
+                             uint64_t(h.nY1) * h.Nt * sizeof(float2), 32u, 1u, uint32_t(h.Mx < 256 ? h.Mx : 256),
+                             &omap) ? 1 : 0;
+      } else if (h.hx >= 1 && h.hx + 1 <= 256 && 2 * h.hx + 1 <= h.Mx) {
+        use_omap = encode_3d(h.G1, 2 * uint64_t(h.Nt), uint64_t(h.nY1), uint64_t(h.nX1),
+                             uint64_t(h.Nt) * sizeof(float2), uint64_t(h.nY1) * h.Nt * sizeof(float2), 32u, 1u,
+                             uint32_t(h.hx + 1), &omap) &&
+                   encode_3d(h.G1, 2 * uint64_t(h.Nt), uint64_t(h.nY1), uint64_t(h.nX1),
+                             uint64_t(h.Nt) * sizeof(float2), uint64_t(h.nY1) * h.Nt * sizeof(float2), 32u, 1u,
+                             uint32_t(h.hx), &omap2) ? 1 : 0;
+      }
+    }
     if (!use_omap) std::memset(&omap, 0, sizeof(omap));
     switch (lg) {
 #define PA_COLFFT_CASE(G)                                                                                        \
   case G:                                                                                                        \
     return adjoint ? launch_colfft_pipe(k_colfft_pipe<true, G>, L, PipeThreads<G>::v, smem, nwork, map, use_map, \
-                                        omap, use_omap)                                                          \
+                                        omap, use_omap, omap2)                                                   \
                    : launch_colfft_pipe(k_colfft_pipe<false, G>, L, PipeThreads<G>::v, smem, nwork, map, use_map, \
-                                        omap, 0);
+                                        omap, use_omap, omap2);
       PA_COLFFT_CASE(5) PA_COLFFT_CASE(6) PA_COLFFT_CASE(7) PA_COLFFT_CASE(8) PA_COLFFT_CASE(9)
 #undef PA_COLFFT_CASE
       default: break;
