@@ -31,9 +31,12 @@
 #ifndef PA_SPREAD_MINB
 #define PA_SPREAD_MINB 2
 #endif
-// 1: the row FFT's unpacked rows leave shared memory by TMA stores (My >= 512)
+// 1: the row FFT's unpacked rows leave shared memory by TMA stores
 #ifndef PA_ROWFFT_TMA_STORE
 #define PA_ROWFFT_TMA_STORE 1
+#endif
+#ifndef PA_ROWFFT_STORE_MIN_MY
+#define PA_ROWFFT_STORE_MIN_MY 0
 #endif
 // 1: the column FFT's tiles leave shared memory by TMA stores
 #ifndef PA_COLFFT_TMA_STORE
@@ -1326,12 +1329,12 @@ cudaError_t launch_rowfft(const Launch &L) {
     CUtensorMap map, omap;
     const int use_map = encode_2d(h.G0, uint64_t(h.Nt), uint64_t(h.Mx) * h.My, uint64_t(h.Nt) * sizeof(float), 32u,
                                   uint32_t(h.My < 256 ? h.My : 256), &map) ? 1 : 0;
-    // TMA stores of the output (a third buffer of nY1 rows) where a block
-    // per SM is all the two input buffers allow anyway (My >= 512)
+    // TMA stores of the output from a third buffer of nY1 rows (measured
+    // faster at My = 256 and 512 although it lowers the blocks per SM)
     const int hb = h.nY1 <= 256 ? h.nY1 : (h.nY1 + 1) / 2;
     const size_t osmem = size_t(h.nY1) * 16 * sizeof(float4);
     int use_omap = 0;
-    if (use_map && PA_ROWFFT_TMA_STORE && h.My >= 512 && hb <= 256 && smem + osmem <= smem_optin_limit())
+    if (use_map && PA_ROWFFT_TMA_STORE && h.My >= PA_ROWFFT_STORE_MIN_MY && hb <= 256 && smem + osmem <= smem_optin_limit())
       use_omap = encode_2d(h.T, 2 * uint64_t(h.Nt), uint64_t(h.Mx) * h.nY1, uint64_t(h.Nt) * sizeof(float2), 64u,
                            uint32_t(hb), &omap) ? hb : 0;
     if (use_omap) smem += osmem;
