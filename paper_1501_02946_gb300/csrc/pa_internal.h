@@ -96,6 +96,10 @@ struct InstDesc {
   const int *sp_ustart;
   const int *sp_um;
   int sp_urows;
+  // per spread block: its entries [x, y) (the 8 lists of its columns are one
+  // contiguous range), and the most entries any block has
+  const int2 *sp_erange;
+  int sp_emax;
   // deconvolution factors 1/phihat (window normalised to phi(0) = 1)
   const float *invphx;  // [nX1], jx = ix - hx, at jx / Mx
   const float *invphy;  // [nY1], jy, at jy / My

@@ -233,17 +233,29 @@ __global__ void __launch_bounds__(kThreadsSpread, PA_SPREAD_MINB) k_spread(const
 
 // The spread with the block's g rows staged in shared memory.  A block
 // (8 warps = the 8 columns q0 .. q0 + 7 of one strip, one chunk of CH = 32 S
-// samples) first copies the chunk of every g row its entries use -- its
-// union of sensors, in sorted order -- into shared memory with one bulk copy
-// (TMA engine) per row, then sums exactly as k_spread does (same entries,
-// same order, so the same results), reading the samples from shared memory
-// instead of through L1.  Lane l holds the samples n0 + 4 l + 128 k
-// (k < S / 4): 16-byte shared loads that are bank-conflict free.  Union rows
-// past the buffer's sp_urows rows are read from global memory.
+// samples) first copies into shared memory, with bulk copies (TMA engine):
+// the chunk of every g row its entries use -- its union of sensors, in
+// sorted order, one copy per row -- and its entries (tap products and union
+// slots: the 8 lists of its columns are one contiguous range).  It then sums
+// exactly as k_spread does (same entries, same order, so the same results),
+// reading only shared memory: broadcast loads for the entries, and lane l
+// holds the samples n0 + 4 l + 128 k (k < S / 4) of each row (16-byte,
+// bank-conflict-free loads).  Union rows past the buffer's sp_urows rows are
+// read from global memory.
+template <int S>
+struct SpreadTile {
+  static constexpr int CH = 32 * S;
+  // floats: g rows, then the entries' products (4 floats each), then their
+  // slots (+ 8 for the 16-byte rounding of the copy)
+  __host__ __device__ static size_t floats(int urows, int emax) {
+    return size_t(urows) * CH + 4 * size_t(emax) + size_t(emax) + 8;
+  }
+};
+
 template <int S>
 __global__ void __launch_bounds__(kThreadsSpread, 2) k_spread_tile(const InstDesc *__restrict__ descs, IoPtrs io) {
   griddep_enter();  // the previous kernel of the stream has completed
-  constexpr int P = kSpreadP, QC = kSpreadQC, CH = 32 * S, K4 = S / 4;
+  constexpr int P = kSpreadP, QC = kSpreadQC, CH = SpreadTile<S>::CH, K4 = S / 4;
   static_assert(P == 4 && QC * 32 == kThreadsSpread, "tile shape");
   static_assert(S % 4 == 0, "samples per lane load as float4");
   extern __shared__ __align__(128) float4 smem_a128[];
@@ -263,29 +275,28 @@ __global__ void __launch_bounds__(kThreadsSpread, 2) k_spread_tile(const InstDes
   const int blk = st * ncb + cb;
   const int u0 = __ldg(d.sp_ustart + blk), nu = __ldg(d.sp_ustart + blk + 1) - u0;
   const int ur = min(nu, d.sp_urows);
+  const int2 er = __ldg(d.sp_erange + blk);
+  const int ne = er.y - er.x, ea_al = er.x & ~3, eb_al = (er.y + 3) & ~3;
+  float4 *W = reinterpret_cast<float4 *>(Gs + (size_t)d.sp_urows * CH);  // [sp_emax] tap products
+  int *SL = reinterpret_cast<int *>(W + d.sp_emax);                      // slots from entry ea_al on
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid == 0) {
     mbar_init(&bar, 1);
     mbar_fence_init();
   }
   __syncthreads();
-  if (tid == 0) mbar_arrive_expect_tx(&bar, uint32_t(ur) * uint32_t(nv) * 4u);
+  if (tid == 0)
+    mbar_arrive_expect_tx(&bar, uint32_t(ur) * uint32_t(nv) * 4u + uint32_t(ne) * 16u + uint32_t(eb_al - ea_al) * 4u);
   for (int u = tid; u < ur; u += kThreadsSpread)
     bulk_g2s(Gs + (size_t)u * CH, g + (size_t)__ldg(d.sp_um + u0 + u) * Nt + n0, uint32_t(nv) * 4u, &bar);
-  // the warp's list bounds and its first window of entries load while the
-  // rows are in flight
+  if (tid == kThreadsSpread - 32 && ne > 0) bulk_g2s(W, d.sp_w + er.x, uint32_t(ne) * 16u, &bar);
+  if (tid == kThreadsSpread - 31 && eb_al > ea_al) bulk_g2s(SL, d.sp_slot + ea_al, uint32_t(eb_al - ea_al) * 4u, &bar);
+  // the warp's list bounds load while the copies are in flight
   const int q = cb * QC + (tid >> 5);
-  const int *__restrict__ es = d.sp_slot;
-  const float4 *__restrict__ ew = d.sp_w;
-  int e0 = 0, e1 = 0, sj = 0;
-  float4 wj = make_float4(0.f, 0.f, 0.f, 0.f);
+  int e0 = 0, e1 = 0;
   if (q < My) {
-    e0 = __ldg(d.sp_start + (size_t)st * My + q);
-    e1 = __ldg(d.sp_start + (size_t)st * My + q + 1);
-    if (lane < e1 - e0) {
-      sj = __ldg(es + e0 + lane);
-      wj = __ldg(ew + e0 + lane);
-    }
+    e0 = __ldg(d.sp_start + (size_t)st * My + q) - er.x;
+    e1 = __ldg(d.sp_start + (size_t)st * My + q + 1) - er.x;
   }
   if (__syncthreads_or(!mbar_wait(&bar, 0))) {
     if (tid == 0) atomicOr(d.status, kStatusWaitTimeout);
@@ -294,47 +305,34 @@ __global__ void __launch_bounds__(kThreadsSpread, 2) k_spread_tile(const InstDes
   }
   if (q >= My) return;  // whole warps leave; no block barrier follows
   const int p0 = st * P;
+  const int *SLe = SL + (er.x - ea_al);  // slot of block entry e at SLe[e]
   float4 acc[P][K4];
 #pragma unroll
   for (int r = 0; r < P; ++r)
 #pragma unroll
     for (int k = 0; k < K4; ++k) acc[r][k] = make_float4(0.f, 0.f, 0.f, 0.f);
-  // entries in windows of 32: lane j loads entry j's slot and tap products,
-  // entry b reaches every lane by shuffles
-  for (int e = e0; e < e1; e += 32) {
-    const int cnt = min(32, e1 - e);
-    if (e > e0) {
-      sj = 0;
-      wj = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (lane < cnt) {
-        sj = __ldg(es + e + lane);
-        wj = __ldg(ew + e + lane);
-      }
-    }
 #pragma unroll 4
-    for (int b = 0; b < cnt; ++b) {
-      const int slot = __shfl_sync(0xffffffffu, sj, b);
-      const float4 w = make_float4(__shfl_sync(0xffffffffu, wj.x, b), __shfl_sync(0xffffffffu, wj.y, b),
-                                   __shfl_sync(0xffffffffu, wj.z, b), __shfl_sync(0xffffffffu, wj.w, b));
-      float4 v[K4];
-      if (slot < ur) {
-        const float4 *row = reinterpret_cast<const float4 *>(Gs + (size_t)slot * CH) + lane;
+  for (int e = e0; e < e1; ++e) {
+    const int slot = SLe[e];
+    const float4 w = W[e];
+    float4 v[K4];
+    if (slot < ur) {
+      const float4 *row = reinterpret_cast<const float4 *>(Gs + (size_t)slot * CH) + lane;
 #pragma unroll
-        for (int k = 0; k < K4; ++k) v[k] = row[32 * k];
-      } else {
-        const float *row = g + (size_t)__ldg(d.sp_um + u0 + slot) * Nt + n0 + 4 * lane;
+      for (int k = 0; k < K4; ++k) v[k] = row[32 * k];
+    } else {
+      const float *row = g + (size_t)__ldg(d.sp_um + u0 + slot) * Nt + n0 + 4 * lane;
 #pragma unroll
-        for (int k = 0; k < K4; ++k)
-          v[k] = 4 * lane + 128 * k < nv ? __ldg(reinterpret_cast<const float4 *>(row + 128 * k))
-                                         : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
+      for (int k = 0; k < K4; ++k)
+        v[k] = 4 * lane + 128 * k < nv ? __ldg(reinterpret_cast<const float4 *>(row + 128 * k))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 #pragma unroll
-      for (int k = 0; k < K4; ++k) {
-        fma4(w.x, v[k], acc[0][k]);
-        fma4(w.y, v[k], acc[1][k]);
-        fma4(w.z, v[k], acc[2][k]);
-        fma4(w.w, v[k], acc[3][k]);
-      }
+    for (int k = 0; k < K4; ++k) {
+      fma4(w.x, v[k], acc[0][k]);
+      fma4(w.y, v[k], acc[1][k]);
+      fma4(w.z, v[k], acc[2][k]);
+      fma4(w.w, v[k], acc[3][k]);
     }
   }
 #pragma unroll
@@ -1277,7 +1275,7 @@ static cudaError_t set_smem(K kernel, size_t smem) {
 template <int S>
 static cudaError_t launch_spread_tile(const Launch &L) {
   const InstDesc &h = *L.host;
-  const size_t smem = size_t(h.sp_urows > 0 ? h.sp_urows : 1) * 32 * S * sizeof(float);
+  const size_t smem = SpreadTile<S>::floats(h.sp_urows, h.sp_emax) * sizeof(float);
   auto kern = k_spread_tile<S>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
@@ -1286,7 +1284,8 @@ static cudaError_t launch_spread_tile(const Launch &L) {
 
 cudaError_t launch_spread(const Launch &L, int spl) {
   if (L.host && !L.work && L.host->sp_slot && (L.host->Nt % 4) == 0 &&
-      (reinterpret_cast<uintptr_t>(L.io.g_in) & 15u) == 0 && PA_SPREAD_TILE) {
+      (reinterpret_cast<uintptr_t>(L.io.g_in) & 15u) == 0 && PA_SPREAD_TILE &&
+      SpreadTile<8>::floats(L.host->sp_urows, L.host->sp_emax) * sizeof(float) <= smem_optin_limit()) {
     if (spl == 8) return launch_spread_tile<8>(L);
     if (spl == 4) return launch_spread_tile<4>(L);
   }

@@ -377,9 +377,11 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
   // strip, the sensors of its entries in sorted order, and each entry's
   // position in its block's union.
   const int QC = pa::kSpreadQC, ncb = (My + QC - 1) / QC;
-  std::vector<int> sp_slot(nent), sp_ustart(size_t(nstrips) * ncb + 1, 0), sp_um;
+  // (sp_slot is padded so that a block's slots copy as whole 16-byte words)
+  std::vector<int> sp_slot(nent + 8, 0), sp_ustart(size_t(nstrips) * ncb + 1, 0), sp_um;
+  std::vector<int2> sp_erange(size_t(nstrips) * ncb);
   sp_um.reserve(nent / 4 + 16);
-  int umax = 0;
+  int umax = 0, emax = 0;
   {
     std::vector<int> uni;
     for (int st = 0; st < nstrips; ++st) {
@@ -393,13 +395,16 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
         for (size_t e = ea; e < eb; ++e)
           sp_slot[e] = int(std::lower_bound(uni.begin(), uni.end(), sp_i[e]) - uni.begin());
         sp_ustart[blk] = int(sp_um.size());
+        sp_erange[blk] = make_int2(int(ea), int(eb));
         for (int i : uni) sp_um.push_back(perm[i]);
         umax = std::max(umax, int(uni.size()));
+        emax = std::max(emax, int(eb - ea));
       }
     }
     sp_ustart.back() = int(sp_um.size());
   }
   P->h.sp_urows = std::min(umax, pa::kSpreadUrowsMax);
+  P->h.sp_emax = emax;
   size_t off = 0;
   auto place = [&](size_t bytes) {
     const size_t o = off;
@@ -412,6 +417,7 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
   const size_t o_sl = place(sizeof(int) * sp_slot.size());
   const size_t o_us = place(sizeof(int) * sp_ustart.size());
   const size_t o_um = place(sizeof(int) * sp_um.size());
+  const size_t o_er = place(sizeof(int2) * sp_erange.size());
   const size_t need = off;
   if (need > P->entries_bytes) {
     if (P->d_entries) {
@@ -430,6 +436,7 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
   P->h.sp_slot = reinterpret_cast<const int *>(V + o_sl);
   P->h.sp_ustart = reinterpret_cast<const int *>(V + o_us);
   P->h.sp_um = reinterpret_cast<const int *>(V + o_um);
+  P->h.sp_erange = reinterpret_cast<const int2 *>(V + o_er);
   auto upv = [&](const void *dst, const void *src, size_t bytes) {
     return bytes ? cudaMemcpyAsync(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice, stream)
                  : cudaSuccess;
@@ -440,6 +447,7 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
   PA_CUDA(upv(P->h.sp_slot, sp_slot.data(), sizeof(int) * sp_slot.size()));
   PA_CUDA(upv(P->h.sp_ustart, sp_ustart.data(), sizeof(int) * sp_ustart.size()));
   PA_CUDA(upv(P->h.sp_um, sp_um.data(), sizeof(int) * sp_um.size()));
+  PA_CUDA(upv(P->h.sp_erange, sp_erange.data(), sizeof(int2) * sp_erange.size()));
   // pageable sources: the copies above are complete when they return
   return PA_OK;
 }
@@ -1190,7 +1198,8 @@ int pa_plan_update_positions_device(pa_plan *plan, const float *xy_dev, void *st
   h.sp_w = a.sp_w;
   // the staged spread's union lists are built on the host only
   h.sp_slot = h.sp_ustart = h.sp_um = nullptr;
-  h.sp_urows = 0;
+  h.sp_erange = nullptr;
+  h.sp_urows = h.sp_emax = 0;
   // pageable source: the copy has consumed the descriptor when it returns
   PA_CUDA(cudaMemcpyAsync(P->d_desc, &h, sizeof(InstDesc), cudaMemcpyHostToDevice, s));
   return PA_OK;
