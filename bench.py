@@ -385,11 +385,25 @@ def run_ours(args):
     import paper_1501_02946_gb300 as pa
     import synth
 
-    P = synth.c3()
+    if args.case == "columns128":
+        # the large workload's sample count, depth and kernel instantiations on
+        # a 128x128 grid (16384 dart-thrown sensors, random data): a case small
+        # enough for a profiler's full metric set
+        import numpy as np
+        rng = np.random.default_rng(7)
+        xy = synth.dart_throwing(rng, 128 * 128, 128 * 0.5e-4, 4e-5)
+        grid = synth.Grid(128, 128, 512, 1e-4, 1e-4, 1e-4)
+        P = synth.Problem("columns128", xy, np.full(xy.shape[0], (128e-4) ** 2 / xy.shape[0]),
+                          rng.normal(size=(xy.shape[0], 1024)), 10e-9, synth.C_WATER, grid)
+    else:
+        P = synth.c3()
     Nx, Ny, Nz = P.grid.shape
     voxels = Nx * Ny * Nz
     plan = pa.Plan(P.xy, P.n_t, P.dt, P.c, P.grid.as_tuple(), weights=P.h)
-    shapes = plan.autotune()  # plan setup, outside the timed region
+    # plan setup, outside the timed region; a profiled step keeps the default
+    # shapes (what the tuner keeps at this size) so that a profiler's slowdown
+    # of the tuning launches cannot change them
+    shapes = plan.autotune() if not args.profile_step else "default"
     g = torch.tensor(P.g, dtype=torch.float32, device=dev)
     f = torch.empty(P.grid.shape, dtype=torch.float32, device=dev)
     g2 = torch.empty_like(g)
@@ -725,7 +739,11 @@ def main():
     ap.add_argument("--batch", action="store_true", help="time the uneven 64-instance batch alone")
     ap.add_argument("--profile-step", action="store_true",
                     help="run one step between cudaProfilerStart/Stop (for ncu --profile-from-start off) and exit")
+    ap.add_argument("--case", choices=["workload", "columns128"], default="workload",
+                    help="with --profile-step: the workload, or its transform lengths on a 128x128 grid")
     args = ap.parse_args()
+    if args.case != "workload" and not args.profile_step:
+        ap.error("--case selects the profiled step's problem; it needs --profile-step")
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

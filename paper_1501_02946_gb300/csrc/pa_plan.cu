@@ -927,7 +927,7 @@ int create_plan(pa_plan **out, int64_t n_sensors, const double *sensor_xy, const
   if (pa::smem_ner(h) > 48 * 1024) h.ner_cb = 2;
   // launch shapes before any tuning (pa_plan_autotune measures the others)
   h.spread_spl = Nt > 128 ? 8 : 4;
-  h.interp_ty = width <= 8 ? 32 : 16;
+  h.interp_ty = 16;  // measured fastest at 128x128x256 and 256x256x512 (pa_plan_autotune may change it)
   h.ner_lperm = ner_lperm_for(h.Nz, h.ner_cb);
 
   // deconvolution tables and time-frequency constants
