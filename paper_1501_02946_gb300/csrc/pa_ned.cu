@@ -46,6 +46,10 @@
 #ifndef PA_ROWIFFT_TMA_STORE
 #define PA_ROWIFFT_TMA_STORE 1
 #endif
+// blocks per SM the staged spread's register budget is set for
+#ifndef PA_SPREAD_TILE_MINB
+#define PA_SPREAD_TILE_MINB 3
+#endif
 // 1: single-plan spreads stage their g rows in shared memory (k_spread_tile)
 #ifndef PA_SPREAD_TILE
 #define PA_SPREAD_TILE 1
@@ -253,7 +257,7 @@ struct SpreadTile {
 };
 
 template <int S>
-__global__ void __launch_bounds__(kThreadsSpread, 2) k_spread_tile(const InstDesc *__restrict__ descs, IoPtrs io) {
+__global__ void __launch_bounds__(kThreadsSpread, PA_SPREAD_TILE_MINB) k_spread_tile(const InstDesc *__restrict__ descs, IoPtrs io) {
   griddep_enter();  // the previous kernel of the stream has completed
   constexpr int P = kSpreadP, QC = kSpreadQC, CH = SpreadTile<S>::CH, K4 = S / 4;
   static_assert(P == 4 && QC * 32 == kThreadsSpread, "tile shape");
