@@ -48,7 +48,10 @@
 #endif
 // blocks per SM the staged spread's register budget is set for
 #ifndef PA_SPREAD_TILE_MINB
-#define PA_SPREAD_TILE_MINB 3
+#define PA_SPREAD_TILE_MINB 4
+#endif
+#ifndef PA_SPREAD_TILE4_MINB
+#define PA_SPREAD_TILE4_MINB 4
 #endif
 // 1: single-plan spreads stage their g rows in shared memory (k_spread_tile)
 #ifndef PA_SPREAD_TILE
@@ -257,7 +260,7 @@ struct SpreadTile {
 };
 
 template <int S>
-__global__ void __launch_bounds__(kThreadsSpread, PA_SPREAD_TILE_MINB) k_spread_tile(const InstDesc *__restrict__ descs, IoPtrs io) {
+__global__ void __launch_bounds__(kThreadsSpread, S == 4 ? PA_SPREAD_TILE4_MINB : PA_SPREAD_TILE_MINB) k_spread_tile(const InstDesc *__restrict__ descs, IoPtrs io) {
   griddep_enter();  // the previous kernel of the stream has completed
   constexpr int P = kSpreadP, QC = kSpreadQC, CH = SpreadTile<S>::CH, K4 = S / 4;
   static_assert(P == 4 && QC * 32 == kThreadsSpread, "tile shape");
