@@ -395,6 +395,14 @@ def run_ours(args):
         grid = synth.Grid(128, 128, 512, 1e-4, 1e-4, 1e-4)
         P = synth.Problem("columns128", xy, np.full(xy.shape[0], (128e-4) ** 2 / xy.shape[0]),
                           rng.normal(size=(xy.shape[0], 1024)), 10e-9, synth.C_WATER, grid)
+    elif args.case == "rows256":
+        # the large workload's grid, sensors and depth with 256 samples: its
+        # spatial and image transform lengths (512-point row and column FFTs,
+        # 256-point image transforms) at a quarter of its G0
+        import numpy as np
+        P0 = synth.c3()
+        P = synth.Problem("rows256", P0.xy, P0.h, np.random.default_rng(7).normal(size=(P0.xy.shape[0], 256)),
+                          P0.dt, P0.c, P0.grid)
     else:
         P = synth.c3()
     Nx, Ny, Nz = P.grid.shape
@@ -739,8 +747,9 @@ def main():
     ap.add_argument("--batch", action="store_true", help="time the uneven 64-instance batch alone")
     ap.add_argument("--profile-step", action="store_true",
                     help="run one step between cudaProfilerStart/Stop (for ncu --profile-from-start off) and exit")
-    ap.add_argument("--case", choices=["workload", "columns128"], default="workload",
-                    help="with --profile-step: the workload, or its transform lengths on a 128x128 grid")
+    ap.add_argument("--case", choices=["workload", "columns128", "rows256"], default="workload",
+                    help="with --profile-step: the workload; its sample count and depth on a 128x128 grid "
+                         "(columns128); or its grid with 256 samples (rows256)")
     args = ap.parse_args()
     if args.case != "workload" and not args.profile_step:
         ap.error("--case selects the profiled step's problem; it needs --profile-step")
