@@ -63,12 +63,29 @@ namespace pa {
 namespace {
 
 constexpr int kThreadsCol = 256;
-// Block size of the persistent transform pipelines of length 2^LGL: 512
-// threads from length 512 on, where the two tile buffers leave room for one
-// block per SM only.
+// Tiles of the persistent transform pipelines of length 2^LGL: nc sample
+// pairs (row transforms) or complex samples (column transform) per tile,
+// threads per block, and the blocks per SM their registers are budgeted for.
+// Below length 512: 16 per tile, 256 threads.  From length 512 on, PA_FFT9_NCP
+// per tile and PA_FFT9_THREADS threads (16 and 512: two tile buffers of
+// 64 KB, one block per SM).
+#ifndef PA_FFT9_NCP
+#define PA_FFT9_NCP 16
+#endif
+#ifndef PA_FFT9_THREADS
+#define PA_FFT9_THREADS 512
+#endif
+#ifndef PA_FFT9_MINB
+#define PA_FFT9_MINB 1
+#endif
+static_assert(PA_FFT9_NCP == 16 || PA_FFT9_NCP == 8, "length-512 tile width");
+__host__ __device__ constexpr int pipe_nc(int lgl) { return lgl >= 9 ? PA_FFT9_NCP : 16; }
 template <int LGL>
-struct PipeThreads {
-  static constexpr int v = LGL >= 9 ? 512 : 256;
+struct PipeTile {
+  static constexpr int threads = LGL >= 9 ? PA_FFT9_THREADS : 256;
+  static constexpr int minb = LGL >= 9 ? PA_FFT9_MINB : 1;
+  static constexpr int nc = pipe_nc(LGL);
+  static constexpr int lgnc = nc == 16 ? 4 : 3;
 };
 constexpr int kThreadsSpread = 256;  // 8 warps = 8 grid columns of one strip
 constexpr int kThreadsInterp = 256;
@@ -498,14 +515,14 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft(const InstDesc *__restri
 // 0 .. hx, in omap; hx for rows 0 .. hx - 1, from bins L - hx .. L - 1, in
 // omap2).
 template <bool ADJ, int LGL>
-__global__ void __launch_bounds__(PipeThreads<LGL>::v) k_colfft_pipe(const InstDesc *__restrict__ descs, int nwork,
+__global__ void __launch_bounds__(PipeTile<LGL>::threads, PipeTile<LGL>::minb) k_colfft_pipe(const InstDesc *__restrict__ descs, int nwork,
                                                              const __grid_constant__ CUtensorMap map, int use_map,
                                                              const __grid_constant__ CUtensorMap omap, int use_omap,
                                                              const __grid_constant__ CUtensorMap omap2) {
   griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
   __shared__ __align__(8) uint64_t bars[2];
-  constexpr int L = 1 << LGL, NC = kColNC, LGNC = 4, BOX = L < 256 ? L : 256;
+  constexpr int L = 1 << LGL, NC = PipeTile<LGL>::nc, LGNC = PipeTile<LGL>::lgnc, BOX = L < 256 ? L : 256;
   static_assert(NC == 1 << LGNC, "tile width");
   float2 *buf0 = reinterpret_cast<float2 *>(smem_a128);
   float2 *buf1 = buf0 + L * NC;
@@ -606,13 +623,13 @@ __global__ void __launch_bounds__(PipeThreads<LGL>::v) k_colfft_pipe(const InstD
 // T (floats; dims 2 Nt, Mx nY1; box 64 x hb): one box when hb = nY1, else
 // two (rows [0, hb) and [nY1 - hb, nY1)).
 template <int LGL>
-__global__ void __launch_bounds__(PipeThreads<LGL>::v) k_rowfft_pipe(const InstDesc *__restrict__ descs, int nwork,
+__global__ void __launch_bounds__(PipeTile<LGL>::threads, PipeTile<LGL>::minb) k_rowfft_pipe(const InstDesc *__restrict__ descs, int nwork,
                                                              const __grid_constant__ CUtensorMap map, int use_map,
                                                              const __grid_constant__ CUtensorMap omap, int use_omap) {
   griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
   __shared__ __align__(8) uint64_t bars[2];
-  constexpr int L = 1 << LGL, NCP = 16, LGNCP = 4, BOX = L < 256 ? L : 256;
+  constexpr int L = 1 << LGL, NCP = PipeTile<LGL>::nc, LGNCP = PipeTile<LGL>::lgnc, BOX = L < 256 ? L : 256;
   float2 *buf0 = reinterpret_cast<float2 *>(smem_a128);  // [My][NCP] sample pairs
   float2 *buf1 = buf0 + L * NCP;
   const InstDesc &d = descs[0];
@@ -747,13 +764,13 @@ __global__ void __launch_bounds__(kThreadsCol) k_rowifft(const InstDesc *__restr
 // stored by the TMA engine; the next tile's spectrum is built in the same
 // buffer only after the stores have read it.
 template <int LGL>
-__global__ void __launch_bounds__(PipeThreads<LGL>::v) k_rowifft_pipe(const InstDesc *__restrict__ descs, int nwork,
+__global__ void __launch_bounds__(PipeTile<LGL>::threads, PipeTile<LGL>::minb) k_rowifft_pipe(const InstDesc *__restrict__ descs, int nwork,
                                                               const __grid_constant__ CUtensorMap map, int use_map,
                                                               const __grid_constant__ CUtensorMap omap, int use_omap) {
   griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
   __shared__ __align__(8) uint64_t bars[2];
-  constexpr int L = 1 << LGL, NCP = 16, LGNCP = 4;
+  constexpr int L = 1 << LGL, NCP = PipeTile<LGL>::nc, LGNCP = PipeTile<LGL>::lgnc;
   const InstDesc &d = descs[0];
   if (!smem_aligned_128(smem_a128, d.status)) return;
   const int Nt = d.Nt, nY1 = d.nY1;
@@ -1329,20 +1346,20 @@ static bool encode_g0_box(const InstDesc &h, int hx, int hy, CUtensorMap *map) {
 cudaError_t launch_rowfft(const Launch &L) {
   if (L.host && !L.work && (L.host->Nt % 4) == 0) {
     const InstDesc &h = *L.host;
-    const int lg = pow2_log(h.My);
-    const int nwork = h.Mx * ((h.Nt + 31) / 32);
-    size_t smem = 2 * size_t(h.My) * 16 * sizeof(float2);
+    const int lg = pow2_log(h.My), ncp = pipe_nc(lg);
+    const int nwork = h.Mx * ((h.Nt + 2 * ncp - 1) / (2 * ncp));
+    size_t smem = 2 * size_t(h.My) * ncp * sizeof(float2);
     CUtensorMap map, omap;
-    const int use_map = encode_2d(h.G0, uint64_t(h.Nt), uint64_t(h.Mx) * h.My, uint64_t(h.Nt) * sizeof(float), 32u,
-                                  uint32_t(h.My < 256 ? h.My : 256), &map) ? 1 : 0;
+    const int use_map = encode_2d(h.G0, uint64_t(h.Nt), uint64_t(h.Mx) * h.My, uint64_t(h.Nt) * sizeof(float),
+                                  uint32_t(2 * ncp), uint32_t(h.My < 256 ? h.My : 256), &map) ? 1 : 0;
     // TMA stores of the output from a third buffer of nY1 rows (measured
     // faster at My = 256 and 512 although it lowers the blocks per SM)
     const int hb = h.nY1 <= 256 ? h.nY1 : (h.nY1 + 1) / 2;
-    const size_t osmem = size_t(h.nY1) * 16 * sizeof(float4);
+    const size_t osmem = size_t(h.nY1) * ncp * sizeof(float4);
     int use_omap = 0;
     if (use_map && PA_ROWFFT_TMA_STORE && h.My >= PA_ROWFFT_STORE_MIN_MY && hb <= 256 && smem + osmem <= smem_optin_limit())
-      use_omap = encode_2d(h.T, 2 * uint64_t(h.Nt), uint64_t(h.Mx) * h.nY1, uint64_t(h.Nt) * sizeof(float2), 64u,
-                           uint32_t(hb), &omap) ? hb : 0;
+      use_omap = encode_2d(h.T, 2 * uint64_t(h.Nt), uint64_t(h.Mx) * h.nY1, uint64_t(h.Nt) * sizeof(float2),
+                           uint32_t(4 * ncp), uint32_t(hb), &omap) ? hb : 0;
     if (use_omap) smem += osmem;
     else std::memset(&omap, 0, sizeof(omap));
     switch (lg) {
@@ -1351,8 +1368,8 @@ cudaError_t launch_rowfft(const Launch &L) {
     auto kern = k_rowfft_pipe<G>;                                                                         \
     const cudaError_t e = set_smem(kern, smem);                                                           \
     if (e != cudaSuccess) return e;                                                                       \
-    const int grid = persistent_grid(kern, PipeThreads<G>::v, smem, nwork);                               \
-    return launch_pdl(kern, grid, PipeThreads<G>::v, smem, L.stream, L.descs, nwork, map, use_map, omap,  \
+    const int grid = persistent_grid(kern, PipeTile<G>::threads, smem, nwork);                               \
+    return launch_pdl(kern, grid, PipeTile<G>::threads, smem, L.stream, L.descs, nwork, map, use_map, omap,  \
                       use_omap);                                                                          \
   }
       PA_ROWFFT_CASE(5) PA_ROWFFT_CASE(6) PA_ROWFFT_CASE(7) PA_ROWFFT_CASE(8) PA_ROWFFT_CASE(9)
@@ -1380,17 +1397,19 @@ static cudaError_t launch_colfft_pipe(K kernel, const Launch &L, int threads, si
 cudaError_t launch_colfft(const Launch &L, bool adjoint) {
   if (L.host && !L.work && (L.host->Nt % 2) == 0) {
     const InstDesc &h = *L.host;
-    const int lg = pow2_log(h.Mx);
-    const int nwork = h.nY1 * ((h.Nt + kColNC - 1) / kColNC);
-    const size_t smem = 2 * size_t(h.Mx) * kColNC * sizeof(float2);
+    const int lg = pow2_log(h.Mx), nc = pipe_nc(lg);
+    const int nwork = h.nY1 * ((h.Nt + nc - 1) / nc);
+    const size_t smem = 2 * size_t(h.Mx) * nc * sizeof(float2);
     CUtensorMap map;
     int use_map = 0;
     if (!adjoint) {
       use_map = encode_3d(h.T, 2 * uint64_t(h.Nt), uint64_t(h.nY1), uint64_t(h.Mx), uint64_t(h.Nt) * sizeof(float2),
-                          uint64_t(h.nY1) * h.Nt * sizeof(float2), 32u, 1u, uint32_t(h.Mx < 256 ? h.Mx : 256), &map);
-    } else if (h.hx + 1 <= 256 && 2 * h.hx + 1 < h.Mx) {
+                          uint64_t(h.nY1) * h.Nt * sizeof(float2), uint32_t(2 * nc), 1u,
+                          uint32_t(h.Mx < 256 ? h.Mx : 256), &map);
+    } else if (h.hx + 1 <= 256 && 2 * h.hx + 1 < h.Mx && (size_t(h.Mx - h.hx - 1) * nc * sizeof(float2)) % 128 == 0) {
+      // (the second box lands at bin Mx - hx - 1, which must be 128-byte aligned)
       use_map = encode_3d(h.G1, 2 * uint64_t(h.Nt), uint64_t(h.nY1), uint64_t(h.nX1), uint64_t(h.Nt) * sizeof(float2),
-                          uint64_t(h.nY1) * h.Nt * sizeof(float2), 32u, 1u, uint32_t(h.hx + 1), &map);
+                          uint64_t(h.nY1) * h.Nt * sizeof(float2), uint32_t(2 * nc), 1u, uint32_t(h.hx + 1), &map);
     } else {
       std::memset(&map, 0, sizeof(map));
     }
@@ -1403,24 +1422,26 @@ cudaError_t launch_colfft(const Launch &L, bool adjoint) {
     if (use_map && PA_COLFFT_TMA_STORE) {
       if (adjoint) {
         use_omap = encode_3d(h.T, 2 * uint64_t(h.Nt), uint64_t(h.nY1), uint64_t(h.Mx), uint64_t(h.Nt) * sizeof(float2),
-                             uint64_t(h.nY1) * h.Nt * sizeof(float2), 32u, 1u, uint32_t(h.Mx < 256 ? h.Mx : 256),
-                             &omap) ? 1 : 0;
-      } else if (h.hx >= 1 && h.hx + 1 <= 256 && 2 * h.hx + 1 <= h.Mx) {
+                             uint64_t(h.nY1) * h.Nt * sizeof(float2), uint32_t(2 * nc), 1u,
+                             uint32_t(h.Mx < 256 ? h.Mx : 256), &omap) ? 1 : 0;
+      } else if (h.hx >= 1 && h.hx + 1 <= 256 && 2 * h.hx + 1 <= h.Mx &&
+                 (size_t(h.Mx - h.hx) * nc * sizeof(float2)) % 128 == 0) {
+        // (the second box leaves from bin Mx - hx, which must be 128-byte aligned)
         use_omap = encode_3d(h.G1, 2 * uint64_t(h.Nt), uint64_t(h.nY1), uint64_t(h.nX1),
-                             uint64_t(h.Nt) * sizeof(float2), uint64_t(h.nY1) * h.Nt * sizeof(float2), 32u, 1u,
-                             uint32_t(h.hx + 1), &omap) &&
+                             uint64_t(h.Nt) * sizeof(float2), uint64_t(h.nY1) * h.Nt * sizeof(float2),
+                             uint32_t(2 * nc), 1u, uint32_t(h.hx + 1), &omap) &&
                    encode_3d(h.G1, 2 * uint64_t(h.Nt), uint64_t(h.nY1), uint64_t(h.nX1),
-                             uint64_t(h.Nt) * sizeof(float2), uint64_t(h.nY1) * h.Nt * sizeof(float2), 32u, 1u,
-                             uint32_t(h.hx), &omap2) ? 1 : 0;
+                             uint64_t(h.Nt) * sizeof(float2), uint64_t(h.nY1) * h.Nt * sizeof(float2),
+                             uint32_t(2 * nc), 1u, uint32_t(h.hx), &omap2) ? 1 : 0;
       }
     }
     if (!use_omap) std::memset(&omap, 0, sizeof(omap));
     switch (lg) {
 #define PA_COLFFT_CASE(G)                                                                                        \
   case G:                                                                                                        \
-    return adjoint ? launch_colfft_pipe(k_colfft_pipe<true, G>, L, PipeThreads<G>::v, smem, nwork, map, use_map, \
+    return adjoint ? launch_colfft_pipe(k_colfft_pipe<true, G>, L, PipeTile<G>::threads, smem, nwork, map, use_map, \
                                         omap, use_omap, omap2)                                                   \
-                   : launch_colfft_pipe(k_colfft_pipe<false, G>, L, PipeThreads<G>::v, smem, nwork, map, use_map, \
+                   : launch_colfft_pipe(k_colfft_pipe<false, G>, L, PipeTile<G>::threads, smem, nwork, map, use_map, \
                                         omap, use_omap, omap2);
       PA_COLFFT_CASE(5) PA_COLFFT_CASE(6) PA_COLFFT_CASE(7) PA_COLFFT_CASE(8) PA_COLFFT_CASE(9)
 #undef PA_COLFFT_CASE
@@ -1495,28 +1516,29 @@ cudaError_t launch_interp_width(const Launch &L, int width, bool grad, int ty) {
 cudaError_t launch_rowifft(const Launch &L) {
   if (L.host && !L.work && (L.host->Nt % 4) == 0) {
     const InstDesc &h = *L.host;
-    const int lg = pow2_log(h.My);
-    const int nwork = h.Mx * ((h.Nt + 31) / 32);
-    const size_t stage = size_t((h.nY1 * 32 + 15) & ~15);
-    const size_t smem = (size_t(h.My) * 16 + 2 * stage) * sizeof(float2);
+    const int lg = pow2_log(h.My), ncp = pipe_nc(lg);
+    const int nwork = h.Mx * ((h.Nt + 2 * ncp - 1) / (2 * ncp));
+    const size_t stage = size_t((h.nY1 * 2 * ncp + 15) & ~15);
+    const size_t smem = (size_t(h.My) * ncp + 2 * stage) * sizeof(float2);
     CUtensorMap map;
     // the staging rows hold exactly nY1 rows: one box of nY1 rows, or two
     // boxes of ceil(nY1 / 2) rows (boxes are at most 256 high)
     const int hb = h.nY1 <= 256 ? h.nY1 : (h.nY1 + 1) / 2;
     const int use_map = hb <= 256 && encode_2d(h.T, 2 * uint64_t(h.Nt), uint64_t(h.Mx) * h.nY1,
-                                               uint64_t(h.Nt) * sizeof(float2), 64u, uint32_t(hb), &map) ? hb : 0;
+                                               uint64_t(h.Nt) * sizeof(float2), uint32_t(4 * ncp), uint32_t(hb), &map)
+                            ? hb : 0;
     CUtensorMap omap;
     const int use_omap = PA_ROWIFFT_TMA_STORE &&
-                         encode_2d(h.G0, uint64_t(h.Nt), uint64_t(h.Mx) * h.My, uint64_t(h.Nt) * sizeof(float), 32u,
-                                   uint32_t(h.My < 256 ? h.My : 256), &omap) ? 1 : 0;
+                         encode_2d(h.G0, uint64_t(h.Nt), uint64_t(h.Mx) * h.My, uint64_t(h.Nt) * sizeof(float),
+                                   uint32_t(2 * ncp), uint32_t(h.My < 256 ? h.My : 256), &omap) ? 1 : 0;
     switch (lg) {
 #define PA_ROWIFFT_CASE(G)                                                                               \
   case G: {                                                                                              \
     auto kern = k_rowifft_pipe<G>;                                                                       \
     const cudaError_t e = set_smem(kern, smem);                                                          \
     if (e != cudaSuccess) return e;                                                                      \
-    const int grid = persistent_grid(kern, PipeThreads<G>::v, smem, nwork);                              \
-    return launch_pdl(kern, grid, PipeThreads<G>::v, smem, L.stream, L.descs, nwork, map, use_map, omap, \
+    const int grid = persistent_grid(kern, PipeTile<G>::threads, smem, nwork);                              \
+    return launch_pdl(kern, grid, PipeTile<G>::threads, smem, L.stream, L.descs, nwork, map, use_map, omap, \
                       use_omap);                                                                         \
   }
       PA_ROWIFFT_CASE(5) PA_ROWIFFT_CASE(6) PA_ROWIFFT_CASE(7) PA_ROWIFFT_CASE(8) PA_ROWIFFT_CASE(9)
