@@ -67,16 +67,17 @@ constexpr int kThreadsCol = 256;
 // pairs (row transforms) or complex samples (column transform) per tile,
 // threads per block, and the blocks per SM their registers are budgeted for.
 // Below length 512: 16 per tile, 256 threads.  From length 512 on, PA_FFT9_NCP
-// per tile and PA_FFT9_THREADS threads (16 and 512: two tile buffers of
-// 64 KB, one block per SM).
+// per tile, PA_FFT9_THREADS threads and PA_FFT9_MINB blocks per SM: 8, 256
+// and 2 (two tile buffers of 32 KB; two blocks per SM hide each other's
+// barrier waits between the transform passes), or 16, 512 and 1.
 #ifndef PA_FFT9_NCP
-#define PA_FFT9_NCP 16
+#define PA_FFT9_NCP 8
 #endif
 #ifndef PA_FFT9_THREADS
-#define PA_FFT9_THREADS 512
+#define PA_FFT9_THREADS 256
 #endif
 #ifndef PA_FFT9_MINB
-#define PA_FFT9_MINB 1
+#define PA_FFT9_MINB 2
 #endif
 static_assert(PA_FFT9_NCP == 16 || PA_FFT9_NCP == 8, "length-512 tile width");
 __host__ __device__ constexpr int pipe_nc(int lgl) { return lgl >= 9 ? PA_FFT9_NCP : 16; }
@@ -503,10 +504,11 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft(const InstDesc *__restri
 // plan): the rows of the next tile arrive by bulk copies (TMA engine) while
 // the current tile is transformed.  Same arithmetic as k_colfft.
 // With use_map the rows arrive as boxes of a 3-D tensor map (floats): over T
-// (dims 2 Nt, nY1, Mx; box 32 x 1 x min(Mx, 256)) forward, over G1 (dims
-// 2 Nt, nY1, nX1; box 32 x 1 x (hx + 1)) for the adjoint, whose two boxes
-// start at rows hx and -1 (the row before 0 reads as zeros and lands on a
-// bin that is cleared anyway).
+// (dims 2 Nt, nY1, Mx; box 2 NC x 1 x min(Mx, 256)) forward, over G1 (dims
+// 2 Nt, nY1, nX1; box 2 NC x 1 x (hx + kb), kb = use_map = 1 or 2) for the
+// adjoint, whose two boxes start at rows hx and -kb (rows outside the grid
+// read as zeros and land on bins that are cleared anyway); kb makes the
+// second box's destination, bin L - hx - kb, 128-byte aligned.
 // With use_omap (adjoint), the transformed tile leaves shared memory as boxes
 // of the 3-D tensor map omap over T (the forward's input map) stored by the
 // TMA engine; the buffer is refilled only after the stores have read it.
@@ -542,9 +544,10 @@ __global__ void __launch_bounds__(PipeTile<LGL>::threads, PipeTile<LGL>::minb) k
           for (int b = 0; b < L; b += BOX) tma_load_3d(buf + b * NC, &map, 2 * n0, jy, b, bar);
         } else {
           if (use_omap) bulk_wait_read<0>();  // this buffer's last tile has been stored
-          mbar_arrive_expect_tx(bar, uint32_t(2 * (hx + 1) * NC * sizeof(float2)));
-          tma_load_3d(buf, &map, 2 * n0, jy, hx, bar);                       // ix = hx .. 2 hx
-          tma_load_3d(buf + (L - hx - 1) * NC, &map, 2 * n0, jy, -1, bar);  // ix = -1 .. hx - 1
+          const int kb = use_map;
+          mbar_arrive_expect_tx(bar, uint32_t(2 * (hx + kb) * NC * sizeof(float2)));
+          tma_load_3d(buf, &map, 2 * n0, jy, hx, bar);                          // ix = hx .. 2 hx (+ zeros)
+          tma_load_3d(buf + (L - hx - kb) * NC, &map, 2 * n0, jy, -kb, bar);  // ix = -kb .. hx - 1
         }
       }
       return;
@@ -1406,11 +1409,17 @@ cudaError_t launch_colfft(const Launch &L, bool adjoint) {
       use_map = encode_3d(h.T, 2 * uint64_t(h.Nt), uint64_t(h.nY1), uint64_t(h.Mx), uint64_t(h.Nt) * sizeof(float2),
                           uint64_t(h.nY1) * h.Nt * sizeof(float2), uint32_t(2 * nc), 1u,
                           uint32_t(h.Mx < 256 ? h.Mx : 256), &map);
-    } else if (h.hx + 1 <= 256 && 2 * h.hx + 1 < h.Mx && (size_t(h.Mx - h.hx - 1) * nc * sizeof(float2)) % 128 == 0) {
-      // (the second box lands at bin Mx - hx - 1, which must be 128-byte aligned)
-      use_map = encode_3d(h.G1, 2 * uint64_t(h.Nt), uint64_t(h.nY1), uint64_t(h.nX1), uint64_t(h.Nt) * sizeof(float2),
-                          uint64_t(h.nY1) * h.Nt * sizeof(float2), uint32_t(2 * nc), 1u, uint32_t(h.hx + 1), &map);
     } else {
+      // boxes of hx + kb rows, kb = 1 or 2 so that the second lands on a
+      // 128-byte aligned bin Mx - hx - kb; both fit the Mx bins
+      const int kb = (size_t(h.Mx - h.hx - 1) * nc * sizeof(float2)) % 128 == 0 ? 1 : 2;
+      if (h.hx + kb <= 256 && 2 * (h.hx + kb) <= h.Mx &&
+          (size_t(h.Mx - h.hx - kb) * nc * sizeof(float2)) % 128 == 0 &&
+          encode_3d(h.G1, 2 * uint64_t(h.Nt), uint64_t(h.nY1), uint64_t(h.nX1), uint64_t(h.Nt) * sizeof(float2),
+                    uint64_t(h.nY1) * h.Nt * sizeof(float2), uint32_t(2 * nc), 1u, uint32_t(h.hx + kb), &map))
+        use_map = kb;
+    }
+    if (!use_map) {
       std::memset(&map, 0, sizeof(map));
     }
     // outputs by TMA stores (issued by the thread that issues the loads, so

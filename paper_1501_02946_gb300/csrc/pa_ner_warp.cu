@@ -25,6 +25,11 @@
 #ifndef PA_NER_FWD_MINB
 #define PA_NER_FWD_MINB 4
 #endif
+// 1: the adjoint's sliding windows add the points they leave without atomics
+// where no two lanes can reach the same entry.
+#ifndef PA_NER_PLAIN_FLUSH
+#define PA_NER_PLAIN_FLUSH 0
+#endif
 #ifndef PA_NER_ADJ_MINB
 #define PA_NER_ADJ_MINB 4
 #endif
@@ -217,13 +222,69 @@ __device__ __forceinline__ void spread_split(float2 *He, float2 *Ho, ff tau, flo
   }
 }
 
-// Adds v into the half-spectrum entry of grid point pu mod Mt (zeros skipped).
-__device__ __forceinline__ void flush_point(float2 *He, float2 *Ho, int pu, int Mt, float2 v) {
+// Adds v into the half-spectrum entry of grid point pu mod Mt (zeros
+// skipped): atomically, or (plain) by a read-modify-write where no other lane
+// can add to the same entry at the same time.
+__device__ __forceinline__ void flush_point(float2 *He, float2 *Ho, int pu, int Mt, float2 v, bool plain = false) {
   if (v.x == 0.f && v.y == 0.f) return;
   const int p = wrap(pu, Mt);
   float2 *q = ((p & 1) ? Ho : He) + (p >> 1);
-  atomicAdd(&q->x, v.x);
-  atomicAdd(&q->y, v.y);
+  if (plain) {
+    *q = cadd(*q, v);
+  } else {
+    atomicAdd(&q->x, v.x);
+    atomicAdd(&q->y, v.y);
+  }
+}
+
+// Number of lanes i with P[i] <= x, for P[0..31] non-decreasing.
+__device__ __forceinline__ int count_le(const int *P, int x) {
+  int c = 0;
+#pragma unroll
+  for (int st = 16; st > 0; st >>= 1)
+    if (P[c + st - 1] <= x) c += st;
+  if (c < 32 && P[c] <= x) ++c;
+  return c;
+}
+
+// Adds the warp's last sliding windows into the half spectrum: lane i's
+// window acc[t] belongs to the grid point sgn (P[i] + t), t < W, with P
+// non-decreasing in i (lanes without a window hold a P above every point).
+// Neighbouring lanes' windows overlap, often with equal P where tau varies
+// slowly, so instead of one atomic add per lane and point (serialised on the
+// shared addresses) each lane parks its window in F[i][t], and the warp then
+// takes the points P[0] .. pmax + W - 1 one per lane, summing the windows
+// that reach each (lanes count_le(p - W) .. count_le(p) - 1) and adding the
+// sum with a plain read-modify-write: every point is written by one lane.
+// If the points span more than Mt (two could wrap onto one entry) the sums
+// are added atomically.
+template <int W>
+__device__ __forceinline__ void flush_windows(float2 *He, float2 *Ho, float2 *F, const int *P, const float2 (&acc)[W],
+                                              int lane, int pmax, int sgn, int Mt) {
+#pragma unroll
+  for (int t = 0; t < W; ++t) F[lane * W + t] = acc[t];
+  __syncwarp();
+  const int p0 = P[0], npts = pmax + W - p0;
+  const bool plain = npts <= Mt;
+  for (int q0 = 0; q0 < npts; q0 += 32) {
+    const int p = p0 + q0 + lane;
+    if (q0 + lane < npts) {
+      const int hi = count_le(P, p);
+      float2 v = make_float2(0.f, 0.f);
+      for (int i = count_le(P, p - W); i < hi; ++i) v = cadd(v, F[i * W + (p - P[i])]);
+      if (v.x != 0.f || v.y != 0.f) {
+        const int e = wrap(sgn * p, Mt);
+        float2 *q = ((e & 1) ? Ho : He) + (e >> 1);
+        if (plain) {
+          *q = cadd(*q, v);
+        } else {
+          atomicAdd(&q->x, v.x);
+          atomicAdd(&q->y, v.y);
+        }
+      }
+    }
+  }
+  __syncwarp();
 }
 
 // Forward NER, warp v of the grid on slot v: the slot's column (both sources
@@ -333,6 +394,9 @@ __global__ void __launch_bounds__(128, PA_NER_ADJ_MINB) k_ner_warp_adj(const Ins
   float2 *He = reinterpret_cast<float2 *>(smem_f4) + (size_t)wib * (2 * HH + FS);
   float2 *Ho = He + HH;
   float2 *Fs = Ho + HH;
+  static_assert(FS >= 32 * W, "window park in the depth scratch");
+  __shared__ int s_last[4][32];  // last window start of each lane (<= 4 warps per block)
+  int *P = s_last[wib];
   const float2 *twT = d.tw + d.wtw + wtw_T(LGT);
   const float2 *twZ = d.tw + d.wtw + wtw_T(LGZ);
   const float2 *twF = d.tw + d.wtw + wtw_F(LGT + 1);
@@ -358,6 +422,14 @@ __global__ void __launch_bounds__(128, PA_NER_ADJ_MINB) k_ner_warp_adj(const Ins
     // tap advances.  Only the points a window leaves, and its last W, reach
     // shared memory.  l = 0 and the unpaired l = -hz are spread on their own.
     constexpr int C2 = Nz / 64;  // pairs per lane: l = 1 + lane C2 .. (l < hz)
+    // Points a window leaves inside the loop: lane i's are base values in
+    // [first base, last base) of its own depths, ranges that do not overlap
+    // from lane to lane (u increases with l), so lanes never add to the same
+    // +tau point, nor to the same -tau point.  A +tau point and a -tau point
+    // (of two lanes) can be one entry only near 0 (the +tau points start at
+    // 1 - W/2, the -tau points end at W/2 - 1) or, if the points reach Nt,
+    // across the period; elsewhere the loop adds without atomics.
+    const bool far_seam = 2.f * tau_at(d, tb, hz - 1).hi + float(W + 2) < float(Nt);
     float2 acc[W], accn[W];
 #pragma unroll
     for (int t = 0; t < W; ++t) acc[t] = accn[t] = make_float2(0.f, 0.f);
@@ -383,17 +455,19 @@ __global__ void __launch_bounds__(128, PA_NER_ADJ_MINB) k_ner_warp_adj(const Ins
       }
       int adv = pu - base;
       if (adv < 0 || adv >= W) {
+        const bool plain = PA_NER_PLAIN_FLUSH && far_seam && base > W;
 #pragma unroll
         for (int t = 0; t < W; ++t) {
-          flush_point(He, Ho, base + t, 2 * Nt, acc[t]);
-          flush_point(He, Ho, -(base + t), 2 * Nt, accn[t]);
+          flush_point(He, Ho, base + t, 2 * Nt, acc[t], plain);
+          flush_point(He, Ho, -(base + t), 2 * Nt, accn[t], plain);
           acc[t] = accn[t] = make_float2(0.f, 0.f);
         }
         base = pu;
       } else {
         for (; adv > 0; --adv) {
-          flush_point(He, Ho, base, 2 * Nt, acc[0]);
-          flush_point(He, Ho, -base, 2 * Nt, accn[0]);
+          const bool plain = PA_NER_PLAIN_FLUSH && far_seam && base > W;
+          flush_point(He, Ho, base, 2 * Nt, acc[0], plain);
+          flush_point(He, Ho, -base, 2 * Nt, accn[0], plain);
 #pragma unroll
           for (int t = 0; t + 1 < W; ++t) {
             acc[t] = acc[t + 1];
@@ -409,20 +483,21 @@ __global__ void __launch_bounds__(128, PA_NER_ADJ_MINB) k_ner_warp_adj(const Ins
         accn[t] = __ffma2_rn(make_float2(wt[t], wt[t]), vn, accn[t]);
       }
     }
-    if (open) {
-#pragma unroll
-      for (int t = 0; t < W; ++t) {
-        flush_point(He, Ho, base + t, 2 * Nt, acc[t]);
-        flush_point(He, Ho, -(base + t), 2 * Nt, accn[t]);
-      }
-    }
+    // the last windows (points base + t and -(base + t)); base does not
+    // decrease from lane to lane, and the lanes without any depth are last
+    const float2 fs1 = Fs[lane == 0 ? 0 : hz];  // read before Fs takes the windows
+    P[lane] = open ? base : (1 << 29);
+    const int pmax = __reduce_max_sync(0xffffffffu, open ? base : -(1 << 29));
+    __syncwarp();  // every lane's loop (its reads of Fs and its flushes) is done
+    flush_windows<W>(He, Ho, Fs, P, acc, lane, pmax, 1, 2 * Nt);
+    flush_windows<W>(He, Ho, Fs, P, accn, lane, pmax, -1, 2 * Nt);
     if (lane == 0 && ci.jx == 0 && ci.jy == 0) {  // l = 0 (W(j != 0, 0) = 0)
       const ff tau = tau_at(d, tb, 0);
-      spread_split<W>(He, Ho, tau, cscale(Fs[0], weight_of(d, tau, 0) * d.scale * half), d, ht);
+      spread_split<W>(He, Ho, tau, cscale(fs1, weight_of(d, tau, 0) * d.scale * half), d, ht);
     } else if (lane == 1) {  // the depth Nyquist l = -hz also reaches -tau
       const int l = -hz;
       const ff tau = tau_at(d, tb, l);
-      const float2 hv = cscale(Fs[hz], 0.5f * weight_of(d, tau, l) * d.scale);
+      const float2 hv = cscale(fs1, 0.5f * weight_of(d, tau, l) * d.scale);
       if (!nyq) {
         spread_split<W>(He, Ho, tau, hv, d, ht);
         spread_split<W>(He, Ho, ff_neg(tau), hv, d, ht);
