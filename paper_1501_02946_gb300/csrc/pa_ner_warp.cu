@@ -28,7 +28,7 @@
 // 1: the adjoint's sliding windows add the points they leave without atomics
 // where no two lanes can reach the same entry.
 #ifndef PA_NER_PLAIN_FLUSH
-#define PA_NER_PLAIN_FLUSH 0
+#define PA_NER_PLAIN_FLUSH 1
 #endif
 #ifndef PA_NER_ADJ_MINB
 #define PA_NER_ADJ_MINB 4
