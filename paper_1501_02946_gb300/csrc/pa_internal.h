@@ -87,7 +87,7 @@ struct InstDesc {
   const float4 *sp_w;
   // the same entries for the staged spread: block b = strip * ceil(My / 8)
   // + (q / 8) stages the g rows of its union of sensors (caller indices
-  // sp_um[sp_ustart[b] ..  sp_ustart[b + 1]), in sorted order) in shared
+  // sp_um[sp_ustart[b] ..  sp_ustart[b + 1]), most used first) in shared
   // memory, and entry e names its sensor by the position sp_slot[e] in that
   // union; sp_urows is the number of rows the staging buffer holds (rows past
   // it are read from global memory).  Null when not built (then the spread
@@ -157,6 +157,11 @@ struct IoPtrs {
 constexpr int kSpreadP = 4;      // oversampled rows per forward spread strip
 constexpr int kSpreadQC = 8;     // columns per spread block (one warp each)
 constexpr int kSpreadUrowsMax = 128;  // g rows the staged spread holds in shared memory
+constexpr int kSpreadUrowsMin = 32;   // ... at least, when held down for more blocks per SM
+constexpr int kSpreadTileBlocks = 4;  // staged-spread blocks per SM its shared memory is sized for
+// floats of a staged-spread block after its g rows: the entries' tap products
+// (4 each), their slots, and 8 for the 16-byte rounding of the slot copy
+inline long SpreadTileEntryFloats(int emax) { return 5L * emax + 8; }
 constexpr int kColNC = 16;       // samples per column-FFT tile
 constexpr int kInterpNC = 32;    // samples per adjoint interpolation tile
 constexpr int kImgZC = 16;       // depth samples per inverse-x tile

@@ -259,14 +259,15 @@ __global__ void __launch_bounds__(kThreadsSpread, PA_SPREAD_MINB) k_spread(const
 // The spread with the block's g rows staged in shared memory.  A block
 // (8 warps = the 8 columns q0 .. q0 + 7 of one strip, one chunk of CH = 32 S
 // samples) first copies into shared memory, with bulk copies (TMA engine):
-// the chunk of every g row its entries use -- its union of sensors, in
-// sorted order, one copy per row -- and its entries (tap products and union
+// the chunk of every g row its entries use -- its union of sensors, most
+// used first, one copy per row -- and its entries (tap products and union
 // slots: the 8 lists of its columns are one contiguous range).  It then sums
 // exactly as k_spread does (same entries, same order, so the same results),
 // reading only shared memory: broadcast loads for the entries, and lane l
 // holds the samples n0 + 4 l + 128 k (k < S / 4) of each row (16-byte,
-// bank-conflict-free loads).  Union rows past the buffer's sp_urows rows are
-// read from global memory.
+// bank-conflict-free loads).  Union rows past the buffer's sp_urows rows (the
+// least used; the buffer is sized so that four blocks share an SM) are read
+// from global memory.
 template <int S>
 struct SpreadTile {
   static constexpr int CH = 32 * S;

@@ -381,9 +381,15 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
   std::vector<int> sp_slot(nent + 8, 0), sp_ustart(size_t(nstrips) * ncb + 1, 0), sp_um;
   std::vector<int2> sp_erange(size_t(nstrips) * ncb);
   sp_um.reserve(nent / 4 + 16);
+  // A block's union is ordered by the number of its entries that use each
+  // sensor (most used first), so that when the union is longer than the rows
+  // the kernel stages, the rows it reads from global memory instead serve the
+  // fewest entries.  The sums run in entry order whatever the slots are.
   int umax = 0, emax = 0;
   {
     std::vector<int> uni;
+    std::vector<std::pair<int, int>> cnt;  // (-uses, sensor)
+    std::vector<int> slot_of(size_t(M), 0);
     for (int st = 0; st < nstrips; ++st) {
       for (int cb = 0; cb < ncb; ++cb) {
         const size_t blk = size_t(st) * ncb + cb;
@@ -391,19 +397,42 @@ int upload_sensors(pa_plan *P, const double *xy, cudaStream_t stream) {
         const size_t ea = size_t(sp_start[size_t(st) * My + qa]), eb = size_t(sp_start[size_t(st) * My + qb]);
         uni.assign(sp_i.begin() + ea, sp_i.begin() + eb);
         std::sort(uni.begin(), uni.end());
-        uni.erase(std::unique(uni.begin(), uni.end()), uni.end());
-        for (size_t e = ea; e < eb; ++e)
-          sp_slot[e] = int(std::lower_bound(uni.begin(), uni.end(), sp_i[e]) - uni.begin());
+        cnt.clear();
+        for (size_t k = 0; k < uni.size();) {
+          size_t k1 = k;
+          while (k1 < uni.size() && uni[k1] == uni[k]) ++k1;
+          cnt.emplace_back(-int(k1 - k), uni[k]);
+          k = k1;
+        }
+        std::sort(cnt.begin(), cnt.end());
+        for (size_t k = 0; k < cnt.size(); ++k) slot_of[size_t(cnt[k].second)] = int(k);
+        for (size_t e = ea; e < eb; ++e) sp_slot[e] = slot_of[size_t(sp_i[e])];
         sp_ustart[blk] = int(sp_um.size());
         sp_erange[blk] = make_int2(int(ea), int(eb));
-        for (int i : uni) sp_um.push_back(perm[i]);
-        umax = std::max(umax, int(uni.size()));
+        for (const auto &c : cnt) sp_um.push_back(perm[c.second]);
+        umax = std::max(umax, int(cnt.size()));
         emax = std::max(emax, int(eb - ea));
       }
     }
     sp_ustart.back() = int(sp_um.size());
   }
-  P->h.sp_urows = std::min(umax, pa::kSpreadUrowsMax);
+  // Staged rows: every block reserves the same shared memory, so the longest
+  // union would set it for all.  The rows are held to what lets
+  // kSpreadTileBlocks blocks of 8-sample lanes (1 KB per row) share an SM
+  // (rows past it are read from global memory), unless that leaves fewer
+  // than kSpreadUrowsMin.
+  {
+    // (1 KB of each block's shared memory is reserved by the system)
+    int dev = 0, sm_smem = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) sm_smem = 0;
+    const long budget = long(sm_smem) / pa::kSpreadTileBlocks - 1024 -
+                        4L * long(pa::SpreadTileEntryFloats(emax));
+    const int fit = int(std::max(0L, budget) / (32 * 8 * 4));
+    int cap = std::min(umax, pa::kSpreadUrowsMax);
+    if (fit >= pa::kSpreadUrowsMin) cap = std::min(cap, fit);
+    P->h.sp_urows = cap;
+  }
   P->h.sp_emax = emax;
   size_t off = 0;
   auto place = [&](size_t bytes) {

@@ -415,6 +415,29 @@ def test_cubic_baseline_is_less_accurate():
     assert e_nufft < e_cubic < 1.0
 
 
+def test_staged_spread_rows_past_the_buffer():
+    """Four sensors per output cell (one per oversampled cell): every spread
+    block's union of g rows (about 165) is longer than the rows its shared
+    buffer holds (sized so that four blocks share an SM), so most rows come
+    from global memory.  The forward equals the unstaged spread's (the batch's
+    stage mode) bit for bit, and the oracle."""
+    rng = np.random.default_rng(31)
+    n, nt = 32, 64
+    grid = synth.Grid(n, n, 64, 1e-4, 1e-4, 1e-4)
+    xy = synth.jittered_lattice(rng, 2 * n, 2 * n, grid.dx / 2, grid.dy / 2)
+    X = n * grid.dx
+    P = synth.Problem("dense", xy, np.full(xy.shape[0], X * X / xy.shape[0]), rng.normal(size=(xy.shape[0], nt)),
+                      20e-9, 1500.0, grid)
+    plan = plan_of(P)
+    g = dev(P.g)
+    f = host(plan.reconstruct(g))
+    assert plan.status() == 0
+    fs = torch.empty(plan.image_shape, device="cuda")
+    pa().Batch([plan], mode=1).run([g], [fs])
+    assert np.array_equal(host(fs), f)
+    close(f, ndft.reconstruct(P.xy, P.h, P.g, P.dt, P.c, P.grid), "dense sensors forward vs O1")
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_batch_matches_single_plans(mode):
     rng = np.random.default_rng(5)
