@@ -79,14 +79,14 @@ constexpr int kThreadsCol = 256;
 #ifndef PA_FFT9_MINB
 #define PA_FFT9_MINB 2
 #endif
-static_assert(PA_FFT9_NCP == 16 || PA_FFT9_NCP == 8, "length-512 tile width");
+static_assert(PA_FFT9_NCP == 16 || PA_FFT9_NCP == 8 || PA_FFT9_NCP == 4, "length-512 tile width");
 __host__ __device__ constexpr int pipe_nc(int lgl) { return lgl >= 9 ? PA_FFT9_NCP : 16; }
 template <int LGL>
 struct PipeTile {
   static constexpr int threads = LGL >= 9 ? PA_FFT9_THREADS : 256;
   static constexpr int minb = LGL >= 9 ? PA_FFT9_MINB : 1;
   static constexpr int nc = pipe_nc(LGL);
-  static constexpr int lgnc = nc == 16 ? 4 : 3;
+  static constexpr int lgnc = nc == 16 ? 4 : (nc == 8 ? 3 : 2);
 };
 constexpr int kThreadsSpread = 256;  // 8 warps = 8 grid columns of one strip
 constexpr int kThreadsInterp = 256;
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(kThreadsCol) k_colfft(const InstDesc *__restri
 // the current tile is transformed.  Same arithmetic as k_colfft.
 // With use_map the rows arrive as boxes of a 3-D tensor map (floats): over T
 // (dims 2 Nt, nY1, Mx; box 2 NC x 1 x min(Mx, 256)) forward, over G1 (dims
-// 2 Nt, nY1, nX1; box 2 NC x 1 x (hx + kb), kb = use_map = 1 or 2) for the
+// 2 Nt, nY1, nX1; box 2 NC x 1 x (hx + kb), kb = use_map, 1 to 4) for the
 // adjoint, whose two boxes start at rows hx and -kb (rows outside the grid
 // read as zeros and land on bins that are cleared anyway); kb makes the
 // second box's destination, bin L - hx - kb, 128-byte aligned.
@@ -1411,9 +1411,10 @@ cudaError_t launch_colfft(const Launch &L, bool adjoint) {
                           uint64_t(h.nY1) * h.Nt * sizeof(float2), uint32_t(2 * nc), 1u,
                           uint32_t(h.Mx < 256 ? h.Mx : 256), &map);
     } else {
-      // boxes of hx + kb rows, kb = 1 or 2 so that the second lands on a
+      // boxes of hx + kb rows, kb >= 1 the least that puts the second on a
       // 128-byte aligned bin Mx - hx - kb; both fit the Mx bins
-      const int kb = (size_t(h.Mx - h.hx - 1) * nc * sizeof(float2)) % 128 == 0 ? 1 : 2;
+      int kb = 1;
+      while (kb < 4 && (size_t(h.Mx - h.hx - kb) * nc * sizeof(float2)) % 128 != 0) ++kb;
       if (h.hx + kb <= 256 && 2 * (h.hx + kb) <= h.Mx &&
           (size_t(h.Mx - h.hx - kb) * nc * sizeof(float2)) % 128 == 0 &&
           encode_3d(h.G1, 2 * uint64_t(h.Nt), uint64_t(h.nY1), uint64_t(h.nX1), uint64_t(h.Nt) * sizeof(float2),

@@ -30,11 +30,6 @@
 #ifndef PA_NER_PLAIN_FLUSH
 #define PA_NER_PLAIN_FLUSH 1
 #endif
-// > 0: registers of the forward kernels at Nt = 1024 (else the launch
-// bounds leave them 255, and 8 warps per SM).
-#ifndef PA_NER_FWD10_REGS
-#define PA_NER_FWD10_REGS 0
-#endif
 #ifndef PA_NER_ADJ_MINB
 #define PA_NER_ADJ_MINB 4
 #endif
@@ -296,7 +291,8 @@ __device__ __forceinline__ void flush_windows(float2 *He, float2 *Ho, float2 *F,
 // of a two-source column, which lead at slot v with kind 2) is transformed in
 // t, interpolated at tau(j, l), weighted and transformed back over depth.
 template <int LGT, int LGZ, int W>
-__device__ __forceinline__ void ner_warp_fwd(const InstDesc *__restrict__ descs, const HornerTable &ht) {
+__global__ void __launch_bounds__(128, LGT <= 9 ? PA_NER_FWD_MINB : 1) k_ner_warp(const InstDesc *__restrict__ descs,
+                                                  const __grid_constant__ HornerTable ht) {
   griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ float4 smem_f4[];
   constexpr int Nt = 1 << LGT, Nz = 1 << LGZ;
@@ -377,22 +373,6 @@ __device__ __forceinline__ void ner_warp_fwd(const InstDesc *__restrict__ descs,
   float2 *dst = d.Fz + ((size_t)(lead.jx + d.hx) * d.nY1 + lead.iy) * Nz;
   warp_fft<LGZ, +1>(Fs, twZ, lane, [&](int z) { return Fs[z]; }, [&](int k, float2 y) { dst[k] = y; });
 }
-
-template <int LGT, int LGZ, int W>
-__global__ void __launch_bounds__(128, LGT <= 9 ? PA_NER_FWD_MINB : 1) k_ner_warp(const InstDesc *__restrict__ descs,
-                                                  const __grid_constant__ HornerTable ht) {
-  ner_warp_fwd<LGT, LGZ, W>(descs, ht);
-}
-
-#if PA_NER_FWD10_REGS > 0
-// Nt = 1024 (blocks of two warps) with a register cap instead of the
-// launch-bound budget.
-template <int LGZ, int W>
-__global__ void __maxnreg__(PA_NER_FWD10_REGS) k_ner_warp10(const InstDesc *__restrict__ descs,
-                                                           const __grid_constant__ HornerTable ht) {
-  ner_warp_fwd<10, LGZ, W>(descs, ht);
-}
-#endif
 
 // Adjoint NER: depth DFT of the cotangent column, transposed weight and
 // window (spread into He/Ho), the two inverse Nt-point transforms, their
@@ -578,9 +558,6 @@ cudaError_t launch_warp_kernel(K kernel, const Launch &L, const InstDesc &h, int
 template <int LGT, int LGZ>
 cudaError_t launch_tz(const Launch &L, const InstDesc &h, const HornerTable &ht, int which) {
   if (which == 1) return launch_warp_kernel(k_ner_warp_adj<LGT, LGZ, 8>, L, h, ner_adj_slots(h), ht);
-#if PA_NER_FWD10_REGS > 0
-  if constexpr (LGT == 10) return launch_warp_kernel(k_ner_warp10<LGZ, 8>, L, h, ner_fwd_slots(h), ht);
-#endif
   return launch_warp_kernel(k_ner_warp<LGT, LGZ, 8>, L, h, ner_fwd_slots(h), ht);
 }
 
