@@ -17,6 +17,10 @@ namespace pa {
 namespace {
 
 constexpr int kThreadsImg = 256;
+// Blocks per SM the persistent image transforms budget registers for.
+#ifndef PA_IMG_MINB
+#define PA_IMG_MINB 1
+#endif
 
 __device__ __forceinline__ IoPtrs io_of_img(const IoPtrs &io, const IoPtrs *table, int inst) {
   return table ? table[inst] : io;
@@ -157,7 +161,7 @@ __global__ void __launch_bounds__(kThreadsImg) k_imgy(const InstDesc *__restrict
 // source (floats; dims 2 Nz, nY1, Nx; box 32 x 1 x Nx/2): rows a >= hx to
 // buffer rows 0.., rows a < hx to buffer rows Nx - hx.. (hx = Nx/2).
 template <bool ADJ, int LGL>
-__global__ void __launch_bounds__(kThreadsImg) k_imgx_pipe(const InstDesc *__restrict__ descs, int nwork,
+__global__ void __launch_bounds__(kThreadsImg, PA_IMG_MINB) k_imgx_pipe(const InstDesc *__restrict__ descs, int nwork,
                                                            const __grid_constant__ CUtensorMap map, int use_map) {
   griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
@@ -209,7 +213,7 @@ __global__ void __launch_bounds__(kThreadsImg) k_imgx_pipe(const InstDesc *__res
 // of the 2-D map over f_in (dims Nz, Nx Ny; box 32 x Ny/2), rows y >= hy to
 // buffer rows 0.., rows y < hy to buffer rows Ny - hy.. (hy = Ny/2).
 template <bool ADJ, int LGL>
-__global__ void __launch_bounds__(kThreadsImg) k_imgy_pipe(const InstDesc *__restrict__ descs, int nwork, IoPtrs io,
+__global__ void __launch_bounds__(kThreadsImg, PA_IMG_MINB) k_imgy_pipe(const InstDesc *__restrict__ descs, int nwork, IoPtrs io,
                                                            const __grid_constant__ CUtensorMap map, int use_map) {
   griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ __align__(128) float4 smem_a128[];  // box destinations 128-byte aligned
