@@ -17,9 +17,11 @@ namespace pa {
 namespace {
 
 constexpr int kThreadsImg = 256;
-// Blocks per SM the persistent image transforms budget registers for.
+// Blocks per SM the persistent image transforms budget registers for (with
+// a budget for one, ptxas gives them about 160 registers and one block per
+// SM: 57 -> 73 us at 256x256x512).
 #ifndef PA_IMG_MINB
-#define PA_IMG_MINB 1
+#define PA_IMG_MINB 2
 #endif
 
 __device__ __forceinline__ IoPtrs io_of_img(const IoPtrs &io, const IoPtrs *table, int inst) {

@@ -33,16 +33,6 @@
 #ifndef PA_NER_ADJ_MINB
 #define PA_NER_ADJ_MINB 4
 #endif
-// 1: the adjoint kernels with Nz <= 512 keep each lane's depth values in
-// registers, so that their shared memory is the two half spectra and a park
-// of 8 lanes' windows (at Nt = 1024, 12 warps per SM instead of 10, with a
-// register budget for PA_NER_ADJ10_MINB blocks of two warps).
-#ifndef PA_NER_ADJ_REGZ
-#define PA_NER_ADJ_REGZ 0
-#endif
-#ifndef PA_NER_ADJ10_MINB
-#define PA_NER_ADJ10_MINB 6
-#endif
 
 namespace pa {
 
@@ -297,72 +287,6 @@ __device__ __forceinline__ void flush_windows(float2 *He, float2 *Ho, float2 *F,
   __syncwarp();
 }
 
-// Number of the 8 lanes i with P[i] <= x, for P[0..7] non-decreasing.
-__device__ __forceinline__ int count_le8(const int *P, int x) {
-  int c = 0;
-#pragma unroll
-  for (int st = 4; st > 0; st >>= 1)
-    if (P[c + st - 1] <= x) c += st;
-  if (c < 8 && P[c] <= x) ++c;
-  return c;
-}
-
-// flush_windows with a park of 8 lanes' windows (F[8][W]): the lanes
-// 8 g .. 8 g + 7 park theirs and the warp adds their sums, one group after
-// the other (groups may reach the same points; the passes are ordered).
-template <int W>
-__device__ __forceinline__ void flush_windows8(float2 *He, float2 *Ho, float2 *F, const int *P, const float2 (&acc)[W],
-                                               int lane, int sgn, int Mt) {
-#pragma unroll 1
-  for (int g = 0; g < 4; ++g) {
-    const int *Pg = P + 8 * g;
-    const int p0 = Pg[0];
-    if (p0 >= (1 << 29)) break;  // no window in this group or after it
-    int pm = p0;
-#pragma unroll
-    for (int i = 1; i < 8; ++i) pm = Pg[i] < (1 << 29) ? Pg[i] : pm;
-    if ((lane >> 3) == g) {
-#pragma unroll
-      for (int t = 0; t < W; ++t) F[(lane & 7) * W + t] = acc[t];
-    }
-    __syncwarp();
-    const int npts = pm + W - p0;
-    const bool plain = npts <= Mt;
-    for (int q0 = 0; q0 < npts; q0 += 32) {
-      const int p = p0 + q0 + lane;
-      if (q0 + lane < npts) {
-        const int hi = count_le8(Pg, p);
-        float2 v = make_float2(0.f, 0.f);
-        for (int i = count_le8(Pg, p - W); i < hi; ++i) v = cadd(v, F[i * W + (p - Pg[i])]);
-        if (v.x != 0.f || v.y != 0.f) {
-          const int e = wrap(sgn * p, Mt);
-          float2 *q = ((e & 1) ? Ho : He) + (e >> 1);
-          if (plain) {
-            *q = cadd(*q, v);
-          } else {
-            atomicAdd(&q->x, v.x);
-            atomicAdd(&q->y, v.y);
-          }
-        }
-      }
-    }
-    __syncwarp();
-  }
-}
-
-// Shared-memory shape of the adjoint warp kernels: REGZ keeps the depth
-// values in registers (Nz <= 512, and the depth transform's scratch fits in
-// the two half spectra), PARK entries follow the half spectra, and blocks of
-// THREADS threads get a register budget for MINB of them per SM.
-template <int LGT, int LGZ, int W>
-struct NerAdjShape {
-  static constexpr int HH = NerWarpShape<LGT, W>::HH, FS = NerWarpFs<LGZ>::FS;
-  static constexpr bool REGZ = PA_NER_ADJ_REGZ && LGZ <= 9 && 2 * HH >= FS;
-  static constexpr int PARK = REGZ ? 8 * W : FS;
-  static constexpr int THREADS = REGZ && LGT == 10 ? 64 : 128;
-  static constexpr int MINB = REGZ && LGT == 10 ? PA_NER_ADJ10_MINB : PA_NER_ADJ_MINB;
-};
-
 // Forward NER, warp v of the grid on slot v: the slot's column (both sources
 // of a two-source column, which lead at slot v with kind 2) is transformed in
 // t, interpolated at tau(j, l), weighted and transformed back over depth.
@@ -455,24 +379,22 @@ __global__ void __launch_bounds__(128, LGT <= 9 ? PA_NER_FWD_MINB : 1) k_ner_war
 // combination into the Nt centred samples, 1/phihat, into the G1 row of the
 // slot (summed over a two-source group).
 template <int LGT, int LGZ, int W>
-__global__ void __launch_bounds__(NerAdjShape<LGT, LGZ, W>::THREADS, NerAdjShape<LGT, LGZ, W>::MINB)
-    k_ner_warp_adj(const InstDesc *__restrict__ descs, const __grid_constant__ HornerTable ht) {
+__global__ void __launch_bounds__(128, PA_NER_ADJ_MINB) k_ner_warp_adj(const InstDesc *__restrict__ descs,
+                                                      const __grid_constant__ HornerTable ht) {
   griddep_enter();  // the previous kernel of the stream has completed
   extern __shared__ float4 smem_f4[];
   constexpr int Nt = 1 << LGT, Nz = 1 << LGZ;
-  using SH = NerAdjShape<LGT, LGZ, W>;
-  constexpr int HH = SH::HH, FS = SH::FS;
-  constexpr bool REGZ = SH::REGZ;
+  constexpr int HH = NerWarpShape<LGT, W>::HH, FS = NerWarpFs<LGZ>::FS;
   const InstDesc &d = descs[0];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int v = blockIdx.x * (blockDim.x >> 5) + wib;
   if (v >= ner_adj_slots(d)) return;
   const NerSlot lead = adj_slot(d, v);
   if (lead.kind != 1 && lead.kind != 2) return;
-  float2 *He = reinterpret_cast<float2 *>(smem_f4) + (size_t)wib * (2 * HH + SH::PARK);
+  float2 *He = reinterpret_cast<float2 *>(smem_f4) + (size_t)wib * (2 * HH + FS);
   float2 *Ho = He + HH;
-  float2 *Fs = Ho + HH;  // the depth values and the 32-lane park, or (REGZ) the 8-lane park
-  static_assert(REGZ || FS >= 32 * W, "window park in the depth scratch");
+  float2 *Fs = Ho + HH;
+  static_assert(FS >= 32 * W, "window park in the depth scratch");
   __shared__ int s_last[4][32];  // last window start of each lane (<= 4 warps per block)
   int *P = s_last[wib];
   const float2 *twT = d.tw + d.wtw + wtw_T(LGT);
@@ -485,23 +407,7 @@ __global__ void __launch_bounds__(NerAdjShape<LGT, LGZ, W>::THREADS, NerAdjShape
     const NerSlot sl = s == 0 ? lead : adj_slot(d, v + 1);
     const ColInfo ci = col_info(d, sl.jx, sl.iy);
     const float2 *srcz = d.Fz + ((size_t)(sl.jx + hx) * nY1 + sl.iy) * Nz;
-    constexpr int C2 = Nz / 64;  // pairs per lane: l = 1 + lane C2 .. (l < hz)
-    float2 zp[REGZ ? C2 : 1], zn[REGZ ? C2 : 1], fs1 = make_float2(0.f, 0.f);
-    if constexpr (REGZ) {
-      // the depth transform in the half spectra (free until they are
-      // cleared), then each lane's values F(l), F(-l) into registers
-      warp_fft<LGZ, -1>(He, twZ, lane, [&](int z) { return __ldg(srcz + z); }, [&](int k, float2 y) { He[k] = y; });
-      __syncwarp();
-#pragma unroll
-      for (int j = 0; j < C2; ++j) {
-        zp[j] = He[1 + lane * C2 + j];
-        zn[j] = He[Nz - 1 - lane * C2 - j];
-      }
-      fs1 = He[lane == 0 ? 0 : hz];
-      __syncwarp();
-    } else {
-      warp_fft<LGZ, -1>(Fs, twZ, lane, [&](int z) { return __ldg(srcz + z); }, [&](int k, float2 y) { Fs[k] = y; });
-    }
+    warp_fft<LGZ, -1>(Fs, twZ, lane, [&](int z) { return __ldg(srcz + z); }, [&](int k, float2 y) { Fs[k] = y; });
     for (int i = lane; i < 2 * HH; i += 32) He[i] = make_float2(0.f, 0.f);
     __syncwarp();
     const bool nyq = ci.xnyq || ci.ynyq;
@@ -515,6 +421,7 @@ __global__ void __launch_bounds__(NerAdjShape<LGT, LGZ, W>::THREADS, NerAdjShape
     // together (adding the points they leave into shared memory) as the first
     // tap advances.  Only the points a window leaves, and its last W, reach
     // shared memory.  l = 0 and the unpaired l = -hz are spread on their own.
+    constexpr int C2 = Nz / 64;  // pairs per lane: l = 1 + lane C2 .. (l < hz)
     // Points a window leaves inside the loop: lane i's are base values in
     // [first base, last base) of its own depths, ranges that do not overlap
     // from lane to lane (u increases with l), so lanes never add to the same
@@ -528,8 +435,10 @@ __global__ void __launch_bounds__(NerAdjShape<LGT, LGZ, W>::THREADS, NerAdjShape
     for (int t = 0; t < W; ++t) acc[t] = accn[t] = make_float2(0.f, 0.f);
     int base = 0;
     bool open = false;
-    // depth l = 1 + lane C2 + j with its values F(l), F(-l)
-    auto depth = [&](int l, float2 fl, float2 fml) {
+#pragma unroll 1
+    for (int j = 0; j < C2; ++j) {
+      const int l = 1 + lane * C2 + j;
+      if (l >= hz) break;
       const ff tau = tau_at(d, tb, l);
       const float wgt = weight_of(d, tau, l) * d.scale * half;
       int pu;
@@ -538,8 +447,8 @@ __global__ void __launch_bounds__(NerAdjShape<LGT, LGZ, W>::THREADS, NerAdjShape
       float wt[W];
       window_taps<W>(fr, ht, wt);
       const float2 ph = centring_phase(d, tau);
-      const float2 vp = cmul(cscale(fl, wgt), cconj(ph));
-      const float2 vn = cmul(cscale(fml, wgt), ph);
+      const float2 vp = cmul(cscale(Fs[l], wgt), cconj(ph));
+      const float2 vn = cmul(cscale(Fs[Nz - l], wgt), ph);
       if (!open) {
         base = pu;
         open = true;
@@ -573,32 +482,15 @@ __global__ void __launch_bounds__(NerAdjShape<LGT, LGZ, W>::THREADS, NerAdjShape
         acc[t] = __ffma2_rn(make_float2(wt[t], wt[t]), vp, acc[t]);
         accn[t] = __ffma2_rn(make_float2(wt[t], wt[t]), vn, accn[t]);
       }
-    };
-    if constexpr (REGZ) {
-#pragma unroll
-      for (int j = 0; j < C2; ++j)
-        if (1 + lane * C2 + j < hz) depth(1 + lane * C2 + j, zp[j], zn[j]);
-    } else {
-#pragma unroll 1
-      for (int j = 0; j < C2; ++j) {
-        const int l = 1 + lane * C2 + j;
-        if (l >= hz) break;
-        depth(l, Fs[l], Fs[Nz - l]);
-      }
-      fs1 = Fs[lane == 0 ? 0 : hz];  // read before Fs takes the windows
     }
     // the last windows (points base + t and -(base + t)); base does not
     // decrease from lane to lane, and the lanes without any depth are last
+    const float2 fs1 = Fs[lane == 0 ? 0 : hz];  // read before Fs takes the windows
     P[lane] = open ? base : (1 << 29);
+    const int pmax = __reduce_max_sync(0xffffffffu, open ? base : -(1 << 29));
     __syncwarp();  // every lane's loop (its reads of Fs and its flushes) is done
-    if constexpr (REGZ) {
-      flush_windows8<W>(He, Ho, Fs, P, acc, lane, 1, 2 * Nt);
-      flush_windows8<W>(He, Ho, Fs, P, accn, lane, -1, 2 * Nt);
-    } else {
-      const int pmax = __reduce_max_sync(0xffffffffu, open ? base : -(1 << 29));
-      flush_windows<W>(He, Ho, Fs, P, acc, lane, pmax, 1, 2 * Nt);
-      flush_windows<W>(He, Ho, Fs, P, accn, lane, pmax, -1, 2 * Nt);
-    }
+    flush_windows<W>(He, Ho, Fs, P, acc, lane, pmax, 1, 2 * Nt);
+    flush_windows<W>(He, Ho, Fs, P, accn, lane, pmax, -1, 2 * Nt);
     if (lane == 0 && ci.jx == 0 && ci.jy == 0) {  // l = 0 (W(j != 0, 0) = 0)
       const ff tau = tau_at(d, tb, 0);
       spread_split<W>(He, Ho, tau, cscale(fs1, weight_of(d, tau, 0) * d.scale * half), d, ht);
@@ -645,22 +537,16 @@ __global__ void __launch_bounds__(NerAdjShape<LGT, LGZ, W>::THREADS, NerAdjShape
 // Shared memory of one warp: He and Ho (Nt + W/2 entries each, or the
 // scratch of an Nt-point transform), then Fs (the scratch of an Nz-point
 // transform, >= Nz entries).
-// (the adjoint kernels that keep the depth values in registers: He, Ho and a
-// park of 8 lanes' windows; NerAdjShape)
-size_t smem_per_warp(const InstDesc &d, bool adj = false) {
-  const int scr_t = warp_scratch(pow2_log(d.Nt)), lgz = pow2_log(d.Nz);
+size_t smem_per_warp(const InstDesc &d) {
+  const int scr_t = warp_scratch(pow2_log(d.Nt));
   const int hh = scr_t > d.Nt + d.w / 2 ? scr_t : d.Nt + d.w / 2;
-  const bool regz = adj && PA_NER_ADJ_REGZ && lgz <= 9 && 2 * hh >= warp_scratch(lgz);
-  return size_t(2 * hh + (regz ? 8 * d.w : warp_scratch(lgz))) * sizeof(float2);
+  return size_t(2 * hh + warp_scratch(pow2_log(d.Nz))) * sizeof(float2);
 }
 
-int block_warps(const InstDesc &d, bool adj) { return smem_per_warp(d, adj) <= 12 * 1024 ? 4 : 2; }
-
 template <typename K>
-cudaError_t launch_warp_kernel(K kernel, const Launch &L, const InstDesc &h, int nslots, const HornerTable &ht,
-                               bool adj) {
-  const int nw = block_warps(h, adj);
-  const size_t smem = size_t(nw) * smem_per_warp(h, adj);
+cudaError_t launch_warp_kernel(K kernel, const Launch &L, const InstDesc &h, int nslots, const HornerTable &ht) {
+  const int nw = ner_warp_block_warps(h);
+  const size_t smem = smem_ner_warp(h);
   if (smem > 40 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
@@ -671,8 +557,8 @@ cudaError_t launch_warp_kernel(K kernel, const Launch &L, const InstDesc &h, int
 
 template <int LGT, int LGZ>
 cudaError_t launch_tz(const Launch &L, const InstDesc &h, const HornerTable &ht, int which) {
-  if (which == 1) return launch_warp_kernel(k_ner_warp_adj<LGT, LGZ, 8>, L, h, ner_adj_slots(h), ht, true);
-  return launch_warp_kernel(k_ner_warp<LGT, LGZ, 8>, L, h, ner_fwd_slots(h), ht, false);
+  if (which == 1) return launch_warp_kernel(k_ner_warp_adj<LGT, LGZ, 8>, L, h, ner_adj_slots(h), ht);
+  return launch_warp_kernel(k_ner_warp<LGT, LGZ, 8>, L, h, ner_fwd_slots(h), ht);
 }
 
 template <int LGT>
@@ -694,7 +580,7 @@ bool ner_warp_eligible(const InstDesc &d) {
 
 size_t smem_ner_warp(const InstDesc &d) { return size_t(ner_warp_block_warps(d)) * smem_per_warp(d); }
 
-int ner_warp_block_warps(const InstDesc &d) { return block_warps(d, false); }
+int ner_warp_block_warps(const InstDesc &d) { return smem_per_warp(d) <= 12 * 1024 ? 4 : 2; }
 
 cudaError_t launch_ner_warp(const Launch &L, const HornerTable &ht, int which) {
   if (!L.host || !ner_warp_eligible(*L.host)) return cudaErrorInvalidValue;
