@@ -11,18 +11,12 @@
 // optionally with the sensor-position gradient through the window
 // derivative).
 #include <cstring>
-#include <type_traits>
 
 #include "pa_device.cuh"
 #include "pa_tmap.h"
 
 // Blocks per SM the pipelined interpolation's register budget is set for
 // (its two 54 KB stages allow two).
-// 1: an interpolation tile's sensors past its last full round of lane groups
-// are split by footprint rows over the 4 groups of a warp.
-#ifndef PA_INTERP_SPLIT
-#define PA_INTERP_SPLIT 1
-#endif
 #ifndef PA_INTERP_MINB
 #define PA_INTERP_MINB 2
 #endif
@@ -1143,14 +1137,8 @@ __global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS, PA_INTER
     const int total = rpre[par][TX];
     const int n = n0 + 4 * l8;
     const int c = n0 / NC;
-    // One sensor (SPL false: all W footprint rows, by the lane group), or
-    // (SPL true: the rows q NR .. q NR + NR - 1 of it, q = the group's index
-    // in its warp, the 4 groups' sums then added by shuffles and written by
-    // group 0).
-    auto sensor = [&](auto spl, int u) {
-      constexpr bool SPL = decltype(spl)::value;
-      constexpr int NR = SPL ? W / 4 : W;
-      const int q = SPL ? (lane >> 3) : 0;
+#pragma unroll 1
+    for (int u = grp; u < total; u += ngrp) {
       int r = 0;
       while (r + 1 < TX && rpre[par][r + 1] <= u) ++r;
       const int i = rlo[par][r] + (u - rpre[par][r]);
@@ -1181,19 +1169,10 @@ __global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS, PA_INTER
       const int hr0 = r, hc0 = __float_as_int(pk[2 * W]) - q0;
       const int m = __float_as_int(pk[2 * W + 1]);
       float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (GRAD && n < Nt && (!SPL || q == 0))
-        gv = __ldg(reinterpret_cast<const float4 *>(io.g_in + (size_t)m * Nt + n));
+      if (GRAD && n < Nt) gv = __ldg(reinterpret_cast<const float4 *>(io.g_in + (size_t)m * Nt + n));
       float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), ax = a0, ay = a0;
 #pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        const int rr = SPL ? q * NR + k : k;
-        // the row's taps: with SPL, picked among the 4 groups' rows by q
-        // (selects, not a dynamic register index)
-        float wx = pk[k], dwx = GRAD ? pkd[k] : 0.f;
-        if (SPL) {
-          wx = q == 0 ? pk[k] : q == 1 ? pk[NR + k] : q == 2 ? pk[2 * NR + k] : pk[3 * NR + k];
-          if (GRAD) dwx = q == 0 ? pkd[k] : q == 1 ? pkd[NR + k] : q == 2 ? pkd[2 * NR + k] : pkd[3 * NR + k];
-        }
+      for (int rr = 0; rr < W; ++rr) {
         const float4 *row = reinterpret_cast<const float4 *>(Gs + ((size_t)(hr0 + rr) * HY + hc0) * NC) + l8;
         float4 rs = make_float4(0.f, 0.f, 0.f, 0.f), rsy = rs;
 #pragma unroll
@@ -1209,8 +1188,10 @@ __global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS, PA_INTER
             rsy.w = fmaf(dwy, v.w, rsy.w);
           }
         }
+        const float wx = pk[rr];
         fma4(wx, rs, a0);
         if (GRAD) {
+          const float dwx = pkd[rr];
           ax.x = fmaf(dwx, rs.x, ax.x);
           ax.y = fmaf(dwx, rs.y, ax.y);
           ax.z = fmaf(dwx, rs.z, ax.z);
@@ -1220,23 +1201,6 @@ __global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS, PA_INTER
           ay.z = fmaf(wx, rsy.z, ay.z);
           ay.w = fmaf(wx, rsy.w, ay.w);
         }
-      }
-      if constexpr (SPL) {
-        auto wsum = [](float4 &a) {
-#pragma unroll
-          for (int off = 8; off < 32; off <<= 1) {
-            a.x += __shfl_xor_sync(0xffffffffu, a.x, off);
-            a.y += __shfl_xor_sync(0xffffffffu, a.y, off);
-            a.z += __shfl_xor_sync(0xffffffffu, a.z, off);
-            a.w += __shfl_xor_sync(0xffffffffu, a.w, off);
-          }
-        };
-        wsum(a0);
-        if (GRAD) {
-          wsum(ax);
-          wsum(ay);
-        }
-        if (q != 0) return;
       }
       // Nt % 4 == 0: the 4 samples of a lane are all below Nt or all past it
       if (io.g_out && n < Nt) *reinterpret_cast<float4 *>(io.g_out + (size_t)m * Nt + n) = a0;
@@ -1253,19 +1217,6 @@ __global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS, PA_INTER
         }
         if (l8 == 0) d.grad_part[(size_t)c * M + i] = make_float2(px, py);
       }
-    };
-    // Whole sensors in rounds of one per lane group; with more sensors than
-    // groups, the ones past the last full round go a quarter of their rows
-    // per group, a warp per sensor, so that a tile of ngrp + 8 sensors takes
-    // 1.25 rounds instead of 2.
-    constexpr bool SPLIT = PA_INTERP_SPLIT && W % 4 == 0;
-    const int nwhole = (!SPLIT || total <= ngrp) ? total : total - total % ngrp;
-#pragma unroll 1
-    for (int u = grp; u < nwhole; u += ngrp) sensor(std::false_type{}, u);
-    if constexpr (SPLIT) {
-      const int wp = tid >> 5, nwp = nthr >> 5;
-#pragma unroll 1
-      for (int u = nwhole + wp; u < total; u += nwp) sensor(std::true_type{}, u);  // warp-uniform
     }
   };
   tile_pipeline_n<S::NS>(nwork, buf0, S::BUF / 2, bars, d.status, issue, compute,
