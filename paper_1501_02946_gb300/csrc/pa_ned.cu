@@ -73,6 +73,10 @@ constexpr int kThreadsCol = 256;
 #ifndef PA_FFT9_NCP
 #define PA_FFT9_NCP 8
 #endif
+// blocks per SM the shorter pipelines budget registers for
+#ifndef PA_FFT_MINB
+#define PA_FFT_MINB 1
+#endif
 #ifndef PA_FFT9_THREADS
 #define PA_FFT9_THREADS 256
 #endif
@@ -84,7 +88,7 @@ __host__ __device__ constexpr int pipe_nc(int lgl) { return lgl >= 9 ? PA_FFT9_N
 template <int LGL>
 struct PipeTile {
   static constexpr int threads = LGL >= 9 ? PA_FFT9_THREADS : 256;
-  static constexpr int minb = LGL >= 9 ? PA_FFT9_MINB : 1;
+  static constexpr int minb = LGL >= 9 ? PA_FFT9_MINB : PA_FFT_MINB;
   static constexpr int nc = pipe_nc(LGL);
   static constexpr int lgnc = nc == 16 ? 4 : (nc == 8 ? 3 : 2);
 };
