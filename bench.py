@@ -655,15 +655,24 @@ def run_ours(args):
     ev_cmp = [torch.cuda.Event() for _ in range(2)]
     ev_d2h = [torch.cuda.Event() for _ in range(2)]
 
+    def h2d(k):
+        b = k & 1
+        with torch.cuda.stream(s_h2d):
+            if k >= 2:
+                s_h2d.wait_event(ev_d2h[b])  # set b's previous step is copied out
+            bufs[b][0].copy_(g_h, non_blocking=True)
+            ev_h2d[b].record(s_h2d)
+
     def pipelined(n):
+        # the input copy of step k + 1 is issued before step k's compute and
+        # output copies, so that it never queues behind them (copies of both
+        # directions may share a copy engine, which runs them in issue order)
+        h2d(0)
         for k in range(n):
             b = k & 1
             gb, fb, g2b = bufs[b]
-            with torch.cuda.stream(s_h2d):
-                if k >= 2:
-                    s_h2d.wait_event(ev_d2h[b])  # set b's previous step is copied out
-                gb.copy_(g_h, non_blocking=True)
-                ev_h2d[b].record(s_h2d)
+            if k + 1 < n:
+                h2d(k + 1)
             stream.wait_event(ev_h2d[b])
             plan.reconstruct(gb, out=fb)
             plan.adjoint(fb, out=g2b)
