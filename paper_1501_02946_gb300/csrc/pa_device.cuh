@@ -336,9 +336,12 @@ __device__ __forceinline__ void fft_stage(float2 *buf, int estride, int nb, int 
 // one sequence (b) for all its items of a round.
 __device__ __forceinline__ int ilog2_pow2(int x) { return __ffs(x) - 1; }
 
-template <int R, int DIR, int PADSH>
+// BAND: input rows zlo .. zhi - 1 are read as zeros (not loaded), and output
+// rows olo .. ohi - 1 are not stored.
+template <int R, int DIR, int PADSH, bool BAND = false>
 __device__ __forceinline__ void fft_stage_p2(float2 *buf, int estride, int lgnb, int lgL, int lgNs,
-                                             const float2 *__restrict__ tw, int tid, int lgT, int bar_id) {
+                                             const float2 *__restrict__ tw, int tid, int lgT, int bar_id,
+                                             int zlo = 0, int zhi = 0, int olo = 0, int ohi = 0) {
   constexpr int IPT = Ipt<R>::v;
   constexpr int LGR = R == 32 ? 5 : (R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1)));
   constexpr int LGIPT = IPT == 1 ? 0 : (IPT == 2 ? 1 : 2);
@@ -362,7 +365,8 @@ __device__ __forceinline__ void fft_stage_p2(float2 *buf, int estride, int lgnb,
         const int k = j & kmask;
 #pragma unroll
         for (int t = 0; t < R; ++t) {
-          float2 x = buf[pad_row<PADSH>(j + (t << lgnj)) * estride + b];
+          const int row = j + (t << lgnj);
+          float2 x = (BAND && row >= zlo && row < zhi) ? make_float2(0.f, 0.f) : buf[pad_row<PADSH>(row) * estride + b];
           if (t > 0) {  // tw[0] = 1 leaves x unchanged
             float2 w = __ldg(tw + ((t * k) << lgtw));
             if (DIR > 0) w.y = -w.y;
@@ -381,7 +385,10 @@ __device__ __forceinline__ void fft_stage_p2(float2 *buf, int estride, int lgnb,
         Dft<R, DIR>::run(v[it]);
         const int o = ((j >> lgNs) << (lgNs + LGR)) + k;
 #pragma unroll
-        for (int t = 0; t < R; ++t) buf[pad_row<PADSH>(o + (t << lgNs)) * estride + b] = v[it][t];
+        for (int t = 0; t < R; ++t) {
+          const int row = o + (t << lgNs);
+          if (!BAND || row < olo || row >= ohi) buf[pad_row<PADSH>(row) * estride + b] = v[it][t];
+        }
       }
     }
     group_sync(bar_id, 1 << lgT);
@@ -392,12 +399,16 @@ __device__ __forceinline__ void fft_stage_p2(float2 *buf, int estride, int lgnb,
 // -4 or -2 stage): every index split folds to constants, so the transform can
 // sit inside a loop without its address arithmetic being kept live across
 // iterations.  Sequences and threads as in fft_stage_p2.
-template <int LGL, int DIR, int PADSH = 0>
+// BAND (length 512 only): input rows zlo .. zhi - 1 are zeros and are not
+// read, output rows olo .. ohi - 1 are not needed and are not written.
+template <int LGL, int DIR, int PADSH = 0, bool BAND = false>
 __device__ __forceinline__ void fft_fixed(float2 *buf, int estride, int lgnb, int lgT, const float2 *__restrict__ tw,
-                                          int tid, int bar_id = 0) {
+                                          int tid, int bar_id = 0, int zlo = 0, int zhi = 0, int olo = 0,
+                                          int ohi = 0) {
+  static_assert(!BAND || LGL == 9, "bands for the 512-point schedule only");
   if constexpr (LGL == 9) {  // 16 x 32: two passes through shared memory instead of three
-    fft_stage_p2<16, DIR, PADSH>(buf, estride, lgnb, LGL, 0, tw, tid, lgT, bar_id);
-    fft_stage_p2<32, DIR, PADSH>(buf, estride, lgnb, LGL, 4, tw, tid, lgT, bar_id);
+    fft_stage_p2<16, DIR, PADSH, BAND>(buf, estride, lgnb, LGL, 0, tw, tid, lgT, bar_id, zlo, zhi, 0, 0);
+    fft_stage_p2<32, DIR, PADSH, BAND>(buf, estride, lgnb, LGL, 4, tw, tid, lgT, bar_id, 0, 0, olo, ohi);
     return;
   }
   constexpr int n16 = LGL / 4, rem = LGL % 4;

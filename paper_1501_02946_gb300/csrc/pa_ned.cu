@@ -86,6 +86,12 @@ constexpr int kThreadsCol = 256;
 #define PA_FFT9_MINB 2
 #endif
 static_assert(PA_FFT9_NCP == 16 || PA_FFT9_NCP == 8 || PA_FFT9_NCP == 4, "length-512 tile width");
+// 1: the 512-point transforms skip the rows known to be zero on input (the
+// inverse row FFT's unfilled bins, the adjoint column FFT's dropped ones) and
+// the rows not needed on output (the forward transforms' truncated bins).
+#ifndef PA_FFT9_BAND
+#define PA_FFT9_BAND 1
+#endif
 __host__ __device__ constexpr int pipe_nc(int lgl) { return lgl >= 9 ? PA_FFT9_NCP : 16; }
 template <int LGL>
 struct PipeTile {
@@ -93,6 +99,7 @@ struct PipeTile {
   static constexpr int minb = LGL >= 9 ? PA_FFT9_MINB : PA_FFT_MINB;
   static constexpr int nc = pipe_nc(LGL);
   static constexpr int lgnc = nc == 16 ? 4 : (nc == 8 ? 3 : 2);
+  static constexpr bool band = LGL == 9 && PA_FFT9_BAND;
 };
 constexpr int kThreadsSpread = 256;  // 8 warps = 8 grid columns of one strip
 constexpr int kThreadsInterp = 256;
@@ -572,7 +579,8 @@ __global__ void __launch_bounds__(PipeTile<LGL>::threads, PipeTile<LGL>::minb) k
   auto compute = [&](int w, float2 *buf) {
     const int jy = w / nchunks, n0 = (w - jy * nchunks) * NC;
     if (!ADJ) {
-      fft_fixed<LGL, -1>(buf, NC, LGNC, lgT, tw, tid);
+      // bins hx + 1 .. L - hx - 1 are truncated: not written
+      fft_fixed<LGL, -1, 0, PipeTile<LGL>::band>(buf, NC, LGNC, lgT, tw, tid, 0, 0, 0, hx + 1, L - hx);
       if (use_omap) {
         // scale the kept bins in place (bin (ix - hx) mod L holds row ix)
         for (int idx = tid; idx < nX1 * NC; idx += nthr) {
@@ -597,13 +605,16 @@ __global__ void __launch_bounds__(PipeTile<LGL>::threads, PipeTile<LGL>::minb) k
       }
     } else {
       // bins jx mod Mx hold G1 row jx + hx; scale them, clear the others
+      // (with the band, bins hx + 1 .. L - hx - 1 are not read: left as they are)
+      constexpr bool BAND = PipeTile<LGL>::band;
       for (int idx = tid; idx < L * NC; idx += nthr) {
         const int r = idx >> LGNC;
+        if (BAND && r > hx && r < L - hx) continue;
         const int ix = (r + hx) & (L - 1);
         buf[idx] = ix < nX1 ? cscale(buf[idx], __ldg(d.invphx + ix)) : make_float2(0.f, 0.f);
       }
       __syncthreads();
-      fft_fixed<LGL, +1>(buf, NC, LGNC, lgT, tw, tid);
+      fft_fixed<LGL, +1, 0, BAND>(buf, NC, LGNC, lgT, tw, tid, 0, hx + 1, L - hx);
       if (use_omap) {
         fence_proxy_async_smem();  // the transform's writes precede the stores' reads
         __syncthreads();
@@ -665,7 +676,8 @@ __global__ void __launch_bounds__(PipeTile<LGL>::threads, PipeTile<LGL>::minb) k
   float4 *O = reinterpret_cast<float4 *>(buf1 + L * NCP);  // [nY1][NCP] staged (a, b) pairs
   auto compute = [&](int w, float2 *buf) {
     const int p = w / nchunks, n0 = (w - p * nchunks) * 2 * NCP;
-    fft_fixed<LGL, -1>(buf, NCP, LGNCP, lgT, tw, tid);
+    // bins nY1 .. L - nY1 are read by no jy: not written
+    fft_fixed<LGL, -1, 0, PipeTile<LGL>::band>(buf, NCP, LGNCP, lgT, tw, tid, 0, 0, 0, nY1, L - nY1 + 1);
     if (use_omap) {
       if (tid == 0) bulk_wait_read<0>();  // the previous tile's stores have read O
       __syncthreads();
@@ -829,10 +841,13 @@ __global__ void __launch_bounds__(PipeTile<LGL>::threads, PipeTile<LGL>::minb) k
         S[(L - jy) * NCP + kk] = make_float2(0.5f * (a.x + b.y), 0.5f * (b.x - a.y));
       }
     }
-    for (int idx = tid; idx < (L - 2 * nY1 + 1) * (NCP / 2); idx += nthr)
-      reinterpret_cast<float4 *>(S + nY1 * NCP)[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // (with the band, the transform reads those bins as zeros)
+    constexpr bool BAND = PipeTile<LGL>::band;
+    if (!BAND)
+      for (int idx = tid; idx < (L - 2 * nY1 + 1) * (NCP / 2); idx += nthr)
+        reinterpret_cast<float4 *>(S + nY1 * NCP)[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
-    fft_fixed<LGL, +1>(S, NCP, LGNCP, lgT, tw, tid);
+    fft_fixed<LGL, +1, 0, BAND>(S, NCP, LGNCP, lgT, tw, tid, 0, nY1, L - nY1 + 1);
     if (use_omap) {
       fence_proxy_async_smem();  // the transform's writes precede the stores' reads
       __syncthreads();
