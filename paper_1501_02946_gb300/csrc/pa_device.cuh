@@ -336,12 +336,11 @@ __device__ __forceinline__ void fft_stage(float2 *buf, int estride, int nb, int 
 // one sequence (b) for all its items of a round.
 __device__ __forceinline__ int ilog2_pow2(int x) { return __ffs(x) - 1; }
 
-// BAND: input rows zlo .. zhi - 1 are read as zeros (not loaded), and output
-// rows olo .. ohi - 1 are not stored.
+// BAND: input rows zlo .. zhi - 1 are read as zeros (not loaded).
 template <int R, int DIR, int PADSH, bool BAND = false>
 __device__ __forceinline__ void fft_stage_p2(float2 *buf, int estride, int lgnb, int lgL, int lgNs,
                                              const float2 *__restrict__ tw, int tid, int lgT, int bar_id,
-                                             int zlo = 0, int zhi = 0, int olo = 0, int ohi = 0) {
+                                             int zlo = 0, int zhi = 0) {
   constexpr int IPT = Ipt<R>::v;
   constexpr int LGR = R == 32 ? 5 : (R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1)));
   constexpr int LGIPT = IPT == 1 ? 0 : (IPT == 2 ? 1 : 2);
@@ -385,10 +384,7 @@ __device__ __forceinline__ void fft_stage_p2(float2 *buf, int estride, int lgnb,
         Dft<R, DIR>::run(v[it]);
         const int o = ((j >> lgNs) << (lgNs + LGR)) + k;
 #pragma unroll
-        for (int t = 0; t < R; ++t) {
-          const int row = o + (t << lgNs);
-          if (!BAND || row < olo || row >= ohi) buf[pad_row<PADSH>(row) * estride + b] = v[it][t];
-        }
+        for (int t = 0; t < R; ++t) buf[pad_row<PADSH>(o + (t << lgNs)) * estride + b] = v[it][t];
       }
     }
     group_sync(bar_id, 1 << lgT);
@@ -400,15 +396,14 @@ __device__ __forceinline__ void fft_stage_p2(float2 *buf, int estride, int lgnb,
 // sit inside a loop without its address arithmetic being kept live across
 // iterations.  Sequences and threads as in fft_stage_p2.
 // BAND (length 512 only): input rows zlo .. zhi - 1 are zeros and are not
-// read, output rows olo .. ohi - 1 are not needed and are not written.
+// read (the first pass takes them as zeros; it writes every row).
 template <int LGL, int DIR, int PADSH = 0, bool BAND = false>
 __device__ __forceinline__ void fft_fixed(float2 *buf, int estride, int lgnb, int lgT, const float2 *__restrict__ tw,
-                                          int tid, int bar_id = 0, int zlo = 0, int zhi = 0, int olo = 0,
-                                          int ohi = 0) {
-  static_assert(!BAND || LGL == 9, "bands for the 512-point schedule only");
+                                          int tid, int bar_id = 0, int zlo = 0, int zhi = 0) {
+  static_assert(!BAND || LGL == 9, "a zero band for the 512-point schedule only");
   if constexpr (LGL == 9) {  // 16 x 32: two passes through shared memory instead of three
-    fft_stage_p2<16, DIR, PADSH, BAND>(buf, estride, lgnb, LGL, 0, tw, tid, lgT, bar_id, zlo, zhi, 0, 0);
-    fft_stage_p2<32, DIR, PADSH, BAND>(buf, estride, lgnb, LGL, 4, tw, tid, lgT, bar_id, 0, 0, olo, ohi);
+    fft_stage_p2<16, DIR, PADSH, BAND>(buf, estride, lgnb, LGL, 0, tw, tid, lgT, bar_id, zlo, zhi);
+    fft_stage_p2<32, DIR, PADSH>(buf, estride, lgnb, LGL, 4, tw, tid, lgT, bar_id);
     return;
   }
   constexpr int n16 = LGL / 4, rem = LGL % 4;

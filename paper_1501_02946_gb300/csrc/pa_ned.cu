@@ -86,9 +86,10 @@ constexpr int kThreadsCol = 256;
 #define PA_FFT9_MINB 2
 #endif
 static_assert(PA_FFT9_NCP == 16 || PA_FFT9_NCP == 8 || PA_FFT9_NCP == 4, "length-512 tile width");
-// 1: the 512-point transforms skip the rows known to be zero on input (the
-// inverse row FFT's unfilled bins, the adjoint column FFT's dropped ones) and
-// the rows not needed on output (the forward transforms' truncated bins).
+// 1: the 512-point inverse row FFT reads its unfilled bins nY1 .. L - nY1 as
+// zeros instead of clearing them (skipping truncated bins on output in the
+// forward transforms, or the dropped bins on input of the adjoint column
+// transform, was slower: 357 -> 431, 195 -> 234, 221 -> 235 us).
 #ifndef PA_FFT9_BAND
 #define PA_FFT9_BAND 1
 #endif
@@ -579,8 +580,7 @@ __global__ void __launch_bounds__(PipeTile<LGL>::threads, PipeTile<LGL>::minb) k
   auto compute = [&](int w, float2 *buf) {
     const int jy = w / nchunks, n0 = (w - jy * nchunks) * NC;
     if (!ADJ) {
-      // bins hx + 1 .. L - hx - 1 are truncated: not written
-      fft_fixed<LGL, -1, 0, PipeTile<LGL>::band>(buf, NC, LGNC, lgT, tw, tid, 0, 0, 0, hx + 1, L - hx);
+      fft_fixed<LGL, -1>(buf, NC, LGNC, lgT, tw, tid);
       if (use_omap) {
         // scale the kept bins in place (bin (ix - hx) mod L holds row ix)
         for (int idx = tid; idx < nX1 * NC; idx += nthr) {
@@ -605,16 +605,13 @@ __global__ void __launch_bounds__(PipeTile<LGL>::threads, PipeTile<LGL>::minb) k
       }
     } else {
       // bins jx mod Mx hold G1 row jx + hx; scale them, clear the others
-      // (with the band, bins hx + 1 .. L - hx - 1 are not read: left as they are)
-      constexpr bool BAND = PipeTile<LGL>::band;
       for (int idx = tid; idx < L * NC; idx += nthr) {
         const int r = idx >> LGNC;
-        if (BAND && r > hx && r < L - hx) continue;
         const int ix = (r + hx) & (L - 1);
         buf[idx] = ix < nX1 ? cscale(buf[idx], __ldg(d.invphx + ix)) : make_float2(0.f, 0.f);
       }
       __syncthreads();
-      fft_fixed<LGL, +1, 0, BAND>(buf, NC, LGNC, lgT, tw, tid, 0, hx + 1, L - hx);
+      fft_fixed<LGL, +1>(buf, NC, LGNC, lgT, tw, tid);
       if (use_omap) {
         fence_proxy_async_smem();  // the transform's writes precede the stores' reads
         __syncthreads();
@@ -676,8 +673,7 @@ __global__ void __launch_bounds__(PipeTile<LGL>::threads, PipeTile<LGL>::minb) k
   float4 *O = reinterpret_cast<float4 *>(buf1 + L * NCP);  // [nY1][NCP] staged (a, b) pairs
   auto compute = [&](int w, float2 *buf) {
     const int p = w / nchunks, n0 = (w - p * nchunks) * 2 * NCP;
-    // bins nY1 .. L - nY1 are read by no jy: not written
-    fft_fixed<LGL, -1, 0, PipeTile<LGL>::band>(buf, NCP, LGNCP, lgT, tw, tid, 0, 0, 0, nY1, L - nY1 + 1);
+    fft_fixed<LGL, -1>(buf, NCP, LGNCP, lgT, tw, tid);
     if (use_omap) {
       if (tid == 0) bulk_wait_read<0>();  // the previous tile's stores have read O
       __syncthreads();
