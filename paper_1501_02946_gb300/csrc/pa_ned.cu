@@ -17,12 +17,6 @@
 
 // Blocks per SM the pipelined interpolation's register budget is set for
 // (its two 54 KB stages allow two).
-#ifndef PA_INTERP_NC
-#define PA_INTERP_NC 32
-#endif
-#ifndef PA_INTERP_NC16_MINB
-#define PA_INTERP_NC16_MINB 3
-#endif
 #ifndef PA_INTERP_MINB
 #define PA_INTERP_MINB 2
 #endif
@@ -1035,12 +1029,7 @@ __global__ void __launch_bounds__(kThreadsInterp) k_interp(const InstDesc *__res
 // loads, 128-byte output rows): a warp interpolates 4 sensors at once.
 template <int W, int TY, bool GRAD, int NSTAGE>
 struct InterpPipe {
-  // samples per tile: 32 (4 per lane), or for the interpolation without the
-  // gradient PA_INTERP_NC = 16 (2 per lane: buffers small enough for 3 blocks
-  // per SM, with a register budget for PA_INTERP_NC16_MINB of them)
-  static constexpr int TX = 8, NC = GRAD ? 32 : PA_INTERP_NC;
-  static constexpr int MINB = NC == 16 ? PA_INTERP_NC16_MINB : PA_INTERP_MINB;
-  static_assert(NC == 32 || NC == 16, "tile samples");
+  static constexpr int TX = 8, NC = 32;
   static constexpr int HX = TX + W - 1, HY = TY + W - 1, CELLS = HX * HY;
   static constexpr int SMAX = TX * TY;  // packed sensors per tile
   static constexpr int PW = ipack_words(W), PD = GRAD ? ipackd_words(W) : 0;
@@ -1052,7 +1041,7 @@ struct InterpPipe {
 };
 
 template <int W, int TY, bool GRAD, int NS>
-__global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS, InterpPipe<W, TY, GRAD, NS>::MINB) k_interp_pipe(const InstDesc *__restrict__ descs, IoPtrs io,
+__global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS, PA_INTERP_MINB) k_interp_pipe(const InstDesc *__restrict__ descs, IoPtrs io,
                                                                 int nwork, const __grid_constant__ CUtensorMap g0map,
                                                                 int use_map) {
   griddep_enter();  // the previous kernel of the stream has completed
@@ -1163,7 +1152,7 @@ __global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS, InterpPi
     const float *Gs = reinterpret_cast<const float *>(buf);
     const float *packs = Gs + CELLS * NC, *packd = packs + SMAX * PW;
     const int total = rpre[par][TX];
-    const int n = n0 + (NC / 8) * l8;
+    const int n = n0 + 4 * l8;
     const int c = n0 / NC;
 #pragma unroll 1
     for (int u = grp; u < total; u += ngrp) {
@@ -1196,20 +1185,6 @@ __global__ void __launch_bounds__(InterpPipe<W, TY, GRAD, NS>::THREADS, InterpPi
       }
       const int hr0 = r, hc0 = __float_as_int(pk[2 * W]) - q0;
       const int m = __float_as_int(pk[2 * W + 1]);
-      if constexpr (NC == 16) {  // 2 samples per lane (8-byte shared loads)
-        float2 a0 = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int rr = 0; rr < W; ++rr) {
-          const float2 *row = reinterpret_cast<const float2 *>(Gs + ((size_t)(hr0 + rr) * HY + hc0) * NC) + l8;
-          float2 rs = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int t = 0; t < W; ++t) rs = __ffma2_rn(make_float2(pk[W + t], pk[W + t]), row[t * (NC / 2)], rs);
-          a0 = __ffma2_rn(make_float2(pk[rr], pk[rr]), rs, a0);
-        }
-        // Nt % 4 == 0: the 2 samples of a lane are both below Nt or both past it
-        if (io.g_out && n < Nt) *reinterpret_cast<float2 *>(io.g_out + (size_t)m * Nt + n) = a0;
-        continue;
-      }
       float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
       if (GRAD && n < Nt) gv = __ldg(reinterpret_cast<const float4 *>(io.g_in + (size_t)m * Nt + n));
       float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), ax = a0, ay = a0;
@@ -1368,16 +1343,16 @@ cudaError_t launch_spread(const Launch &L, int spl) {
 // buffers of at most 128 KB).
 
 // Tensor map of the real grid G0 [Mx][My][Nt] (float) with box
-// nc x hy x hx (samples, columns, rows) for the interpolation tiles, through
+// 32 x hy x hx (samples, columns, rows) for the interpolation tiles, through
 // the driver's encoder (looked up once).  False (with the map zeroed) if the
 // encoder or the layout is not available.
-static bool encode_g0_box(const InstDesc &h, int hx, int hy, int nc, CUtensorMap *map) {
+static bool encode_g0_box(const InstDesc &h, int hx, int hy, CUtensorMap *map) {
   std::memset(map, 0, sizeof(*map));
   PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
   if (!encode || (h.Nt % 4) != 0 || hx > 256 || hy > 256 || (reinterpret_cast<uintptr_t>(h.G0) & 15u)) return false;
   const cuuint64_t dims[3] = {cuuint64_t(h.Nt), cuuint64_t(h.My), cuuint64_t(h.Mx)};
   const cuuint64_t strides[2] = {cuuint64_t(h.Nt) * sizeof(float), cuuint64_t(h.My) * h.Nt * sizeof(float)};
-  const cuuint32_t box[3] = {cuuint32_t(nc), cuuint32_t(hy), cuuint32_t(hx)};
+  const cuuint32_t box[3] = {32u, cuuint32_t(hy), cuuint32_t(hx)};
   const cuuint32_t estr[3] = {1u, 1u, 1u};
   const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h.G0, dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1524,8 +1499,8 @@ static bool launch_interp_pipe(const Launch &L, cudaError_t &err) {
   err = set_smem(kp, IP::smem);
   if (err != cudaSuccess) return true;
   CUtensorMap map;
-  const int use_map = encode_g0_box(h, IP::HX, IP::HY, IP::NC, &map) ? 1 : 0;
-  const int nwork = ((h.Mx + IP::TX - 1) / IP::TX) * ((h.My + TY - 1) / TY) * ((h.Nt + IP::NC - 1) / IP::NC);
+  const int use_map = encode_g0_box(h, IP::HX, IP::HY, &map) ? 1 : 0;
+  const int nwork = blocks_interp(h);
   const int grid = persistent_grid(kp, IP::THREADS, IP::smem, nwork);
   err = launch_pdl(kp, grid, IP::THREADS, IP::smem, L.stream, L.descs, L.io, nwork, map, use_map);
   return true;
