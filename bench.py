@@ -638,16 +638,23 @@ def run_ours(args):
         f_h.copy_(f, non_blocking=True)
         g2_h.copy_(g2, non_blocking=True)
     torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(n_e2e):
-        g.copy_(g_h, non_blocking=True)
-        step()
-        f_h.copy_(f, non_blocking=True)
-        g2_h.copy_(g2, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_serial_ms = e0.elapsed_time(e1) / n_e2e
+    # each end-to-end figure is the median of E2E_REPEATS runs of n_e2e steps:
+    # the host copies share the machine's host memory with other jobs, and a
+    # single copy has been seen to stall for several milliseconds
+    E2E_REPEATS = 3
+    serial_runs = []
+    for _ in range(E2E_REPEATS):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_e2e):
+            g.copy_(g_h, non_blocking=True)
+            step()
+            f_h.copy_(f, non_blocking=True)
+            g2_h.copy_(g2, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        serial_runs.append(e0.elapsed_time(e1) / n_e2e)
+    e2e_serial_ms = sorted(serial_runs)[E2E_REPEATS // 2]
 
     NB = 3  # device buffer sets
     bufs = [(g, f, g2)] + [(torch.empty_like(g), torch.empty_like(f), torch.empty_like(g2)) for _ in range(NB - 1)]
@@ -686,12 +693,15 @@ def run_ours(args):
 
     pipelined(4)
     torch.cuda.synchronize(dev)
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record(s_h2d)
-    pipelined(n_e2e)
-    p1.record(s_d2h)
-    torch.cuda.synchronize(dev)
-    e2e_ms = p0.elapsed_time(p1) / n_e2e
+    pipe_runs = []
+    for _ in range(E2E_REPEATS):
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(s_h2d)
+        pipelined(n_e2e)
+        p1.record(s_d2h)
+        torch.cuda.synchronize(dev)
+        pipe_runs.append(p0.elapsed_time(p1) / n_e2e)
+    e2e_ms = sorted(pipe_runs)[E2E_REPEATS // 2]
     if world > 1:
         t = torch.tensor([e2e_ms, e2e_serial_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -700,7 +710,9 @@ def run_ours(args):
            "d2h_bytes_per_step": (f_h.numel() + g2_h.numel()) * 4, "ms_per_step": e2e_ms,
            "overlap": "pipelined: H2D of step k+1 and D2H of step k overlap the compute (three buffer sets, "
                       "three streams); serial_* is copy, compute, copy on one stream",
-           "serial_ms_per_step": e2e_serial_ms, "serial_value": world * voxels / (e2e_serial_ms / 1e3)}
+           "serial_ms_per_step": e2e_serial_ms, "serial_value": world * voxels / (e2e_serial_ms / 1e3),
+           "repeats": {"steps_each": n_e2e, "ms_per_step": [round(x, 4) for x in pipe_runs],
+                       "serial_ms_per_step": [round(x, 4) for x in serial_runs], "reported": "median"}}
     del bufs
 
     cpu, acc = None, None
